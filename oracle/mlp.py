@@ -1,0 +1,97 @@
+"""FP64 reference multilayer perceptron for the learned surrogate (oracle; tests only).
+
+The surrogate is not in the paper; it is a fully connected network
+5 -> 256 -> 256 -> 256 -> 80 with GELU activations on the hidden layers, mapping
+normalized (alpha, log10 K_C, a, log10 K_T, omega) to 40 normalized head positions
+(x, y).  Loss: mean squared error over all outputs of a batch.  Optimizer: Adam
+(Kingma & Ba 2015) with bias correction.
+
+Parameters are a list of (W[out, in], b[out]).  GELU(x) = x Phi(x) = x (1 + erf(x/sqrt 2))/2.
+
+Pins (tests/test_oracle_mlp.py): gradients against central finite differences of the
+loss; GELU derivative against finite differences; an Adam step against its textbook
+formula on one scalar.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+from scipy import special
+
+LAYERS = (5, 256, 256, 256, 80)
+
+
+def init_params(rng, layers=LAYERS):
+    """He-style uniform init: W ~ U(-sqrt(6/in), sqrt(6/in)) / sqrt(2), b = 0."""
+    ps = []
+    for fi, fo in zip(layers[:-1], layers[1:]):
+        lim = math.sqrt(3.0 / fi)
+        ps.append((rng.uniform(-lim, lim, size=(fo, fi)), np.zeros(fo)))
+    return ps
+
+
+def gelu(x):
+    return 0.5 * x * (1.0 + special.erf(x / math.sqrt(2.0)))
+
+
+def gelu_grad(x):
+    return 0.5 * (1.0 + special.erf(x / math.sqrt(2.0))) + x * np.exp(-0.5 * x * x) / math.sqrt(2.0 * math.pi)
+
+
+def forward(params, x, keep=False):
+    """x[batch, 5] -> y[batch, 80]; with keep=True also the pre-activations."""
+    h = np.asarray(x, dtype=np.float64)
+    pre = []
+    acts = [h]
+    for li, (W, b) in enumerate(params):
+        z = h @ W.T + b
+        pre.append(z)
+        h = gelu(z) if li < len(params) - 1 else z
+        acts.append(h)
+    return (h, pre, acts) if keep else h
+
+
+def loss(params, x, t):
+    y = forward(params, x)
+    return float(np.mean((y - t) ** 2))
+
+
+def backward(params, x, t):
+    """Gradients of the mean squared error loss with respect to every W and b."""
+    y, pre, acts = forward(params, x, keep=True)
+    g = 2.0 * (y - t) / y.size
+    grads = [None] * len(params)
+    for li in range(len(params) - 1, -1, -1):
+        W, _ = params[li]
+        if li < len(params) - 1:
+            g = g * gelu_grad(pre[li])
+        grads[li] = (g.T @ acts[li], g.sum(axis=0))
+        g = g @ W
+    return grads
+
+
+def adam_step(params, grads, m, v, step, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8):
+    """One Adam update (in place on copies); step counts from 1."""
+    out_p, out_m, out_v = [], [], []
+    for (W, b), (gW, gb), (mW, mb), (vW, vb) in zip(params, grads, m, v):
+        layer = []
+        for p, g, mm, vv in ((W, gW, mW, vW), (b, gb, mb, vb)):
+            mm = beta1 * mm + (1 - beta1) * g
+            vv = beta2 * vv + (1 - beta2) * g * g
+            mh = mm / (1 - beta1 ** step)
+            vh = vv / (1 - beta2 ** step)
+            layer.append((p - lr * mh / (np.sqrt(vh) + eps), mm, vv))
+        out_p.append((layer[0][0], layer[1][0]))
+        out_m.append((layer[0][1], layer[1][1]))
+        out_v.append((layer[0][2], layer[1][2]))
+    return out_p, out_m, out_v
+
+
+def bf16_round(a):
+    """Round FP64 values to the nearest bfloat16 (round half to even), returned as FP64."""
+    f = np.asarray(a, dtype=np.float32)
+    u = f.view(np.uint32).astype(np.uint64)
+    lsb = (u >> np.uint64(16)) & np.uint64(1)
+    u = (u + np.uint64(0x7FFF) + lsb) & np.uint64(0xFFFF0000)
+    return u.astype(np.uint32).view(np.float32).astype(np.float64)

@@ -1,0 +1,153 @@
+"""Pins of the oracle's TMCMC (Sec. 3.2, Algorithm 1) and of the surrogate MLP."""
+import math
+
+import numpy as np
+import pytest
+
+import synthetic
+from oracle import mlp
+from oracle import tmcmc as tm
+
+
+def _toy(mean, sd):
+    mean = np.asarray(mean)
+    sd = np.asarray(sd)
+
+    def loglik(th):
+        th = np.atleast_2d(th)
+        return -0.5 * np.sum(((th - mean) / sd) ** 2, axis=1)
+
+    return loglik
+
+
+def test_gaussian_toy_posterior():
+    # uniform prior on a wide box x Gaussian likelihood -> posterior N(mean, sd^2) (closed form)
+    mean = np.array([0.7, -1.2, 2.0])
+    sd = np.array([0.3, 0.5, 0.2])
+    lo, hi = np.full(3, -8.0), np.full(3, 8.0)
+    B = 2048
+    th0 = synthetic.prior_samples(11, lo, hi, B)
+    theta, ll, log = tm.run(th0, _toy(mean, sd), lo, hi, 11,
+                            randoms=lambda j: synthetic.stage_randoms(11, j, B, 3))
+    assert log.q[-1] == 1.0
+    assert len(log.q) > 3
+    m = theta.mean(0)
+    s = theta.std(0)
+    # Monte-Carlo standard error of the mean over seeds is ~0.1 sd for B = 2048 (correlated
+    # chains) and ~0.03 for the sd ratio: 3 standard errors each.  A wrong chain target
+    # (f_j instead of f_{j+1}) widens the posterior by ~sqrt(q_{j+1}/q_j) and fails.
+    assert np.all(np.abs(m - mean) < 0.3 * sd)
+    assert np.all(np.abs(s / sd - 1) < 0.1)
+
+
+def test_delayed_acceptance_keeps_target():
+    mean = np.array([0.3, 0.1])
+    sd = np.array([0.2, 0.4])
+    lo, hi = np.full(2, -5.0), np.full(2, 5.0)
+    B = 2048
+    exact = _toy(mean, sd)
+    surrogate = _toy(mean + 0.05, sd * 1.2)  # deliberately biased screen
+    th0 = synthetic.prior_samples(5, lo, hi, B)
+    theta, _, log = tm.run(th0, exact, lo, hi, 5, surrogate_fn=surrogate,
+                           randoms=lambda j: synthetic.stage_randoms(5, j, B, 2))
+    assert np.all(np.abs(theta.mean(0) - mean) < 0.3 * sd)
+    assert np.all(np.abs(theta.std(0) / sd - 1) < 0.12)
+
+
+def test_q_solve_hits_cov_target():
+    rng = np.random.default_rng(0)
+    ll = rng.normal(-500, 40, size=1000)
+    a = tm.analyze(rng.normal(size=(1000, 2)), ll, 0.0)
+    assert 0 < a["q_next"] < 1
+    assert abs(tm.cov_of_weights(ll, a["dq"]) - 1.0) < 1e-10
+    # weights normalised, covariance symmetric positive definite
+    assert abs(a["wbar"].sum() - 1) < 1e-14
+    assert np.all(np.linalg.eigvalsh(a["sigma"]) > 0)
+
+
+def test_q_reaches_one_when_weights_flat():
+    ll = np.full(64, -3.0) + 1e-6 * np.arange(64)
+    a = tm.analyze(np.zeros((64, 1)) + np.arange(64)[:, None], ll, 0.4)
+    assert a["q_next"] == 1.0
+
+
+def test_diverged_samples_have_zero_weight():
+    ll = np.array([-1.0, -np.inf, -2.0, -np.inf])
+    w, _ = tm._weights(ll, 0.5)
+    assert w[1] == 0 and w[3] == 0 and w[0] == 1.0
+
+
+def test_resample_against_brute_force():
+    rng = np.random.default_rng(4)
+    for B in (1, 3, 17, 64):
+        w = rng.uniform(0, 1, B) ** 3
+        w[rng.integers(0, B)] = 1.0
+        if B > 2:
+            w[0] = 0.0
+        u = synthetic.uniforms(9, synthetic.RESAMPLE, B, B)
+        idx = tm.resample(w, u)
+        W = np.floor(w * 2.0 ** 40).astype(np.int64)
+        tot = int(W.sum())
+        for k in range(B):
+            t = min(int(math.floor(u[k] * tot)), tot - 1)
+            acc = 0
+            for i in range(B):
+                acc += int(W[i])
+                if acc > t:
+                    break
+            assert idx[k] == i
+        if B > 2:
+            assert not np.any(idx == 0)  # zero weight never selected
+        uniq, n_c, off = tm.chains(idx, B)
+        assert n_c.sum() == B
+
+
+def test_mlp_gradients_finite_difference():
+    rng = np.random.default_rng(2)
+    params = mlp.init_params(rng, (5, 7, 6, 4))
+    x = rng.normal(size=(9, 5))
+    t = rng.normal(size=(9, 4))
+    grads = mlp.backward(params, x, t)
+    h = 1e-6
+    for li, (W, b) in enumerate(params):
+        for (i, j) in [(0, 0), (W.shape[0] - 1, W.shape[1] - 1), (1, 2)]:
+            Wp = [(a.copy(), c.copy()) for a, c in params]
+            Wm = [(a.copy(), c.copy()) for a, c in params]
+            Wp[li][0][i, j] += h
+            Wm[li][0][i, j] -= h
+            fd = (mlp.loss(Wp, x, t) - mlp.loss(Wm, x, t)) / (2 * h)
+            assert abs(fd - grads[li][0][i, j]) < 1e-7 * max(1.0, abs(fd))
+        Wp = [(a.copy(), c.copy()) for a, c in params]
+        Wm = [(a.copy(), c.copy()) for a, c in params]
+        Wp[li][1][0] += h
+        Wm[li][1][0] -= h
+        fd = (mlp.loss(Wp, x, t) - mlp.loss(Wm, x, t)) / (2 * h)
+        assert abs(fd - grads[li][1][0]) < 1e-7 * max(1.0, abs(fd))
+
+
+def test_gelu_derivative_and_values():
+    x = np.linspace(-4, 4, 33)
+    h = 1e-6
+    fd = (mlp.gelu(x + h) - mlp.gelu(x - h)) / (2 * h)
+    assert np.max(np.abs(fd - mlp.gelu_grad(x))) < 1e-8
+    # GELU(x) = x Phi(x): Phi(1) = 0.8413447460685429
+    assert abs(mlp.gelu(np.array([1.0]))[0] - 0.8413447460685429) < 1e-15
+
+
+def test_adam_step_textbook():
+    p = [(np.array([[1.0]]), np.array([0.5]))]
+    g = [(np.array([[0.2]]), np.array([-0.1]))]
+    z = [(np.zeros((1, 1)), np.zeros(1))]
+    p1, m1, v1 = mlp.adam_step(p, g, z, z, 1, lr=0.01)
+    # first step: m_hat = g, v_hat = g^2 -> update = lr * g/(|g| + eps)
+    assert abs(p1[0][0][0, 0] - (1.0 - 0.01 * 0.2 / (0.2 + 1e-8))) < 1e-15
+    assert abs(p1[0][1][0] - (0.5 + 0.01 * 0.1 / (0.1 + 1e-8))) < 1e-15
+
+
+def test_bf16_rounding():
+    v = np.array([1.0, 1.00390625, 1.005859375, -3.0e-3, 65504.0])
+    r = mlp.bf16_round(v)
+    assert r[0] == 1.0
+    assert r[1] == 1.0          # halfway, rounds to even
+    assert r[2] == 1.0078125    # above halfway rounds up
+    assert abs(r[3] / v[3] - 1) < 2 ** -8
