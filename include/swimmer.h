@@ -1,0 +1,198 @@
+/*
+ * swimmer.h -- C ABI of the GB300 (sm_103a) batched Brinkmanlet swimmer library.
+ *
+ * Method: Larson, Olson & Matzavinos, "Bayesian uncertainty quantification for
+ * micro-swimmers with fully resolved hydrodynamics" (arXiv 1910.12007).
+ *   - forward model g(theta|M): Sec. 2 (Eqs. eqnblob, BrV, Fenergy) and the Appendix
+ *     (Eqs. EFB, curva, EFT; forward Euler);
+ *   - Gaussian likelihood: Sec. 3.1, Eqs. (likelihood), (fitness);
+ *   - TMCMC: Sec. 3.2, Algorithm 1.
+ *
+ * Conventions for every entry point
+ *   - Return value: 0 on success, a negative SWIMMER_E* code otherwise.  Arguments are
+ *     validated on the host before anything is launched; on error nothing is launched
+ *     and no output is written.  swimmer_last_error() gives a message for the last
+ *     failure on the calling thread.
+ *   - Arrays are caller-owned DEVICE pointers unless stated otherwise ("host" below),
+ *     row-major, FP64 unless stated.  The library never frees caller memory.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).  Calls
+ *     are asynchronous on that stream unless stated otherwise.
+ *   - theta rows are (alpha, log10 K_C, a): Brinkman resistance, curvature stiffness,
+ *     beat amplitude.  All other physical parameters come from swimmer_config.
+ *   - Per-sample status codes: SWIMMER_OK, SWIMMER_DIVERGED (non-finite velocity, a
+ *     point moving more than ds in one step, or a segment stretched beyond 20 %),
+ *     SWIMMER_BAD_SAMPLE (parameters outside the supported range).  A sample that is not
+ *     OK has log-likelihood -inf and NaN outputs.
+ */
+#ifndef SWIMMER_H
+#define SWIMMER_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+    SWIMMER_OK = 0,
+    SWIMMER_DIVERGED = 1,
+    SWIMMER_BAD_SAMPLE = 2
+};
+
+enum {
+    SWIMMER_E_ARG = -1,      /* invalid argument (NULL pointer, size out of range) */
+    SWIMMER_E_CUDA = -2,     /* a CUDA runtime call failed */
+    SWIMMER_E_CAPACITY = -3, /* batch larger than the handle's capacity */
+    SWIMMER_E_STATE = -4     /* inconsistent TMCMC state (e.g. all samples diverged) */
+};
+
+enum { SWIMMER_FP64 = 0, SWIMMER_FP32C = 1 };
+
+/* Physical and numerical parameters (Table Tab:param fields).  POD, host memory. */
+typedef struct swimmer_config {
+    int n_max;              /* largest number of points per sample (3 .. 1024) */
+    int b_max;              /* largest batch this handle serves (1 .. 65536) */
+    double length;          /* flagellum length L when ds_fixed == 0 */
+    double ds_fixed;        /* > 0: per-sample length = (n - 1) * ds_fixed (uneven N) */
+    double mu;              /* viscosity */
+    double delta_over_ds;   /* blob width delta in units of ds */
+    double dt;              /* forward Euler step */
+    double k_t;             /* tension stiffness K_T */
+    double eta;             /* wavenumber */
+    double omega;           /* angular frequency */
+    long long steps;        /* time steps per forward run */
+    long long obs_every;    /* observation of the head point every obs_every steps */
+    int precision;          /* SWIMMER_FP64 or SWIMMER_FP32C */
+} swimmer_config;
+
+typedef struct swimmer_handle swimmer_handle;
+
+/* Create a handle on the current CUDA device: allocates the per-sample kernel tables,
+ * the work queues and the TMCMC workspace for b_max samples (device memory owned by the
+ * handle).  Synchronous.  *out receives the handle. */
+int swimmer_init(const swimmer_config *cfg, swimmer_handle **out);
+
+/* Free everything the handle owns.  Synchronizes the device first. */
+int swimmer_destroy(swimmer_handle *h);
+
+/* Message for the last error on the calling thread (static storage). */
+const char *swimmer_last_error(void);
+
+/* Kernel functions of the regularized Brinkmanlet (Sec. 2.1, Eq. BrV):
+ * g1(r) = B''(r) and g2(r) = (r B''(r) - B'(r))/r^3 for (Lap - alpha^2) B = G, Lap G =
+ * phi_delta (Eq. eqnblob), evaluated through the same per-sample table the forward
+ * kernels use.  r[m], g1[m], g2[m]: device arrays; precision selects the FP64 (Chebyshev
+ * degree 9) or the FP32 (cubic) table.  For testing the table build (step A1). */
+int swimmer_kernel_eval(swimmer_handle *h, double alpha, double delta, double r_max, int m,
+                        const double *r, double *g1, double *g2, int precision, void *stream);
+
+/* Batched forward model (Sec. 2; Appendix): for each sample b, B in 1..b_max,
+ *   theta[b*3 + 0..2]   (alpha, log10 K_C, a),
+ *   n_pts[b]            points (3..n_max) or n_pts == NULL for n_max everywhere,
+ * runs cfg.steps forward Euler steps from the straight filament X_k = (k ds, 0) and writes
+ *   head_traj[b][o][0..1]  head point (k = n-1) after every obs_every steps
+ *                          (n_obs = steps / obs_every rows; may be NULL),
+ *   mean_speed[b]          centroid x-displacement / (steps * dt)   (may be NULL),
+ *   status[b]              per-sample status code (required).
+ * One persistent launch for the whole batch (plus the table build). */
+int forward_batch(swimmer_handle *h, int B, const double *theta, const int *n_pts,
+                  double *head_traj, double *mean_speed, int *status, void *stream);
+
+/* Batched log-likelihood (Sec. 3.1, Eqs. likelihood/fitness with Sigma = sigma^2 I):
+ *   loglik[b] = -(m/2) ln(2 pi sigma^2) - sum_o |D_o - head_o(theta_b)|^2 / (2 sigma^2),
+ * m = 2 n_obs, obs = D [n_obs][2] on the device, shared by all samples.  The residuals
+ * are accumulated in FP64 inside the forward kernel; no trajectory is stored. */
+int loglik_batch(swimmer_handle *h, int B, const double *theta, const int *n_pts,
+                 const double *obs, double sigma, double *loglik, int *status, void *stream);
+
+/* ---------------------------------------------------------------------------------------
+ * TMCMC (Sec. 3.2, Algorithm 1) on the device.
+ * ------------------------------------------------------------------------------------- */
+typedef struct tmcmc_state {
+    int B;                 /* samples per stage (<= b_max) */
+    double *theta;         /* device [B][3] current samples (updated in place) */
+    double *loglik;        /* device [B] their log-likelihoods (updated in place) */
+    int *status;           /* device [B] */
+    const int *n_pts;      /* device [B] or NULL (n_max for all) */
+    const double *obs;     /* device [n_obs][2] observations D */
+    double sigma;          /* noise standard deviation */
+    double prior_lo[3];    /* host: box-uniform prior bounds */
+    double prior_hi[3];
+    double q;              /* host: annealing exponent q_j of the current samples */
+    int stage;             /* host: stage index j */
+    /* host outputs of the last stage */
+    double log_s;          /* log S_j (evidence factor) */
+    double mu[3];          /* weighted sample mean mu_j */
+    double sigma_prop[9];  /* scaled covariance b^2 Sigma_j (row-major) */
+    int unique;            /* number of distinct resampled samples (chains) */
+    int max_chain;         /* longest chain */
+    int n_exact;           /* forward-model evaluations this stage */
+    int n_screened;        /* surrogate evaluations this stage (delayed acceptance) */
+    int n_accept;          /* accepted proposals this stage */
+    double *surr_loglik;   /* device [B] surrogate log-likelihoods (delayed acceptance) */
+} tmcmc_state;
+
+/* One TMCMC stage: analyze (q_{j+1} by bisection on COV(w) = 1, w_bar, S_j, mu_j,
+ * Sigma_j = b^2 sum w_bar (theta - mu)(theta - mu)^T, b = 0.2), multinomial resample
+ * (64-bit fixed-point inverse CDF), and the Metropolis chains of length n_{j+1,k} with
+ * target f_{j+1} and Gaussian proposal N(theta, Sigma_j).
+ *   uniforms: device [3][B]: row 0 resampling, row 1 acceptance, row 2 second-step
+ *             acceptance (delayed acceptance only);
+ *   normals:  device [B][3] proposal normals (chain c, step s uses row off_c + s).
+ *   use_surrogate: 1 = delayed acceptance through the surrogate set with
+ *             swimmer_surrogate_set (requires st->surr_loglik), 0 = plain.
+ * Synchronizes `stream` once (the chain lengths decide the launches); updates st. */
+int tmcmc_stage(swimmer_handle *h, tmcmc_state *st, const double *uniforms, const double *normals,
+                int use_surrogate, void *stream);
+
+/* Stage pieces, exposed for testing (Algorithm 1 'Analyze' and 'Resample'):
+ * tmcmc_analyze: from loglik[B] (device), theta[B][3] (device) and q (host) compute on the
+ *   device: out_w[B] = exp(dq (l - l_max)) (0 for -inf), and stats[24] =
+ *   {dq, q_next, log_S, l_max, mu[3], Sigma[9], L[9] (Cholesky), ...} (device FP64).
+ * tmcmc_resample: idx[B] (device int) = min{i : C_i > floor(u_k C_B)}, C = inclusive
+ *   prefix of floor(w_i 2^40); also counts[B] (device int).  Integer results are exact. */
+int tmcmc_analyze(swimmer_handle *h, int B, const double *theta, const double *loglik, double q,
+                  double *out_w, double *stats, void *stream);
+int tmcmc_resample(swimmer_handle *h, int B, const double *w, const double *u, int *idx,
+                   int *counts, void *stream);
+
+/* ---------------------------------------------------------------------------------------
+ * Learned surrogate (not in the paper): MLP 5 -> 256 -> 256 -> 256 -> 80, GELU, BF16
+ * weights with FP32 accumulation; inputs are normalized (alpha, log10 K_C, a, log10 K_T,
+ * omega), outputs normalized head positions at 40 times.
+ * ------------------------------------------------------------------------------------- */
+#define SWIMMER_MLP_IN 5
+#define SWIMMER_MLP_HIDDEN 256
+#define SWIMMER_MLP_OUT 80
+#define SWIMMER_MLP_NPARAM (5 * 256 + 256 + 256 * 256 + 256 + 256 * 256 + 256 + 256 * 80 + 80)
+
+/* Forward pass: x[n][5] (device FP32) -> y[n][80] (device FP32), parameters w32 (device
+ * FP32 master copy, layout W1,b1,W2,b2,W3,b3,W4,b4 with W[out][in]); the kernel rounds
+ * weights to BF16 and accumulates in FP32. */
+int mlp_forward(int n, const float *params, const float *x, float *y, void *stream);
+
+/* Gradient of the mean squared error over the batch: grad[NPARAM] (device FP32, overwritten),
+ * loss_out[1] (device FP32). */
+int mlp_backward(int n, const float *params, const float *x, const float *t, float *grad,
+                 float *loss_out, void *stream);
+
+/* Adam update in place on params (FP32 master weights), moments m, v (device FP32). */
+int mlp_adam(float *params, const float *grad, float *m, float *v, int step, float lr, void *stream);
+
+/* Surrogate log-likelihood for delayed acceptance: attaches trained parameters and the
+ * normalization (host arrays: in_lo[5], in_hi[5] map inputs to [-1,1]; out_mean[80],
+ * out_std[80]) to the handle, plus the observation subsampling (obs_stride: surrogate
+ * output o corresponds to observation row o * obs_stride + obs_stride - 1).  The handle
+ * copies everything; params is a device pointer. */
+int swimmer_surrogate_set(swimmer_handle *h, const float *params, const double *in_lo,
+                          const double *in_hi, const double *out_mean, const double *out_std,
+                          int obs_stride, double log10_kt, double omega);
+
+/* Surrogate log-likelihood of B samples against obs/sigma (device arrays as in
+ * loglik_batch; uses the 40 subsampled observation rows and rescales J by the ratio of
+ * observation counts). */
+int surrogate_loglik_batch(swimmer_handle *h, int B, const double *theta, const double *obs,
+                           double sigma, double *loglik, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SWIMMER_H */

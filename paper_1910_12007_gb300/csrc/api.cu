@@ -1,0 +1,172 @@
+// C-ABI entry points: handle lifetime, argument validation, forward model and likelihood.
+#include <stdarg.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include "common.cuh"
+
+static thread_local char g_err[512] = "";
+
+void set_error(const char *fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+}
+
+extern "C" const char *swimmer_last_error(void) { return g_err; }
+
+static int check_config(const swimmer_config *c) {
+    ARG_CHECK(c != nullptr, "config is NULL");
+    ARG_CHECK(c->n_max >= 3 && c->n_max <= N_PTS_MAX, "n_max %d outside [3, %d]", c->n_max, N_PTS_MAX);
+    ARG_CHECK(c->b_max >= 1 && c->b_max <= 65536, "b_max %d outside [1, 65536]", c->b_max);
+    ARG_CHECK(c->ds_fixed > 0.0 || c->length > 0.0, "length must be > 0 (or ds_fixed > 0)");
+    ARG_CHECK(c->mu > 0.0, "mu must be > 0");
+    ARG_CHECK(c->delta_over_ds > 0.0, "delta_over_ds must be > 0");
+    ARG_CHECK(c->dt > 0.0, "dt must be > 0");
+    ARG_CHECK(c->k_t >= 0.0, "k_t must be >= 0");
+    ARG_CHECK(c->steps >= 1, "steps must be >= 1");
+    ARG_CHECK(c->obs_every >= 1, "obs_every must be >= 1");
+    ARG_CHECK(c->precision == SWIMMER_FP64 || c->precision == SWIMMER_FP32C, "precision must be 0 or 1");
+    return 0;
+}
+
+#define ALLOC(ptr, count)                                                       \
+    do {                                                                        \
+        cudaError_t _e = cudaMalloc((void **)&(ptr), sizeof(*(ptr)) * (size_t)(count)); \
+        if (_e != cudaSuccess) {                                                \
+            set_error("cudaMalloc of %s (%zu bytes) failed: %s", #ptr,           \
+                      sizeof(*(ptr)) * (size_t)(count), cudaGetErrorString(_e)); \
+            swimmer_destroy(h);                                                 \
+            return SWIMMER_E_CUDA;                                              \
+        }                                                                       \
+    } while (0)
+
+extern "C" int swimmer_init(const swimmer_config *cfg, swimmer_handle **out) {
+    int rc = check_config(cfg);
+    if (rc) return rc;
+    ARG_CHECK(out != nullptr, "out is NULL");
+    *out = nullptr;
+    swimmer_handle *h = (swimmer_handle *)calloc(1, sizeof(swimmer_handle));
+    ARG_CHECK(h != nullptr, "out of host memory");
+    h->cfg = *cfg;
+    CUDA_TRY(cudaGetDevice(&h->device));
+    CUDA_TRY(cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device));
+    const int B = cfg->b_max;
+    ALLOC(h->tab64, (size_t)B * TAB64_STRIDE);
+    ALLOC(h->tab32, (size_t)B * TAB32_STRIDE);
+    ALLOC(h->sp, B);
+    ALLOC(h->order, B);
+    ALLOC(h->queue, 4);
+    ALLOC(h->speed_tmp, B);
+    ALLOC(h->w, B);
+    ALLOC(h->stats, 64);
+    ALLOC(h->idx, B);
+    ALLOC(h->counts, B);
+    ALLOC(h->chain_id, B);
+    ALLOC(h->chain_off, B);
+    ALLOC(h->chain_len, B);
+    ALLOC(h->aux, B + 64);
+    ALLOC(h->cur_theta, 3 * B);
+    ALLOC(h->cur_ll, B);
+    ALLOC(h->cur_sl, B);
+    ALLOC(h->prop_theta, 3 * B);
+    ALLOC(h->prop_ll, B);
+    ALLOC(h->prop_sl, B);
+    ALLOC(h->out_theta, 3 * B);
+    ALLOC(h->out_ll, B);
+    ALLOC(h->out_sl, B);
+    ALLOC(h->prop_status, B);
+    ALLOC(h->active, B);
+    ALLOC(h->active2, B);
+    ALLOC(h->surr_norm, 2 * SWIMMER_MLP_OUT);
+    ALLOC(h->surr_params, SWIMMER_MLP_NPARAM);
+    ALLOC(h->surr_x, (size_t)B * SWIMMER_MLP_IN);
+    ALLOC(h->surr_y, (size_t)B * SWIMMER_MLP_OUT);
+    {
+        cudaError_t e1 = cudaMallocHost((void **)&h->host_pinned, 64 * sizeof(int));
+        cudaError_t e2 = cudaMallocHost((void **)&h->host_pinned_d, 64 * sizeof(double));
+        if (e1 != cudaSuccess || e2 != cudaSuccess) {
+            set_error("cudaMallocHost failed");
+            swimmer_destroy(h);
+            return SWIMMER_E_CUDA;
+        }
+    }
+    rc = gl_init();
+    if (rc) {
+        swimmer_destroy(h);
+        return rc;
+    }
+    CUDA_TRY(cudaDeviceSynchronize());
+    *out = h;
+    return 0;
+}
+
+extern "C" int swimmer_destroy(swimmer_handle *h) {
+    if (!h) return 0;
+    cudaDeviceSynchronize();
+    void *ptrs[] = {h->tab64, h->tab32, h->sp, h->order, h->queue, h->speed_tmp, h->w, h->stats,
+                    h->idx, h->counts, h->chain_id, h->chain_off, h->chain_len, h->aux,
+                    h->cur_theta, h->cur_ll, h->cur_sl, h->prop_theta, h->prop_ll, h->prop_sl,
+                    h->out_theta, h->out_ll, h->out_sl, h->prop_status, h->active, h->active2,
+                    h->surr_norm, h->surr_params, h->surr_x, h->surr_y};
+    for (void *p : ptrs)
+        if (p) cudaFree(p);
+    if (h->host_pinned) cudaFreeHost(h->host_pinned);
+    if (h->host_pinned_d) cudaFreeHost(h->host_pinned_d);
+    free(h);
+    return 0;
+}
+
+extern "C" int swimmer_kernel_eval(swimmer_handle *h, double alpha, double delta, double r_max, int m,
+                                   const double *r, double *g1, double *g2, int precision, void *stream) {
+    ARG_CHECK(h != nullptr, "handle is NULL");
+    ARG_CHECK(m >= 0, "m must be >= 0");
+    ARG_CHECK(m == 0 || (r && g1 && g2), "r, g1, g2 must be device pointers");
+    ARG_CHECK(alpha >= 0.0 && delta > 0.0 && r_max > 0.0, "need alpha >= 0, delta > 0, r_max > 0");
+    ARG_CHECK(r_max / delta < 4000.0, "r_max/delta beyond the table range");
+    ARG_CHECK(alpha * r_max <= X_MAX, "alpha * r_max beyond %g", X_MAX);
+    ARG_CHECK(precision == SWIMMER_FP64 || precision == SWIMMER_FP32C, "precision must be 0 or 1");
+    cudaStream_t s = (cudaStream_t)stream;
+    int rc = launch_set_sample(h, alpha, delta, r_max, s);
+    if (!rc) rc = launch_table_build(h, 1, 1, s);
+    if (!rc && m > 0) rc = launch_kernel_eval(h, m, r, g1, g2, precision, s);
+    return rc;
+}
+
+static int check_batch(swimmer_handle *h, int B, const double *theta, const int *status) {
+    ARG_CHECK(h != nullptr, "handle is NULL");
+    ARG_CHECK(B >= 1 && B <= h->cfg.b_max, "B = %d outside [1, b_max = %d]", B, h ? h->cfg.b_max : 0);
+    ARG_CHECK(theta != nullptr, "theta is NULL");
+    ARG_CHECK(status != nullptr, "status is NULL");
+    return 0;
+}
+
+int run_forward(swimmer_handle *h, int B, const double *theta, const int *n_pts, const double *obs,
+                double sigma, double *loglik, double *head_traj, double *mean_speed, int *status,
+                cudaStream_t s) {
+    int rc = launch_prepare(h, B, theta, n_pts, s);
+    if (!rc) rc = launch_table_build(h, B, h->cfg.precision == SWIMMER_FP64, s);
+    if (!rc) rc = launch_forward(h, B, obs, sigma, loglik, head_traj, mean_speed, status, h->cfg.precision, s);
+    return rc;
+}
+
+extern "C" int forward_batch(swimmer_handle *h, int B, const double *theta, const int *n_pts,
+                             double *head_traj, double *mean_speed, int *status, void *stream) {
+    int rc = check_batch(h, B, theta, status);
+    if (rc) return rc;
+    return run_forward(h, B, theta, n_pts, nullptr, 0.0, nullptr, head_traj, mean_speed, status,
+                       (cudaStream_t)stream);
+}
+
+extern "C" int loglik_batch(swimmer_handle *h, int B, const double *theta, const int *n_pts,
+                            const double *obs, double sigma, double *loglik, int *status, void *stream) {
+    int rc = check_batch(h, B, theta, status);
+    if (rc) return rc;
+    ARG_CHECK(obs != nullptr, "obs is NULL");
+    ARG_CHECK(loglik != nullptr, "loglik is NULL");
+    ARG_CHECK(sigma > 0.0, "sigma must be > 0");
+    ARG_CHECK(h->cfg.steps / h->cfg.obs_every >= 1, "no observation within steps");
+    return run_forward(h, B, theta, n_pts, obs, sigma, loglik, nullptr, nullptr, status, (cudaStream_t)stream);
+}

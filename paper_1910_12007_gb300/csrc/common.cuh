@@ -1,0 +1,98 @@
+// Shared definitions of the sm_103a swimmer library (handle, limits, error helpers).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "swimmer.h"
+
+// ---- table layout ------------------------------------------------------------------
+// Both tables cover u = 1 + r^2/delta^2 in [1, 2^n_oct): octave e = floor(log2 u), each
+// octave cut into equal panels.  The kernel functions are analytic in u except at u = 0,
+// so short panels far from 0 make low-degree polynomials accurate.
+constexpr int N_OCT_MAX = 24;          // u < 2^24 (r/delta < 4096)
+constexpr int F64_SUB_LOG2 = 3;        // 8 panels per octave
+constexpr int F64_SUB = 1 << F64_SUB_LOG2;
+constexpr int F64_DEG = 9;             // Chebyshev degree 9 per panel (10 nodes)
+constexpr int F64_NODES = F64_DEG + 1;
+constexpr int F32_SUB_LOG2 = 4;        // 16 panels per octave
+constexpr int F32_SUB = 1 << F32_SUB_LOG2;
+constexpr int F64_PANELS_MAX = N_OCT_MAX * F64_SUB;
+constexpr int F32_PANELS_MAX = N_OCT_MAX * F32_SUB;
+constexpr int NODES_MAX = F64_PANELS_MAX * F64_NODES;   // 1920
+// FP64 table per sample: [2][F64_PANELS_MAX][F64_NODES] Chebyshev coefficients
+constexpr int TAB64_STRIDE = 2 * F64_PANELS_MAX * F64_NODES;
+// FP32 table per sample: [2][F32_PANELS_MAX] float4 monomial cubic coefficients in f
+constexpr int TAB32_STRIDE = 2 * F32_PANELS_MAX;
+constexpr double R_MAX_OVER_L = 1.25;  // table reach in units of the flagellum length
+constexpr double STRETCH_MAX = 0.20;   // segment stretch beyond which a run counts as diverged
+constexpr int N_PTS_MAX = 1024;
+constexpr int P_THETA = 3;
+constexpr double X_MAX = 600.0;        // largest alpha * r the Bessel evaluations accept
+
+// per-sample derived parameters written by the table builder and read by the forward kernel
+struct SampleParams {
+    double alpha, kc, amp, length, ds, delta;
+    int n, n_oct, status, pad;
+};
+
+struct swimmer_handle {
+    swimmer_config cfg;
+    int device;
+    int num_sms;
+    // per-sample workspace (b_max samples)
+    double *tab64;          // [b_max][TAB64_STRIDE]
+    float4 *tab32;          // [b_max][TAB32_STRIDE]
+    SampleParams *sp;       // [b_max]
+    int *order;             // [b_max] processing order (longest first)
+    int *queue;             // [4] work counters
+    double *speed_tmp;      // [b_max]
+    // TMCMC workspace
+    double *w;              // [b_max]
+    double *stats;          // [64]
+    int *idx, *counts, *chain_id, *chain_off, *chain_len, *aux;  // [b_max] each, aux [b_max+64]
+    double *cur_theta, *cur_ll, *cur_sl, *prop_theta, *prop_ll, *prop_sl, *out_theta, *out_ll, *out_sl;
+    int *prop_status, *active, *active2;
+    int *host_pinned;       // pinned host scratch (64 ints)
+    double *host_pinned_d;  // pinned host scratch (64 doubles)
+    // surrogate
+    float *surr_params;     // device copy of the trained parameters (NPARAM)
+    double surr_in_lo[5], surr_in_hi[5];
+    double *surr_norm;      // device [2][80] out_mean, out_std
+    int surr_obs_stride;
+    double surr_log10_kt, surr_omega;
+    int surr_ready;
+    float *surr_x, *surr_y; // [b_max][5], [b_max][80]
+};
+
+// ---- error reporting -----------------------------------------------------------------
+void set_error(const char *fmt, ...);
+
+#define CUDA_TRY(expr)                                                               \
+    do {                                                                             \
+        cudaError_t _e = (expr);                                                     \
+        if (_e != cudaSuccess) {                                                     \
+            set_error("%s failed: %s (%s:%d)", #expr, cudaGetErrorString(_e), __FILE__, \
+                      __LINE__);                                                     \
+            return SWIMMER_E_CUDA;                                                   \
+        }                                                                            \
+    } while (0)
+
+#define ARG_CHECK(cond, ...)                                                         \
+    do {                                                                             \
+        if (!(cond)) {                                                               \
+            set_error(__VA_ARGS__);                                                  \
+            return SWIMMER_E_ARG;                                                    \
+        }                                                                            \
+    } while (0)
+
+// ---- launchers implemented in the kernel translation units ----------------------------
+int launch_prepare(swimmer_handle *h, int B, const double *theta, const int *n_pts, cudaStream_t s);
+int launch_table_build(swimmer_handle *h, int B, int need64, cudaStream_t s);
+int launch_forward(swimmer_handle *h, int B, const double *obs, double sigma, double *loglik,
+                   double *head_traj, double *mean_speed, int *status, int precision,
+                   cudaStream_t s);
+int launch_kernel_eval(swimmer_handle *h, int m, const double *r, double *g1, double *g2,
+                       int precision, cudaStream_t s);
+int gl_init();
+int launch_set_sample(swimmer_handle *h, double alpha, double delta, double r_max, cudaStream_t s);

@@ -1,0 +1,441 @@
+// K2: fused persistent forward model + log-likelihood, one CTA per sample at a time.
+//
+// Per time step (Appendix, last paragraph; Sec. 2.1):
+//   A  segment vectors e_k = X_{k+1} - X_k (FP64 differences) and spring tension
+//      2 K_T (|e_k|/ds - 1)/|e_k| (Eq. EFT read as Hookean springs), with the strain taken
+//      from |e|^2/ds^2 - 1 in FP64 so that no cancellation reaches FP32;
+//   B  nonlinear curvature zeta_k (Eq. curva) from central differences, preferred
+//      curvature zeta^_k(t), and c_k d zeta_k / d X_{k-1,k,k+1} with c_k = 2 K_C ds (zeta - zeta^)
+//      (gradient of Eq. EFB);
+//   C  point forces F = -dE/dX (Eq. Fenergy) gathered from the stencils;
+//   D  Brinkmanlet pair sum (Eq. BrV) v_i = (1/mu) sum_j [-F_j g1 + (F_j . d) d g2]:
+//      sources (x, y, Fx, Fy) as one float4 / double4 per point in shared memory, the
+//      S threads of a target split the sources and combine with warp shuffles; g1, g2
+//      from the per-sample shared-memory table (cubic in FP32, Chebyshev degree 9 in FP64);
+//      FP32 partial sums of 32 sources are folded into a (hi, lo) pair by TwoSum
+//      (compensated accumulation);
+//   E  forward Euler X += dt v in FP64; every obs_every steps the head point is compared
+//      with the observations and the squared residual accumulated in FP64 (Eq. fitness).
+// A run stops early, with status DIVERGED, when a velocity is not finite, a point moves
+// more than ds in one step, or a segment stretches beyond STRETCH_MAX.
+#include <math.h>
+
+#include "common.cuh"
+
+namespace {
+
+constexpr double PI = 3.14159265358979323846;
+constexpr int CHUNK = 32;  // sources per compensated partial sum
+
+struct FwdArgs {
+    int B;
+    const SampleParams *sp;
+    const int *order;
+    int *queue;
+    const double *tab64;
+    const float4 *tab32;
+    double mu, dt, kt, eta, omega;
+    long long steps, obs_every;
+    const double *obs;
+    double sigma;
+    double *loglik;
+    double *head_traj;
+    double *speed;
+    int *status;
+    int n_max;
+    int threads;
+};
+
+struct __align__(32) dbl4 {
+    double x, y, z, w;
+};
+
+template <bool F64>
+struct Types;
+template <>
+struct Types<false> {
+    typedef float R;
+    typedef float4 R4;
+};
+template <>
+struct Types<true> {
+    typedef double R;
+    typedef dbl4 R4;
+};
+
+__device__ __forceinline__ void two_sum(float &s, float &e, float b) {
+    float t = s + b;
+    float bp = t - s;
+    e += (s - (t - bp)) + (b - bp);
+    s = t;
+}
+
+template <bool F64>
+__host__ __device__ size_t smem_bytes(int n_max) {
+    typedef typename Types<F64>::R R;
+    typedef typename Types<F64>::R4 R4;
+    size_t b = 2 * sizeof(double) * n_max + sizeof(R4) * n_max + 9 * sizeof(R) * n_max;
+    b = (b + 15) & ~size_t(15);
+    return b + (F64 ? sizeof(double) * TAB64_STRIDE : sizeof(float4) * TAB32_STRIDE);
+}
+
+__device__ __forceinline__ void kern_f32(const float4 *__restrict__ t1, const float4 *__restrict__ t2, int pmax,
+                                         float u, float &g1, float &g2) {
+    unsigned bits = __float_as_uint(u);
+    unsigned p = (bits >> (23 - F32_SUB_LOG2)) - (127u << F32_SUB_LOG2);
+    p = min(p, (unsigned)pmax);
+    float f = __uint_as_float(0x3f800000u | ((bits << F32_SUB_LOG2) & 0x7fffffu)) - 1.0f;
+    float4 a = t1[p];
+    float4 c = t2[p];
+    g1 = fmaf(f, fmaf(f, fmaf(f, a.w, a.z), a.y), a.x);
+    g2 = fmaf(f, fmaf(f, fmaf(f, c.w, c.z), c.y), c.x);
+}
+
+__device__ __forceinline__ void kern_f64(const double *__restrict__ tab, int pmax, double u, double &g1, double &g2) {
+    unsigned long long bits = (unsigned long long)__double_as_longlong(u);
+    unsigned long long p = (bits >> (52 - F64_SUB_LOG2)) - (1023ull << F64_SUB_LOG2);
+    if (p > (unsigned long long)pmax) p = pmax;
+    double f = __longlong_as_double(0x3ff0000000000000LL | (long long)((bits << F64_SUB_LOG2) & 0x000fffffffffffffull)) - 1.0;
+    double t = 2.0 * f - 1.0, t2 = 2.0 * t;
+    const double *c1 = tab + p * F64_NODES;
+    const double *c2 = tab + (F64_PANELS_MAX + p) * F64_NODES;
+    double a1 = 0.0, a2 = 0.0, b1 = 0.0, b2 = 0.0;
+#pragma unroll
+    for (int k = F64_DEG; k >= 1; --k) {
+        double a0 = fma(t2, a1, c1[k] - a2);
+        a2 = a1;
+        a1 = a0;
+        double b0 = fma(t2, b1, c2[k] - b2);
+        b2 = b1;
+        b1 = b0;
+    }
+    g1 = fma(t, a1, c1[0] - a2);
+    g2 = fma(t, b1, c2[0] - b2);
+}
+
+template <bool F64>
+__global__ void __launch_bounds__(1024) forward_kernel(FwdArgs a) {
+    typedef typename Types<F64>::R R;
+    typedef typename Types<F64>::R4 R4;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    const int n_max = a.n_max;
+    double *sx = (double *)smraw;
+    double *sy = sx + n_max;
+    R4 *src = (R4 *)(sy + n_max);
+    R *segx = (R *)(src + n_max);
+    R *segy = segx + n_max;
+    R *tens = segy + n_max;
+    R *bend = tens + n_max;  // [6][n_max]
+    size_t off = (2 * sizeof(double) * n_max + sizeof(R4) * n_max + 9 * sizeof(R) * n_max + 15) & ~size_t(15);
+    unsigned char *tabraw = smraw + off;
+    __shared__ int s_work;
+    __shared__ double s_red[32];
+
+    const int tid = threadIdx.x, T = blockDim.x;
+    const int lane = tid & 31;
+
+    for (;;) {
+        if (tid == 0) s_work = atomicAdd(a.queue, 1);
+        __syncthreads();
+        const int w = s_work;
+        if (w >= a.B) break;
+        const int b = a.order[w];
+        const SampleParams p = a.sp[b];
+        const int n = p.n;
+        const long long n_obs = a.steps / a.obs_every;
+        if (p.status != SWIMMER_OK) {
+            if (tid == 0) {
+                a.status[b] = p.status;
+                if (a.loglik) a.loglik[b] = -INFINITY;
+                if (a.speed) a.speed[b] = nan("");
+            }
+            if (a.head_traj)
+                for (long long o = tid; o < 2 * n_obs; o += T) a.head_traj[(size_t)b * 2 * n_obs + o] = nan("");
+            __syncthreads();
+            continue;
+        }
+        // ---- table into shared memory
+        const int npan = p.n_oct * (F64 ? F64_SUB : F32_SUB);
+        if (F64) {
+            const double *g = a.tab64 + (size_t)b * TAB64_STRIDE;
+            double *t = (double *)tabraw;
+            for (int i = tid; i < npan * F64_NODES; i += T) {
+                t[i] = g[i];
+                t[F64_PANELS_MAX * F64_NODES + i] = g[F64_PANELS_MAX * F64_NODES + i];
+            }
+        } else {
+            const float4 *g = a.tab32 + (size_t)b * TAB32_STRIDE;
+            float4 *t = (float4 *)tabraw;
+            for (int i = tid; i < npan; i += T) {
+                t[i] = g[i];
+                t[F32_PANELS_MAX + i] = g[F32_PANELS_MAX + i];
+            }
+        }
+        // ---- initial straight filament X_k = (k ds, 0)
+        const double ds = p.ds, L = p.length;
+        for (int k = tid; k < n; k += T) {
+            sx[k] = k * ds;
+            sy[k] = 0.0;
+        }
+        const double xref = 0.5 * L;
+        const double inv_ds2 = 1.0 / (ds * ds);
+        const R r_ds = (R)ds, r_inv2ds = (R)(0.5 / ds), r_invds2 = (R)inv_ds2;
+        const R kt2 = (R)(2.0 * a.kt), kc2ds = (R)(2.0 * p.kc * ds);
+        const R r_amp = (R)p.amp, r_eta = (R)a.eta, r_omega = (R)a.omega, r_L = (R)L;
+        const R inv_d2 = (R)(1.0 / (p.delta * p.delta));
+        const double dt_mu = a.dt / a.mu;
+        // thread -> (target slot, source split)
+        int S = 1;
+        while (S < 32 && 2 * S * n <= T) S <<= 1;
+        const int slot = tid / S, split = tid % S;
+        const int tgt = slot;  // one target per slot
+        const bool owner = (split == 0) && (tgt < n);
+        double J = 0.0;
+        int status = SWIMMER_OK;
+        long long steps_done = a.steps;
+        __syncthreads();
+
+        for (long long step = 0; step < a.steps; ++step) {
+            const R tR = (R)(step * a.dt);
+            int bad = 0;
+            // ---- A: segments, tension, relative positions
+            for (int k = tid; k < n; k += T) {
+                if (k + 1 < n) {
+                    double ex = sx[k + 1] - sx[k], ey = sy[k + 1] - sy[k];
+                    double s2 = fma(fma(ex, ex, ey * ey), inv_ds2, -1.0);  // l^2/ds^2 - 1
+                    R s2r = (R)s2;
+                    R strain = s2r / ((R)1 + sqrt((R)1 + s2r));
+                    R ell = r_ds * ((R)1 + strain);
+                    segx[k] = (R)ex;
+                    segy[k] = (R)ey;
+                    tens[k] = kt2 * strain / ell;
+                    if (!(fabs((double)strain) <= STRETCH_MAX)) bad = 1;
+                }
+                R4 q;
+                q.x = (R)(sx[k] - xref);
+                q.y = (R)sy[k];
+                src[k] = q;
+            }
+            __syncthreads();
+            // ---- B: curvature stencils
+            for (int k = tid; k < n; k += T) {
+                if (k >= 1 && k + 1 < n) {
+                    R emx = segx[k - 1], emy = segy[k - 1], epx = segx[k], epy = segy[k];
+                    R A = (emx + epx) * r_inv2ds, Bv = (emy + epy) * r_inv2ds;
+                    R C = (epx - emx) * r_invds2, D = (epy - emy) * r_invds2;
+                    R S2 = A * A + Bv * Bv;
+                    R rs = (R)1 / sqrt(S2);
+                    R S15 = rs * rs * rs;
+                    R S25 = S15 / S2;
+                    R cross = A * D - Bv * C;
+                    R zeta = cross * S15;
+                    R s = (R)k * r_ds;
+                    R ph = r_eta * s - r_omega * tR;
+                    R sn, cs;
+                    if (F64) {
+                        double sd, cd;
+                        sincos((double)ph, &sd, &cd);
+                        sn = (R)sd;
+                        cs = (R)cd;
+                    } else {
+                        float sf, cf;
+                        sincosf((float)ph, &sf, &cf);
+                        sn = (R)sf;
+                        cs = (R)cf;
+                    }
+                    R zhat = -r_amp * ((R)2 * r_eta / r_L * cs + ((R)1 - s / r_L) * r_eta * r_eta * sn);
+                    R ck = kc2ds * (zeta - zhat);
+                    R za = D * S15 - (R)3 * A * cross * S25;
+                    R zb = -C * S15 - (R)3 * Bv * cross * S25;
+                    R zc = -Bv * S15, zd = A * S15;
+                    bend[0 * n_max + k] = ck * (-za * r_inv2ds + zc * r_invds2);
+                    bend[1 * n_max + k] = ck * (-zb * r_inv2ds + zd * r_invds2);
+                    bend[2 * n_max + k] = ck * ((R)-2 * zc * r_invds2);
+                    bend[3 * n_max + k] = ck * ((R)-2 * zd * r_invds2);
+                    bend[4 * n_max + k] = ck * (za * r_inv2ds + zc * r_invds2);
+                    bend[5 * n_max + k] = ck * (zb * r_inv2ds + zd * r_invds2);
+                }
+            }
+            __syncthreads();
+            // ---- C: point forces
+            for (int k = tid; k < n; k += T) {
+                R fx = 0, fy = 0;
+                if (k + 1 < n) {
+                    fx += tens[k] * segx[k];
+                    fy += tens[k] * segy[k];
+                }
+                if (k >= 1) {
+                    fx -= tens[k - 1] * segx[k - 1];
+                    fy -= tens[k - 1] * segy[k - 1];
+                }
+                if (k >= 2) {
+                    fx -= bend[4 * n_max + k - 1];
+                    fy -= bend[5 * n_max + k - 1];
+                }
+                if (k >= 1 && k + 1 < n) {
+                    fx -= bend[2 * n_max + k];
+                    fy -= bend[3 * n_max + k];
+                }
+                if (k + 2 < n) {
+                    fx -= bend[0 * n_max + k + 1];
+                    fy -= bend[1 * n_max + k + 1];
+                }
+                src[k].z = fx;
+                src[k].w = fy;
+            }
+            __syncthreads();
+            // ---- D: pair sum
+            double vxd = 0.0, vyd = 0.0;
+            if (tgt < n) {
+                const R4 me = src[tgt];
+                const R xi = me.x, yi = me.y;
+                if (F64) {
+                    const double *tab = (const double *)tabraw;
+                    double vx = 0.0, vy = 0.0;
+                    for (int j = split; j < n; j += S) {
+                        R4 q = src[j];
+                        double dx = (double)xi - (double)q.x, dy = (double)yi - (double)q.y;
+                        double u = fma(fma(dx, dx, dy * dy), (double)inv_d2, 1.0);
+                        double g1, g2;
+                        kern_f64(tab, npan - 1, u, g1, g2);
+                        double fd = fma((double)q.z, dx, (double)q.w * dy);
+                        double wv = fd * g2;
+                        vx = fma(wv, dx, fma(-(double)q.z, g1, vx));
+                        vy = fma(wv, dy, fma(-(double)q.w, g1, vy));
+                    }
+                    vxd = vx;
+                    vyd = vy;
+                } else {
+                    const float4 *t1 = (const float4 *)tabraw;
+                    const float4 *t2 = t1 + F32_PANELS_MAX;
+                    const float4 *s4 = (const float4 *)src;
+                    const float fxi = (float)xi, fyi = (float)yi, fid2 = (float)inv_d2;
+                    float hx = 0.f, lx = 0.f, hy = 0.f, ly = 0.f;
+                    for (int j0 = split; j0 < n; j0 += S * CHUNK) {
+                        float px = 0.f, py = 0.f;
+                        const int jend = min(n, j0 + S * CHUNK);
+#pragma unroll 4
+                        for (int j = j0; j < jend; j += S) {
+                            float4 q = s4[j];
+                            float dx = fxi - q.x, dy = fyi - q.y;
+                            float u = fmaf(fmaf(dx, dx, dy * dy), fid2, 1.0f);
+                            float g1, g2;
+                            kern_f32(t1, t2, npan - 1, u, g1, g2);
+                            float fd = fmaf(q.z, dx, q.w * dy);
+                            float wv = fd * g2;
+                            px = fmaf(wv, dx, fmaf(-q.z, g1, px));
+                            py = fmaf(wv, dy, fmaf(-q.w, g1, py));
+                        }
+                        two_sum(hx, lx, px);
+                        two_sum(hy, ly, py);
+                    }
+                    vxd = (double)hx + (double)lx;
+                    vyd = (double)hy + (double)ly;
+                }
+            }
+            // combine the S source splits (lanes of one warp)
+            for (int o = S >> 1; o >= 1; o >>= 1) {
+                vxd += __shfl_xor_sync(0xffffffffu, vxd, o);
+                vyd += __shfl_xor_sync(0xffffffffu, vyd, o);
+            }
+            // ---- E: Euler step (FP64), divergence, observations
+            if (owner) {
+                double vx = vxd * dt_mu, vy = vyd * dt_mu;  // displacement this step
+                if (!isfinite(vx) || !isfinite(vy) || fmax(fabs(vx), fabs(vy)) > ds) bad = 1;
+                sx[tgt] += vx;
+                sy[tgt] += vy;
+                if (tgt == n - 1 && (step + 1) % a.obs_every == 0) {
+                    long long o = (step + 1) / a.obs_every - 1;
+                    if (a.obs) {
+                        double rx = a.obs[2 * o] - sx[tgt], ry = a.obs[2 * o + 1] - sy[tgt];
+                        J = fma(rx, rx, fma(ry, ry, J));
+                    }
+                    if (a.head_traj) {
+                        a.head_traj[((size_t)b * n_obs + o) * 2] = sx[tgt];
+                        a.head_traj[((size_t)b * n_obs + o) * 2 + 1] = sy[tgt];
+                    }
+                }
+            }
+            if (__syncthreads_or(bad)) {
+                status = SWIMMER_DIVERGED;
+                steps_done = step + 1;
+                break;
+            }
+        }
+        // ---- outputs
+        if (a.speed) {
+            double cx = 0.0;
+            for (int k = tid; k < n; k += T) cx += sx[k];
+            for (int o = 16; o >= 1; o >>= 1) cx += __shfl_xor_sync(0xffffffffu, cx, o);
+            if (lane == 0) s_red[tid >> 5] = cx;
+            __syncthreads();
+            if (tid == 0) {
+                double tot = 0.0;
+                for (int i = 0; i < (T + 31) / 32; ++i) tot += s_red[i];
+                a.speed[b] = status == SWIMMER_OK ? (tot / n - 0.5 * L) / (a.steps * a.dt) : nan("");
+            }
+        }
+        if (owner && tgt == n - 1) {
+            a.status[b] = status;
+            if (a.loglik) {
+                double s2 = a.sigma * a.sigma;
+                a.loglik[b] = status == SWIMMER_OK ? -(double)n_obs * log(2.0 * PI * s2) - 0.5 * J / s2 : -INFINITY;
+            }
+            if (status != SWIMMER_OK && a.head_traj) {
+                // observations after the divergence were never taken
+                for (long long o = steps_done / a.obs_every; o < n_obs; ++o) {
+                    a.head_traj[((size_t)b * n_obs + o) * 2] = nan("");
+                    a.head_traj[((size_t)b * n_obs + o) * 2 + 1] = nan("");
+                }
+            }
+        }
+        __syncthreads();
+    }
+}
+
+}  // namespace
+
+int launch_forward(swimmer_handle *h, int B, const double *obs, double sigma, double *loglik,
+                   double *head_traj, double *mean_speed, int *status, int precision, cudaStream_t s) {
+    FwdArgs a;
+    a.B = B;
+    a.sp = h->sp;
+    a.order = h->order;
+    a.queue = h->queue;
+    a.tab64 = h->tab64;
+    a.tab32 = h->tab32;
+    a.mu = h->cfg.mu;
+    a.dt = h->cfg.dt;
+    a.kt = h->cfg.k_t;
+    a.eta = h->cfg.eta;
+    a.omega = h->cfg.omega;
+    a.steps = h->cfg.steps;
+    a.obs_every = h->cfg.obs_every;
+    a.obs = obs;
+    a.sigma = sigma;
+    a.loglik = loglik;
+    a.head_traj = head_traj;
+    a.speed = mean_speed;
+    a.status = status;
+    a.n_max = h->cfg.n_max;
+    int T = 32;
+    while (T < h->cfg.n_max && T < 1024) T <<= 1;
+    if (T < 128) T = 128;
+    a.threads = T;
+    const bool f64 = precision == SWIMMER_FP64;
+    size_t smem = f64 ? smem_bytes<true>(a.n_max) : smem_bytes<false>(a.n_max);
+    auto kern = f64 ? forward_kernel<true> : forward_kernel<false>;
+    CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int per_sm = 0;
+    CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, T, smem));
+    if (per_sm < 1) {
+        set_error("forward kernel does not fit on an SM (threads %d, smem %zu)", T, smem);
+        return SWIMMER_E_CUDA;
+    }
+    int grid = per_sm * h->num_sms;
+    if (grid > B) grid = B;
+    CUDA_TRY(cudaMemsetAsync(h->queue, 0, sizeof(int), s));
+    kern<<<grid, T, smem, s>>>(a);
+    CUDA_TRY(cudaGetLastError());
+    return 0;
+}
