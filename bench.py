@@ -1,0 +1,376 @@
+#!/usr/bin/env python
+"""Benchmark of the batched Brinkmanlet forward model inside transitional MCMC on GB300.
+
+Workload (one "step" = one TMCMC stage of Algorithm 1 over a batch of synthetic input):
+  1024 samples per stage, N = 128 points, theta = (alpha ~ U[0,10], log10 K_C ~ U[-1,1],
+  a ~ U[0.05,0.2]), observations = head (x, y) every 100 Euler steps, 2e4 steps per forward
+  run, synthetic data from theta* = (1, 0, 0.1) plus 5 % Gaussian noise.  Forward Euler is
+  stable only for dt below 2/lambda_max (lambda_max ~ K_C / ds^3 for the 3-point curvature
+  stencil); dt = 1e-4/64 keeps dt * lambda_max <= 1 at the true K_C, so the 2e4 steps span
+  2e4 * dt time units.  A stage whose annealing exponent reaches 1 is followed by a fresh
+  prior draw and its log-likelihood (Algorithm 1 "Generate"), counted in the next step.
+
+Metric: Brinkmanlet pair evaluations per second executed by the forward kernel over the
+timed stages (one pair-eval = one (target, source) term, self term included), summed over
+ranks, plus TMCMC samples per second.  `--impl reference` times the FP64 CPU oracle on
+the host cores on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Brinkmanlet pair-evals/s & TMCMC samples/s, surrogate vs plain at fixed error"
+N_PTS, B_STAGE, STEPS, OBS_EVERY = 128, 1024, 20000, 100
+DT = 1e-4 / 64
+THETA_TRUE = (1.0, 0.0, 0.1)
+PRIOR_LO = (0.0, -1.0, 0.05)
+PRIOR_HI = (10.0, 1.0, 0.2)
+NOISE = 0.05
+FLOPS_PER_PAIR = 32  # FP32 operations of one table-based pair term
+
+
+def workload_config(precision_name):
+    return {
+        "workload": "TMCMC stage: 1024 samples, N=128 flagellum points, 3 unknowns, head x,y every "
+                    "100 steps, 2e4 Euler steps per forward run (dt=1e-4/64), 5% noise",
+        "samples_per_stage": B_STAGE, "n_points": N_PTS, "steps_per_run": STEPS, "dt": DT,
+        "obs_every": OBS_EVERY, "precision": precision_name,
+        "l2": "256 MiB buffer written between timed steps (inputs are < L2)",
+    }
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sms, maxes, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sms.append(float(parts[1]))
+                maxes.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        if not sms:
+            return None
+        return {"sm_mhz": statistics.median(sms), "sm_max_mhz": max(maxes), "reasons": sorted(reasons),
+                "samples": len(sms)}
+
+
+def kernel_traffic():
+    """DRAM bytes per forward-kernel launch from the committed ncu summary, if it was
+    captured on the current kernel source (else None)."""
+    src = os.path.join(ROOT, "paper_1910_12007_gb300", "csrc", "forward.cu")
+    path = os.path.join(ROOT, "profiles", "forward_kernel_traffic.json")
+    try:
+        with open(src, "rb") as f:
+            digest = hashlib.sha256(f.read()).hexdigest()
+        with open(path) as f:
+            rec = json.load(f)
+        if rec.get("forward_cu_sha256") != digest:
+            return None
+        return rec["dram_bytes_per_pair_eval"]
+    except Exception:
+        return None
+
+
+# -------------------------------------------------------------------------------------
+# oracle (CPU) legs
+# -------------------------------------------------------------------------------------
+def oracle_sample(samples=16, steps=10000, threads=None):
+    """Time the FP64 C oracle on `samples` forward runs of the workload's swimmer."""
+    import numpy as np
+
+    import synthetic
+    from oracle import swimmer as sw
+
+    threads = threads or os.cpu_count() or 1
+    base = sw.SwimmerParams(n=N_PTS, dt=DT, steps=steps, obs_every=OBS_EVERY)
+    thetas = synthetic.prior_samples(99, PRIOR_LO, PRIOR_HI, samples)
+    thetas[:, 1] = np.minimum(thetas[:, 1], 0.2)  # stay in the stable K_C range
+    ps = [base.with_theta(t) for t in thetas]
+    t0 = time.perf_counter()
+    tables = [sw.kernel_table(p) for p in ps]
+    t1 = time.perf_counter()
+    sw.run_c_batch(ps, tables, threads=threads)
+    t2 = time.perf_counter()
+    pairs = samples * N_PTS * N_PTS * steps
+    return {"pairs": pairs, "seconds": t2 - t0, "table_seconds": t1 - t0, "cores": threads,
+            "sample": f"{samples} forward runs x {steps} Euler steps of the N=128 workload swimmer "
+                      f"(FP64 C oracle, OpenMP over samples, kernel tables included)"}
+
+
+def reference_arm(args, rank):
+    if rank != 0:
+        return 0
+    W, K = args.warmup, args.steps
+    times, pairs = [], 0
+    r = None
+    for i in range(W + K):
+        r = oracle_sample(samples=8, steps=1000)
+        if i >= W:
+            times.append(r["seconds"])
+            pairs += r["pairs"]
+    tot = sum(times)
+    value = pairs / tot
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "pair-evals/s", "n_gpus": args.gpus,
+        "steps": K, "warmup": W, "ms_per_step": 1e3 * tot / K, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": workload_config("fp64-oracle"),
+        "cpu_baseline": {"value": value, "unit": "pair-evals/s", "cores": r["cores"], "kind": "oracle",
+                         "sample": "per step: " + r["sample"]},
+        "e2e": {"value": value, "unit": "pair-evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# -------------------------------------------------------------------------------------
+# GPU leg
+# -------------------------------------------------------------------------------------
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="fp32c", choices=["fp32c", "fp64"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return reference_arm(args, rank)
+
+    import numpy as np
+    import torch
+
+    import paper_1910_12007_gb300 as g
+    import synthetic
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=dev)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    prec = g.FP64 if args.precision == "fp64" else g.FP32C
+    cfg = g.SwimmerConfig(n_max=N_PTS, b_max=B_STAGE, length=1.0, dt=DT, steps=STEPS, obs_every=OBS_EVERY,
+                          precision=prec)
+    h = g.swimmer_init(cfg)
+    seed0 = 1000 + 97 * rank
+
+    # synthetic observations: forward model at theta*, plus 5 % noise (untimed set-up)
+    th_true = torch.tensor([THETA_TRUE], dtype=torch.float64, device=dev)
+    traj, _, st_true = g.forward_batch(h, th_true)
+    xi = traj[0].cpu().numpy()
+    sigma = NOISE * float(np.mean(np.abs(xi)))
+    D = xi + sigma * synthetic.normals(1234, synthetic.NOISE, 0, xi.size).reshape(xi.shape)
+    obs = torch.tensor(D, dtype=torch.float64, device=dev)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MiB
+
+    class Job:
+        """Algorithm 1 over and over: stage after stage, a fresh prior draw after q = 1."""
+
+        def __init__(self):
+            self.seed = seed0
+            self.stage = 0
+            self.state = None
+            self.stages_done = 0
+
+        def generate(self):
+            th0 = torch.tensor(synthetic.prior_samples(self.seed, PRIOR_LO, PRIOR_HI, B_STAGE), device=dev)
+            ll, _ = g.loglik_batch(h, th0, obs, sigma)
+            self.state = g.TmcmcState(th0, ll, obs, sigma, PRIOR_LO, PRIOR_HI)
+            self.stage = 0
+
+        def randoms(self):
+            u_res, u_acc, z = synthetic.stage_randoms(self.seed, self.stage, B_STAGE, 3)
+            return np.concatenate([u_res[None], u_acc]), z
+
+        def step(self, host_io=None):
+            if self.state is None or self.state.q >= 1.0:
+                self.seed += 1
+                self.generate()
+            U, Z = self.randoms()
+            if host_io is None:
+                Ud = torch.tensor(U, device=dev)
+                Zd = torch.tensor(Z, device=dev)
+            else:
+                Ud, Zd = host_io(U, Z)
+            g.tmcmc_stage(h, self.state, Ud, Zd)
+            self.stage += 1
+            self.stages_done += 1
+
+    job = Job()
+    for _ in range(args.warmup):
+        job.step()
+        flush.zero_()
+    torch.cuda.synchronize()
+
+    # ---- device-timed region: inputs of each stage are made on the device side of the
+    #      API (H2D of the random numbers is part of the e2e leg below)
+    clocks = ClockSampler(local_rank)
+    g.swimmer_profile(h, 1)
+    barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    stages0 = job.stages_done
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        job.step()
+        flush.zero_()
+    e1.record()
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    barrier()
+    clk = clocks.stop()
+    k2_ms, k2_launches, launches, pairs = g.swimmer_profile(h, 2)
+    g.swimmer_profile(h, 0)
+    ms_total = e0.elapsed_time(e1)
+    stages = job.stages_done - stages0
+
+    # ---- end-to-end: host buffers in, results out, per stage
+    pin_u = torch.empty((3, B_STAGE), dtype=torch.float64).pin_memory()
+    pin_z = torch.empty((B_STAGE, 3), dtype=torch.float64).pin_memory()
+    out_th = torch.empty((B_STAGE, 3), dtype=torch.float64).pin_memory()
+    out_ll = torch.empty(B_STAGE, dtype=torch.float64).pin_memory()
+    dev_u = torch.empty((3, B_STAGE), dtype=torch.float64, device=dev)
+    dev_z = torch.empty((B_STAGE, 3), dtype=torch.float64, device=dev)
+
+    def host_io(U, Z):
+        pin_u.copy_(torch.from_numpy(U))
+        pin_z.copy_(torch.from_numpy(Z))
+        dev_u.copy_(pin_u, non_blocking=True)
+        dev_z.copy_(pin_z, non_blocking=True)
+        return dev_u, dev_z
+
+    g.swimmer_profile(h, 1)
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    for _ in range(args.steps):
+        job.step(host_io)
+        out_th.copy_(job.state.theta, non_blocking=True)
+        out_ll.copy_(job.state.loglik, non_blocking=True)
+        torch.cuda.synchronize()
+    t3 = time.perf_counter()
+    _, _, _, pairs_e2e = g.swimmer_profile(h, 2)
+    g.swimmer_profile(h, 0)
+
+    # ---- aggregate over ranks (max time, summed work)
+    tot = torch.tensor([pairs, stages * B_STAGE, pairs_e2e], dtype=torch.float64, device=dev)
+    tmax = torch.tensor([ms_total, t3 - t2], dtype=torch.float64, device=dev)
+    if dist is not None:
+        dist.all_reduce(tot, op=dist.ReduceOp.SUM)
+        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+    pairs_all, samples_all, pairs_e2e_all = tot.tolist()
+    ms_all, e2e_s = tmax.tolist()
+
+    if rank == 0:
+        peaks, peak_src = load_peaks()
+        sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
+        max_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+        fp32_peak = sm_count * 128 * 2 * max_mhz * 1e6 / 1e12  # TFLOP/s
+        k2_avg_ms = k2_ms / max(k2_launches, 1)
+        achieved = FLOPS_PER_PAIR * pairs / (k2_ms * 1e-3) / 1e12 if k2_ms > 0 else 0.0
+        traffic_pp = kernel_traffic()
+        value = pairs_all / (ms_all * 1e-3)
+        line = {
+            "metric": METRIC, "value": value, "unit": "pair-evals/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_all / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32" if prec == g.FP32C else "f64",
+            "data": "synthetic", "config": dict(workload_config(args.precision), parallelism=f"dp{world} (independent TMCMC per GPU)"),
+            "tmcmc_samples_per_s": samples_all / (ms_all * 1e-3),
+            "clocks": clk,
+            "e2e": {"value": pairs_e2e_all / e2e_s, "unit": "pair-evals/s",
+                    "h2d_bytes_per_step": int(6 * B_STAGE * 8),
+                    "d2h_bytes_per_step": int(4 * B_STAGE * 8)},
+            "gpu_launches": int(launches),
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
+                         "frac": achieved / fp32_peak,
+                         "traffic": (traffic_pp * pairs / max(k2_launches, 1)) if traffic_pp else None,
+                         "kernel": "forward_kernel<fp32c>" if prec == g.FP32C else "forward_kernel<fp64>",
+                         "launches": int(k2_launches), "avg_launch_ms": k2_avg_ms,
+                         "peak_note": f"FP32 {sm_count} SMs x 128 lanes x 2 x {max_mhz:.0f} MHz ({peak_src} max clock)"},
+        }
+        if world == 1 and not args.no_cpu_baseline:
+            r = oracle_sample()
+            line["cpu_baseline"] = {"value": r["pairs"] / r["seconds"], "unit": "pair-evals/s", "cores": r["cores"],
+                                    "kind": "oracle", "sample": r["sample"]}
+        print(json.dumps(line), flush=True)
+    h.close()
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

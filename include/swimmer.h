@@ -27,6 +27,8 @@
 #ifndef SWIMMER_H
 #define SWIMMER_H
 
+#include <stddef.h>
+
 #ifdef __cplusplus
 extern "C" {
 #endif
@@ -76,6 +78,14 @@ int swimmer_destroy(swimmer_handle *h);
 /* Message for the last error on the calling thread (static storage). */
 const char *swimmer_last_error(void);
 
+/* Opt-in profiling.  mode 1: time every forward-kernel (K2) launch with CUDA events
+ * recorded on its stream and count all kernel launches of this handle; mode 0: stop;
+ * mode 2: wait for the recorded events, write out[4] = {total K2 milliseconds, K2
+ * launches, kernel launches, pair evaluations K2 executed (sum of n^2 x steps run, so
+ * skipped and early-stopped samples count what they did)} (host array) and reset.
+ * Synchronous. */
+int swimmer_profile(swimmer_handle *h, int mode, double *out);
+
 /* Kernel functions of the regularized Brinkmanlet (Sec. 2.1, Eq. BrV):
  * g1(r) = B''(r) and g2(r) = (r B''(r) - B'(r))/r^3 for (Lap - alpha^2) B = G, Lap G =
  * phi_delta (Eq. eqnblob), evaluated through the same per-sample table the forward
@@ -111,7 +121,7 @@ typedef struct tmcmc_state {
     double *theta;         /* device [B][3] current samples (updated in place) */
     double *loglik;        /* device [B] their log-likelihoods (updated in place) */
     int *status;           /* device [B] */
-    const int *n_pts;      /* device [B] or NULL (n_max for all) */
+    const int *n_pts;      /* ignored: every TMCMC sample uses n_max points */
     const double *obs;     /* device [n_obs][2] observations D */
     double sigma;          /* noise standard deviation */
     double prior_lo[3];    /* host: box-uniform prior bounds */
@@ -145,8 +155,9 @@ int tmcmc_stage(swimmer_handle *h, tmcmc_state *st, const double *uniforms, cons
 
 /* Stage pieces, exposed for testing (Algorithm 1 'Analyze' and 'Resample'):
  * tmcmc_analyze: from loglik[B] (device), theta[B][3] (device) and q (host) compute on the
- *   device: out_w[B] = exp(dq (l - l_max)) (0 for -inf), and stats[24] =
- *   {dq, q_next, log_S, l_max, mu[3], Sigma[9], L[9] (Cholesky), ...} (device FP64).
+ *   device: out_w[B] = exp(dq (l - l_max)) (0 for -inf), and stats[32] (device FP64) =
+ *   {dq, q_next, log_S, l_max, mu[3], Sigma[9], L[9] (lower Cholesky factor of Sigma),
+ *   status (0 ok, 1 every log-likelihood is -inf, 2 Sigma not positive definite), ...}.
  * tmcmc_resample: idx[B] (device int) = min{i : C_i > floor(u_k C_B)}, C = inclusive
  *   prefix of floor(w_i 2^40); also counts[B] (device int).  Integer results are exact. */
 int tmcmc_analyze(swimmer_handle *h, int B, const double *theta, const double *loglik, double q,
@@ -164,17 +175,24 @@ int tmcmc_resample(swimmer_handle *h, int B, const double *w, const double *u, i
 #define SWIMMER_MLP_OUT 80
 #define SWIMMER_MLP_NPARAM (5 * 256 + 256 + 256 * 256 + 256 + 256 * 256 + 256 + 256 * 80 + 80)
 
-/* Forward pass: x[n][5] (device FP32) -> y[n][80] (device FP32), parameters w32 (device
- * FP32 master copy, layout W1,b1,W2,b2,W3,b3,W4,b4 with W[out][in]); the kernel rounds
- * weights to BF16 and accumulates in FP32. */
-int mlp_forward(int n, const float *params, const float *x, float *y, void *stream);
+/* Bytes of device workspace mlp_forward / mlp_backward need for a batch of n samples
+ * (hidden pre-activations and activations, outputs and their gradients). */
+size_t mlp_workspace_bytes(int n);
 
-/* Gradient of the mean squared error over the batch: grad[NPARAM] (device FP32, overwritten),
- * loss_out[1] (device FP32). */
+/* Forward pass: x[n][5] (device FP32) -> y[n][80] (device FP32).  params (device FP32
+ * master copy, NPARAM floats, layout W1,b1,W2,b2,W3,b3,W4,b4 with W[out][in]); every
+ * weight is rounded to BF16 as it enters a product, accumulation is FP32.  workspace:
+ * device buffer of mlp_workspace_bytes(n) bytes, owned by the caller. */
+int mlp_forward(int n, const float *params, const float *x, float *y, float *workspace, void *stream);
+
+/* Loss and gradient: loss_out[0] = mean over n x 80 of (y - t)^2 and grad[NPARAM] = its
+ * gradient with respect to params (the BF16-rounded forward differentiated with the same
+ * rounded weights), both device FP32 and overwritten.  Deterministic (no atomics). */
 int mlp_backward(int n, const float *params, const float *x, const float *t, float *grad,
-                 float *loss_out, void *stream);
+                 float *loss_out, float *workspace, void *stream);
 
-/* Adam update in place on params (FP32 master weights), moments m, v (device FP32). */
+/* Adam (beta1 0.9, beta2 0.999, eps 1e-8, bias-corrected; step counts from 1) in place
+ * on the FP32 master params with moments m, v (device FP32, NPARAM each). */
 int mlp_adam(float *params, const float *grad, float *m, float *v, int step, float lr, void *stream);
 
 /* Surrogate log-likelihood for delayed acceptance: attaches trained parameters and the

@@ -279,6 +279,36 @@ def hankel_g(r, alpha, delta, kmax_over_delta=45.0):
     return g1 / (2 * np.pi), g2 / (2 * np.pi)
 
 
+def _node_values(r, alpha, delta):
+    """(g1, g2) at ascending distances r > 0: A1 and C are accumulated from integrals
+    between neighbouring points, then combined exactly as in :func:`kernel_g`."""
+    if alpha == 0.0:
+        return np.stack(stokes_g(r, delta), axis=1)
+    fa = lambda s: i0_minus_1(alpha * s) * float(blob(s, delta)) * s
+    fc = lambda s: k0(alpha * s) * float(blob(s, delta)) * s
+    n = len(r)
+    A = np.zeros(n)
+    C = np.zeros(n)
+    prev, acc = 0.0, 0.0
+    for m in range(n):
+        acc += integrate.quad(fa, prev, r[m], **_QUAD)[0]
+        A[m] = acc
+        prev = r[m]
+    acc = c_integral(r[-1], alpha, delta)
+    C[-1] = acc
+    for m in range(n - 2, -1, -1):
+        acc += integrate.quad(fc, r[m], r[m + 1], **_QUAD)[0]
+        C[m] = acc
+    out = np.zeros((n, 2))
+    for m in range(n):
+        x = alpha * r[m]
+        M = float(m0(r[m], delta))
+        w = 0.5 * (k0(x) + k2(x))
+        out[m, 0] = inv_x2_minus_w(x) * M - w * A[m] - 0.5 * (float(special.i0(x)) + i2(x)) * C[m]
+        out[m, 1] = (two_over_x2_minus_k2(x) * M - k2(x) * A[m] - i2(x) * C[m]) / (r[m] * r[m])
+    return out
+
+
 # ---------------------------------------------------------------------------------
 # interpolation table over u = 1 + r^2/delta^2 (used by the oracle's time stepping)
 # ---------------------------------------------------------------------------------
@@ -290,7 +320,9 @@ class KernelTable:
     cut into ``n_sub`` equal panels; each carries a degree-``deg`` Chebyshev series fitted
     at first-kind Chebyshev nodes from :func:`kernel_g`.  With n_sub = 4 the nearest
     singularity lies >= 9 half-widths from each panel centre, so degree 14 reaches
-    rounding level.  The pin test checks the table against pointwise evaluation.
+    rounding level.  Node values come from :func:`_node_values` (the integrals of
+    :func:`kernel_g` accumulated between neighbouring nodes).  The pin test checks the
+    table against pointwise evaluation.
     """
 
     def __init__(self, alpha, delta, r_max, n_sub=4, deg=14):
@@ -303,15 +335,22 @@ class KernelTable:
         npan = self.n_oct * n_sub
         self.coef = np.zeros((2, npan, deg + 1))
         t = np.cos(np.pi * (np.arange(deg + 1) + 0.5) / (deg + 1))  # Chebyshev nodes
+        # all nodes in ascending u; A1 and C accumulate integrals between neighbouring
+        # nodes (the same integrals kernel_g evaluates from 0 / to infinity)
+        us = []
         for e in range(self.n_oct):
             for j in range(n_sub):
                 ua = 2.0 ** e * (1.0 + j / n_sub)
                 ub = 2.0 ** e * (1.0 + (j + 1) / n_sub)
-                u = 0.5 * (ua + ub) + 0.5 * (ub - ua) * t
-                vals = np.array([kernel_g(delta * math.sqrt(max(ui - 1.0, 0.0)), alpha, delta) for ui in u])
-                p = e * n_sub + j
-                for f in range(2):
-                    self.coef[f, p] = np.polynomial.chebyshev.chebfit(t, vals[:, f], deg)
+                us.append(np.sort(0.5 * (ua + ub) + 0.5 * (ub - ua) * t))
+        u = np.concatenate(us)
+        r = delta * np.sqrt(np.maximum(u - 1.0, 0.0))
+        vals = _node_values(r, alpha, delta)
+        for p in range(npan):
+            vp = vals[p * (deg + 1):(p + 1) * (deg + 1)]
+            tp = np.sort(t)
+            for f in range(2):
+                self.coef[f, p] = np.polynomial.chebyshev.chebfit(tp, vp[:, f], deg)
 
     def locate(self, u):
         u = np.asarray(u, dtype=np.float64)

@@ -293,3 +293,26 @@ def run_c_batch(params_list, tables=None, threads=0, steps=None):
     if rc != 0:
         raise RuntimeError(f"oracle_forward_batch failed: {rc}")
     return obs[:, :n_obs], [Xf[b, : n_arr[b]] for b in range(B)], xc, status
+
+
+# ---------------------------------------------------------------------------------
+# many samples at once: tables + C loop in a spawn-started process pool
+# ---------------------------------------------------------------------------------
+def _loglik_chunk(args):
+    base, thetas, D, sigma = args
+    ps = [base.with_theta(t) for t in thetas]
+    obs, _, _, st = run_c_batch(ps, threads=1)
+    out = np.full(len(ps), -np.inf)
+    for b in range(len(ps)):
+        if st[b] == 0:
+            out[b] = log_likelihood(obs[b], D, sigma)
+    return out
+
+
+def batch_log_likelihood(base: SwimmerParams, thetas, D, sigma, pool=None, chunk=8):
+    """log p(D|theta) for every row of thetas (diverged runs give -inf).  ``pool`` is a
+    multiprocessing pool created with the 'spawn' start method (or None: serial)."""
+    thetas = np.asarray(thetas, dtype=np.float64)
+    parts = [(base, thetas[i:i + chunk], D, sigma) for i in range(0, len(thetas), chunk)]
+    res = pool.map(_loglik_chunk, parts) if pool is not None else [_loglik_chunk(a) for a in parts]
+    return np.concatenate(res) if res else np.zeros(0)

@@ -36,16 +36,18 @@ SIGNATURES = [
     ("swimmer_init", c_int, [P(SwimmerConfigC), P(c_void_p)]),
     ("swimmer_destroy", c_int, [c_void_p]),
     ("swimmer_last_error", ctypes.c_char_p, []),
+    ("swimmer_profile", c_int, [c_void_p, c_int, c_void_p]),
     ("swimmer_kernel_eval", c_int, [c_void_p, c_double, c_double, c_double, c_int, c_void_p, c_void_p, c_void_p, c_int, c_void_p]),
     ("forward_batch", c_int, [c_void_p, c_int, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     ("loglik_batch", c_int, [c_void_p, c_int, c_void_p, c_void_p, c_void_p, c_double, c_void_p, c_void_p, c_void_p]),
     ("tmcmc_stage", c_int, [c_void_p, P(TmcmcStateC), c_void_p, c_void_p, c_int, c_void_p]),
     ("tmcmc_analyze", c_int, [c_void_p, c_int, c_void_p, c_void_p, c_double, c_void_p, c_void_p, c_void_p]),
     ("tmcmc_resample", c_int, [c_void_p, c_int, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
-    ("mlp_forward", c_int, [c_int, c_void_p, c_void_p, c_void_p, c_void_p]),
-    ("mlp_backward", c_int, [c_int, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
+    ("mlp_workspace_bytes", ctypes.c_size_t, [c_int]),
+    ("mlp_forward", c_int, [c_int, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
+    ("mlp_backward", c_int, [c_int, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     ("mlp_adam", c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_int, c_float, c_void_p]),
-    ("swimmer_surrogate_set", c_int, [c_void_p, c_void_p, P(c_double), P(c_double), P(c_double), P(c_double), c_int, c_double, c_double]),
+    ("swimmer_surrogate_set", c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_int, c_double, c_double]),
     ("surrogate_loglik_batch", c_int, [c_void_p, c_int, c_void_p, c_void_p, c_double, c_void_p, c_void_p]),
 ]
 

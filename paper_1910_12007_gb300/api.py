@@ -132,3 +132,164 @@ def loglik_batch(h: Handle, theta, obs, sigma, n_pts=None, stream=None, out=None
     check(lib().loglik_batch(h.ptr, B, _ptr(theta), _ptr(n_pts), _ptr(obs), float(sigma), _ptr(ll),
                              _ptr(status), _stream(stream)))
     return ll, status
+
+
+# ---------------------------------------------------------------------------------
+# TMCMC (Sec. 3.2, Algorithm 1)
+# ---------------------------------------------------------------------------------
+def tmcmc_analyze(h: Handle, theta, loglik, q, stream=None):
+    """Algorithm 1 'Analyze' on the device: returns (w [B], stats [32]) device tensors."""
+    _dev(theta, torch.float64)
+    _dev(loglik, torch.float64)
+    B = loglik.numel()
+    w = torch.empty(B, dtype=torch.float64, device=loglik.device)
+    stats = torch.zeros(32, dtype=torch.float64, device=loglik.device)
+    check(lib().tmcmc_analyze(h.ptr, B, _ptr(theta), _ptr(loglik), float(q), _ptr(w), _ptr(stats), _stream(stream)))
+    return w, stats
+
+
+def tmcmc_resample(h: Handle, w, u, stream=None):
+    """Multinomial resampling indices and counts (exact integers) on the device."""
+    _dev(w, torch.float64)
+    _dev(u, torch.float64)
+    B = w.numel()
+    idx = torch.empty(B, dtype=torch.int32, device=w.device)
+    counts = torch.empty(B, dtype=torch.int32, device=w.device)
+    check(lib().tmcmc_resample(h.ptr, B, _ptr(w), _ptr(u), _ptr(idx), _ptr(counts), _stream(stream)))
+    return idx, counts
+
+
+class TmcmcState:
+    """Device-resident TMCMC state (theta, loglik) plus the host-side stage summary."""
+
+    def __init__(self, theta, loglik, obs, sigma, prior_lo, prior_hi, surr_loglik=None):
+        self.theta = _dev(theta, torch.float64)
+        self.loglik = _dev(loglik, torch.float64)
+        self.status = torch.zeros(theta.shape[0], dtype=torch.int32, device=theta.device)
+        self.obs = _dev(obs, torch.float64)
+        self.surr_loglik = surr_loglik
+        c = TmcmcStateC()
+        c.B = theta.shape[0]
+        c.theta = theta.data_ptr()
+        c.loglik = loglik.data_ptr()
+        c.status = self.status.data_ptr()
+        c.n_pts = None
+        c.obs = obs.data_ptr()
+        c.sigma = float(sigma)
+        for a in range(3):
+            c.prior_lo[a] = float(prior_lo[a])
+            c.prior_hi[a] = float(prior_hi[a])
+        c.q = 0.0
+        c.stage = 0
+        c.surr_loglik = surr_loglik.data_ptr() if surr_loglik is not None else None
+        self.c = c
+
+    @property
+    def q(self):
+        return self.c.q
+
+    def summary(self):
+        c = self.c
+        return dict(stage=c.stage, q=c.q, log_s=c.log_s, mu=list(c.mu), unique=c.unique,
+                    max_chain=c.max_chain, n_exact=c.n_exact, n_screened=c.n_screened, n_accept=c.n_accept)
+
+
+def tmcmc_stage(h: Handle, st: TmcmcState, uniforms, normals, use_surrogate=False, stream=None):
+    """One TMCMC stage on the device; uniforms [3, B], normals [B, 3] (FP64, device)."""
+    _dev(uniforms, torch.float64)
+    _dev(normals, torch.float64)
+    check(lib().tmcmc_stage(h.ptr, ctypes.byref(st.c), _ptr(uniforms), _ptr(normals), int(bool(use_surrogate)),
+                            _stream(stream)))
+    return st.summary()
+
+
+def tmcmc_run(h: Handle, theta0, obs, sigma, prior_lo, prior_hi, randoms, use_surrogate=False, max_stages=100,
+              stream=None, log=None):
+    """Algorithm 1 driven from the host: prior samples theta0 [B, 3] (device), observations
+    obs [n_obs, 2]; ``randoms(stage) -> (u_res [B], u_acc [2, B], z [B, 3])`` numpy arrays
+    (the seeded streams of the ``synthetic`` module).  Returns the final TmcmcState."""
+    ll, status = loglik_batch(h, theta0, obs, sigma, stream=stream)
+    surr = None
+    if use_surrogate:
+        surr = surrogate_loglik_batch(h, theta0, obs, sigma, stream=stream)
+    st = TmcmcState(theta0.clone(), ll, obs, sigma, prior_lo, prior_hi, surr)
+    dev = theta0.device
+    for j in range(max_stages):
+        u_res, u_acc, z = randoms(j)
+        U = torch.tensor(np_stack_uniforms(u_res, u_acc), dtype=torch.float64, device=dev)
+        Z = torch.tensor(z, dtype=torch.float64, device=dev)
+        s = tmcmc_stage(h, st, U, Z, use_surrogate, stream)
+        if log is not None:
+            log.append(s)
+        if st.q >= 1.0:
+            break
+    return st
+
+
+def np_stack_uniforms(u_res, u_acc):
+    import numpy as np
+
+    return np.concatenate([np.asarray(u_res)[None, :], np.asarray(u_acc)], axis=0)
+
+
+# ---------------------------------------------------------------------------------
+# learned surrogate (MLP 5 -> 256 -> 256 -> 256 -> 80)
+# ---------------------------------------------------------------------------------
+MLP_IN, MLP_HIDDEN, MLP_OUT = 5, 256, 80
+MLP_NPARAM = 5 * 256 + 256 + 256 * 256 + 256 + 256 * 256 + 256 + 256 * 80 + 80
+
+
+def mlp_workspace(n, device):
+    nbytes = lib().mlp_workspace_bytes(int(n))
+    return torch.empty(nbytes // 4 + 1, dtype=torch.float32, device=device)
+
+
+def mlp_forward(params, x, workspace=None, stream=None):
+    _dev(params, torch.float32)
+    _dev(x, torch.float32)
+    n = x.shape[0]
+    y = torch.empty((n, MLP_OUT), dtype=torch.float32, device=x.device)
+    ws = workspace if workspace is not None else mlp_workspace(n, x.device)
+    check(lib().mlp_forward(n, _ptr(params), _ptr(x), _ptr(y), _ptr(ws), _stream(stream)))
+    return y
+
+
+def mlp_backward(params, x, t, workspace=None, stream=None, grad=None, loss=None):
+    _dev(params, torch.float32)
+    _dev(x, torch.float32)
+    _dev(t, torch.float32)
+    n = x.shape[0]
+    grad = grad if grad is not None else torch.empty(MLP_NPARAM, dtype=torch.float32, device=x.device)
+    loss = loss if loss is not None else torch.empty(1, dtype=torch.float32, device=x.device)
+    ws = workspace if workspace is not None else mlp_workspace(n, x.device)
+    check(lib().mlp_backward(n, _ptr(params), _ptr(x), _ptr(t), _ptr(grad), _ptr(loss), _ptr(ws), _stream(stream)))
+    return grad, loss
+
+
+def mlp_adam(params, grad, m, v, step, lr, stream=None):
+    check(lib().mlp_adam(_ptr(params), _ptr(grad), _ptr(m), _ptr(v), int(step), float(lr), _stream(stream)))
+
+
+def swimmer_surrogate_set(h: Handle, params, in_lo, in_hi, out_mean, out_std, obs_stride, log10_kt, omega):
+    _dev(params, torch.float32)
+    arr = lambda a, n: (ctypes.c_double * n)(*[float(v) for v in a])
+    check(lib().swimmer_surrogate_set(h.ptr, _ptr(params), arr(in_lo, 5), arr(in_hi, 5), arr(out_mean, MLP_OUT),
+                                      arr(out_std, MLP_OUT), int(obs_stride), float(log10_kt), float(omega)))
+
+
+def surrogate_loglik_batch(h: Handle, theta, obs, sigma, stream=None):
+    _dev(theta, torch.float64)
+    _dev(obs, torch.float64)
+    ll = torch.empty(theta.shape[0], dtype=torch.float64, device=theta.device)
+    check(lib().surrogate_loglik_batch(h.ptr, theta.shape[0], _ptr(theta), _ptr(obs), float(sigma), _ptr(ll),
+                                       _stream(stream)))
+    return ll
+
+
+def swimmer_profile(h: Handle, mode):
+    """mode 1: start timing forward-kernel launches (CUDA events on their stream) and
+    counting kernel launches; mode 2: return (k2_ms, k2_launches, launches, k2_samples) and
+    reset; mode 0: stop."""
+    out = (ctypes.c_double * 4)()
+    check(lib().swimmer_profile(h.ptr, int(mode), out))
+    return tuple(out) if mode == 2 else None

@@ -4,9 +4,74 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <vector>
+
 #include "common.cuh"
 
 static thread_local char g_err[512] = "";
+
+struct ProfileEvents {
+    std::vector<cudaEvent_t> start, stop;
+    std::vector<int> samples;
+    size_t used = 0;
+};
+
+void prof_count(swimmer_handle *h, int launches) { h->n_launch += launches; }
+
+void prof_k2_begin(swimmer_handle *h, cudaStream_t s, int samples) {
+    if (!h->profile) return;
+    ProfileEvents *p = h->prof;
+    if (p->used == p->start.size()) {
+        cudaEvent_t a, b;
+        cudaEventCreate(&a);
+        cudaEventCreate(&b);
+        p->start.push_back(a);
+        p->stop.push_back(b);
+        p->samples.push_back(0);
+    }
+    p->samples[p->used] = samples;
+    cudaEventRecord(p->start[p->used], s);
+}
+
+void prof_k2_end(swimmer_handle *h, cudaStream_t s) {
+    if (!h->profile) return;
+    ProfileEvents *p = h->prof;
+    cudaEventRecord(p->stop[p->used], s);
+    p->used += 1;
+}
+
+extern "C" int swimmer_profile(swimmer_handle *h, int mode, double *out) {
+    ARG_CHECK(h != nullptr, "handle is NULL");
+    ARG_CHECK(mode >= 0 && mode <= 2, "mode must be 0, 1 or 2");
+    ProfileEvents *p = h->prof;
+    if (mode == 2) {
+        ARG_CHECK(out != nullptr, "out is NULL");
+        double ms = 0.0, samples = 0.0;
+        for (size_t i = 0; i < p->used; ++i) {
+            CUDA_TRY(cudaEventSynchronize(p->stop[i]));
+            float t = 0.f;
+            CUDA_TRY(cudaEventElapsedTime(&t, p->start[i], p->stop[i]));
+            ms += t;
+            samples += p->samples[i];
+        }
+        unsigned long long work = 0;
+        CUDA_TRY(cudaMemcpy(&work, h->work, sizeof(work), cudaMemcpyDeviceToHost));
+        out[0] = ms;
+        out[1] = (double)p->used;
+        out[2] = (double)h->n_launch;
+        out[3] = (double)work;
+        p->used = 0;
+        h->n_launch = 0;
+        CUDA_TRY(cudaMemset(h->work, 0, sizeof(work)));
+        return 0;
+    }
+    h->profile = mode;
+    p->used = 0;
+    h->n_launch = 0;
+    CUDA_TRY(cudaDeviceSynchronize());
+    CUDA_TRY(cudaMemset(h->work, 0, sizeof(unsigned long long)));
+    return 0;
+}
 
 void set_error(const char *fmt, ...) {
     va_list ap;
@@ -51,6 +116,7 @@ extern "C" int swimmer_init(const swimmer_config *cfg, swimmer_handle **out) {
     swimmer_handle *h = (swimmer_handle *)calloc(1, sizeof(swimmer_handle));
     ARG_CHECK(h != nullptr, "out of host memory");
     h->cfg = *cfg;
+    h->prof = new ProfileEvents();
     CUDA_TRY(cudaGetDevice(&h->device));
     CUDA_TRY(cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device));
     const int B = cfg->b_max;
@@ -80,12 +146,16 @@ extern "C" int swimmer_init(const swimmer_config *cfg, swimmer_handle **out) {
     ALLOC(h->prop_status, B);
     ALLOC(h->active, B);
     ALLOC(h->active2, B);
+    ALLOC(h->cum, B);
+    ALLOC(h->info, 128);
+    ALLOC(h->work, 1);
+    CUDA_TRY(cudaMemset(h->work, 0, sizeof(unsigned long long)));
     ALLOC(h->surr_norm, 2 * SWIMMER_MLP_OUT);
     ALLOC(h->surr_params, SWIMMER_MLP_NPARAM);
     ALLOC(h->surr_x, (size_t)B * SWIMMER_MLP_IN);
     ALLOC(h->surr_y, (size_t)B * SWIMMER_MLP_OUT);
     {
-        cudaError_t e1 = cudaMallocHost((void **)&h->host_pinned, 64 * sizeof(int));
+        cudaError_t e1 = cudaMallocHost((void **)&h->host_pinned, (B + 128) * sizeof(int));
         cudaError_t e2 = cudaMallocHost((void **)&h->host_pinned_d, 64 * sizeof(double));
         if (e1 != cudaSuccess || e2 != cudaSuccess) {
             set_error("cudaMallocHost failed");
@@ -109,12 +179,17 @@ extern "C" int swimmer_destroy(swimmer_handle *h) {
     void *ptrs[] = {h->tab64, h->tab32, h->sp, h->order, h->queue, h->speed_tmp, h->w, h->stats,
                     h->idx, h->counts, h->chain_id, h->chain_off, h->chain_len, h->aux,
                     h->cur_theta, h->cur_ll, h->cur_sl, h->prop_theta, h->prop_ll, h->prop_sl,
-                    h->out_theta, h->out_ll, h->out_sl, h->prop_status, h->active, h->active2,
-                    h->surr_norm, h->surr_params, h->surr_x, h->surr_y};
+                    h->out_theta, h->out_ll, h->out_sl, h->prop_status, h->active, h->active2, h->cum, h->info, h->work,
+                    h->surr_norm, h->surr_params, h->surr_x, h->surr_y, h->surr_ws};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (h->host_pinned) cudaFreeHost(h->host_pinned);
     if (h->host_pinned_d) cudaFreeHost(h->host_pinned_d);
+    if (h->prof) {
+        for (cudaEvent_t e : h->prof->start) cudaEventDestroy(e);
+        for (cudaEvent_t e : h->prof->stop) cudaEventDestroy(e);
+        delete h->prof;
+    }
     free(h);
     return 0;
 }

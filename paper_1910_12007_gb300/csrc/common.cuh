@@ -36,8 +36,15 @@ struct SampleParams {
     int n, n_oct, status, pad;
 };
 
+struct ProfileEvents;
+
 struct swimmer_handle {
     swimmer_config cfg;
+    // opt-in profiling: CUDA events around every forward-kernel launch, launch counter
+    int profile;
+    long long n_launch;
+    ProfileEvents *prof;
+    unsigned long long *work;  // device counter: pair evaluations executed by the forward kernel
     int device;
     int num_sms;
     // per-sample workspace (b_max samples)
@@ -53,7 +60,9 @@ struct swimmer_handle {
     int *idx, *counts, *chain_id, *chain_off, *chain_len, *aux;  // [b_max] each, aux [b_max+64]
     double *cur_theta, *cur_ll, *cur_sl, *prop_theta, *prop_ll, *prop_sl, *out_theta, *out_ll, *out_sl;
     int *prop_status, *active, *active2;
-    int *host_pinned;       // pinned host scratch (64 ints)
+    unsigned long long *cum;  // [b_max] fixed-point prefix sums
+    int *info;              // [128] device counters / host-visible summary
+    int *host_pinned;       // pinned host scratch (b_max + 128 ints)
     double *host_pinned_d;  // pinned host scratch (64 doubles)
     // surrogate
     float *surr_params;     // device copy of the trained parameters (NPARAM)
@@ -63,6 +72,7 @@ struct swimmer_handle {
     double surr_log10_kt, surr_omega;
     int surr_ready;
     float *surr_x, *surr_y; // [b_max][5], [b_max][80]
+    float *surr_ws;         // MLP workspace for b_max samples (allocated by swimmer_surrogate_set)
 };
 
 // ---- error reporting -----------------------------------------------------------------
@@ -85,6 +95,11 @@ void set_error(const char *fmt, ...);
             return SWIMMER_E_ARG;                                                    \
         }                                                                            \
     } while (0)
+
+// profiling hooks (api.cu): count a kernel launch; bracket a forward-kernel launch
+void prof_count(swimmer_handle *h, int launches);
+void prof_k2_begin(swimmer_handle *h, cudaStream_t s, int samples);
+void prof_k2_end(swimmer_handle *h, cudaStream_t s);
 
 // ---- launchers implemented in the kernel translation units ----------------------------
 int launch_prepare(swimmer_handle *h, int B, const double *theta, const int *n_pts, cudaStream_t s);

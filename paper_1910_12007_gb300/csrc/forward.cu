@@ -42,6 +42,7 @@ struct FwdArgs {
     double *head_traj;
     double *speed;
     int *status;
+    unsigned long long *work;
     int n_max;
     int threads;
 };
@@ -375,6 +376,7 @@ __global__ void __launch_bounds__(1024) forward_kernel(FwdArgs a) {
                 a.speed[b] = status == SWIMMER_OK ? (tot / n - 0.5 * L) / (a.steps * a.dt) : nan("");
             }
         }
+        if (tid == 0) atomicAdd(a.work, (unsigned long long)n * (unsigned long long)n * (unsigned long long)steps_done);
         if (owner && tgt == n - 1) {
             a.status[b] = status;
             if (a.loglik) {
@@ -417,6 +419,7 @@ int launch_forward(swimmer_handle *h, int B, const double *obs, double sigma, do
     a.head_traj = head_traj;
     a.speed = mean_speed;
     a.status = status;
+    a.work = h->work;
     a.n_max = h->cfg.n_max;
     int T = 32;
     while (T < h->cfg.n_max && T < 1024) T <<= 1;
@@ -435,7 +438,10 @@ int launch_forward(swimmer_handle *h, int B, const double *obs, double sigma, do
     int grid = per_sm * h->num_sms;
     if (grid > B) grid = B;
     CUDA_TRY(cudaMemsetAsync(h->queue, 0, sizeof(int), s));
+    prof_k2_begin(h, s, B);
     kern<<<grid, T, smem, s>>>(a);
     CUDA_TRY(cudaGetLastError());
+    prof_k2_end(h, s);
+    prof_count(h, 1);
     return 0;
 }

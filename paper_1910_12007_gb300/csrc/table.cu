@@ -508,6 +508,7 @@ int gl_init() {
 int launch_prepare(swimmer_handle *h, int B, const double *theta, const int *n_pts, cudaStream_t s) {
     prepare_kernel<<<(B + 127) / 128, 128, 0, s>>>(B, theta, n_pts, h->cfg, h->sp, h->order);
     CUDA_TRY(cudaGetLastError());
+    prof_count(h, 1);
     return 0;
 }
 
@@ -521,6 +522,7 @@ int launch_table_build(swimmer_handle *h, int B, int need64, cudaStream_t s) {
     }
     table_build_kernel<<<B, K1_THREADS, smem, s>>>(B, h->sp, h->tab64, h->tab32);
     CUDA_TRY(cudaGetLastError());
+    prof_count(h, 1);
     return 0;
 }
 

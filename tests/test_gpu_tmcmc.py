@@ -1,0 +1,131 @@
+"""GPU parity of the TMCMC stage kernels (Sec. 3.2, Algorithm 1) against the oracle,
+through the C ABI.  Resample indices are compared bit for bit; the annealing solve and
+statistics to FP64 rounding; a whole TMCMC run on a small swimmer problem sample by
+sample (FP64 path) and by posterior moments (FP32-compensated path)."""
+import math
+import multiprocessing as mp
+from dataclasses import replace
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import synthetic
+from oracle import swimmer as sw
+from oracle import tmcmc as tm
+
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+import paper_1910_12007_gb300 as g  # noqa: E402
+
+DEV = torch.device("cuda:0")
+
+
+def _h(b_max, **kw):
+    cfg = g.SwimmerConfig(n_max=12, b_max=b_max, steps=10, obs_every=1)
+    for k, v in kw.items():
+        setattr(cfg, k, v)
+    return g.swimmer_init(cfg)
+
+
+@pytest.mark.parametrize("B,q", [(1000, 0.0), (777, 0.3), (64, 0.9), (4096, 0.05)])
+def test_analyze_matches_oracle(B, q):
+    rng = np.random.default_rng(B)
+    ll = rng.normal(-300, 30, size=B)
+    ll[rng.integers(0, B, size=B // 50)] = -np.inf
+    th = rng.normal(size=(B, 3)) * [0.5, 0.3, 0.05] + [1.0, 0.0, 0.1]
+    a = tm.analyze(th, ll, q)
+    h = _h(B)
+    w, st = g.tmcmc_analyze(h, torch.tensor(th, device=DEV), torch.tensor(ll, device=DEV), q)
+    torch.cuda.synchronize()
+    st = st.cpu().numpy()
+    assert st[25] == 0.0
+    assert abs(st[0] - a["dq"]) <= 1e-12 * max(a["dq"], 1e-300)
+    assert st[1] == pytest.approx(a["q_next"], rel=1e-12)
+    assert st[2] == pytest.approx(a["log_s"], rel=1e-12)
+    assert np.allclose(st[4:7], a["mu"], rtol=1e-11, atol=1e-14)
+    assert np.allclose(st[7:16].reshape(3, 3), a["sigma"], rtol=1e-10, atol=1e-16)
+    assert np.allclose(st[16:25].reshape(3, 3), a["chol"], rtol=1e-10, atol=1e-16)
+    assert np.allclose(w.cpu().numpy(), a["w"], rtol=1e-11, atol=0)
+    h.close()
+
+
+@pytest.mark.parametrize("B", [1, 3, 17, 1024, 4097])
+def test_resample_bit_exact(B):
+    rng = np.random.default_rng(B + 5)
+    w = rng.uniform(0, 1, B) ** 4
+    w[rng.integers(0, B)] = 1.0
+    if B > 3:
+        w[rng.integers(0, B, size=B // 4)] = 0.0
+        w[0] = 1.0
+    u = synthetic.uniforms(2, synthetic.RESAMPLE, B, B)
+    ref = tm.resample(w, u)
+    h = _h(B)
+    idx, counts = g.tmcmc_resample(h, torch.tensor(w, device=DEV), torch.tensor(u, device=DEV))
+    torch.cuda.synchronize()
+    assert np.array_equal(idx.cpu().numpy(), ref)
+    assert np.array_equal(counts.cpu().numpy(), np.bincount(ref, minlength=B))
+    h.close()
+
+
+# a small swimmer inverse problem: theta = (alpha, log10 K_C, a)
+BASE = sw.SwimmerParams(n=12, dt=2e-4, steps=5000, obs_every=250, alpha=1.0, amp=0.1)
+LO = np.array([0.0, -1.0, 0.05])
+HI = np.array([10.0, 1.0, 0.2])
+TRUTH = (1.0, 0.0, 0.1)
+
+
+def _problem():
+    obs, _, _, st = sw.run_c_batch([BASE.with_theta(TRUTH)])
+    xi = obs[0]
+    sigma = sw.noise_sigma(xi, 0.05)
+    D = xi + sigma * synthetic.normals(1234, synthetic.NOISE, 0, xi.size).reshape(xi.shape)
+    return D, sigma
+
+
+def _gpu_run(B, seed, precision, D, sigma):
+    cfg = g.SwimmerConfig(n_max=BASE.n, b_max=B, length=BASE.length, dt=BASE.dt, steps=BASE.steps,
+                          obs_every=BASE.obs_every, precision=precision)
+    h = g.swimmer_init(cfg)
+    th0 = torch.tensor(synthetic.prior_samples(seed, LO, HI, B), device=DEV)
+    log = []
+    st = g.tmcmc_run(h, th0, torch.tensor(D, device=DEV), sigma, LO, HI,
+                     lambda j: synthetic.stage_randoms(seed, j, B, 3), log=log)
+    torch.cuda.synchronize()
+    out = st.theta.cpu().numpy(), st.loglik.cpu().numpy(), log
+    h.close()
+    return out
+
+
+def test_tmcmc_fp64_matches_oracle_sample_by_sample():
+    B, seed = 96, 42
+    D, sigma = _problem()
+    th_g, ll_g, log_g = _gpu_run(B, seed, g.FP64, D, sigma)
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(min(16, mp.cpu_count())) as pool:
+        fn = lambda th: sw.batch_log_likelihood(BASE, th, D, sigma, pool=pool, chunk=4)
+        th_o, ll_o, log_o = tm.run(synthetic.prior_samples(seed, LO, HI, B), fn, LO, HI, seed,
+                                   randoms=lambda j: synthetic.stage_randoms(seed, j, B, 3))
+    assert [s["q"] for s in log_g] == pytest.approx(log_o.q, rel=1e-9)
+    assert [s["unique"] for s in log_g] == log_o.unique
+    assert np.allclose(th_g, th_o, rtol=1e-8, atol=1e-10)
+    assert np.allclose(ll_g, ll_o, rtol=1e-8, atol=1e-8)
+
+
+def test_tmcmc_fp32_posterior_matches_fp64():
+    B, seed = 512, 7
+    D, sigma = _problem()
+    th64, _, log64 = _gpu_run(B, seed, g.FP64, D, sigma)
+    th32, _, log32 = _gpu_run(B, seed, g.FP32C, D, sigma)
+    assert log32[-1]["q"] == 1.0 and log64[-1]["q"] == 1.0
+    m64, s64 = th64.mean(0), th64.std(0)
+    m32, s32 = th32.mean(0), th32.std(0)
+    # posterior means within 2 % (relative to the mean) and standard deviations within 2 %
+    # of the mean's scale; the Monte-Carlo noise between two chains that share random
+    # inputs is far below this
+    assert np.all(np.abs(m32 - m64) <= 0.02 * np.abs(m64) + 0.02 * s64), (m32, m64, s32, s64)
+    assert np.all(np.abs(s32 - s64) <= 0.2 * s64), (s32, s64)
