@@ -193,6 +193,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="fp32c", choices=["fp32c", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile-case", action="store_true",
+                    help="run one forward batch of the workload (1024 samples, 200 steps) for ncu and exit")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -222,7 +224,17 @@ def main():
     prec = g.FP64 if args.precision == "fp64" else g.FP32C
     cfg = g.SwimmerConfig(n_max=N_PTS, b_max=B_STAGE, length=1.0, dt=DT, steps=STEPS, obs_every=OBS_EVERY,
                           precision=prec)
+    if args.profile_case:
+        cfg.steps = 200
+        h = g.swimmer_init(cfg)
+        th = torch.tensor(synthetic.prior_samples(5, PRIOR_LO, (10.0, 0.2, 0.2), B_STAGE), device=dev)
+        for _ in range(2):
+            g.forward_batch(h, th, want_traj=False)
+        torch.cuda.synchronize()
+        h.close()
+        return 0
     h = g.swimmer_init(cfg)
+    tuned = g.swimmer_autotune(h, steps=400)  # launch shape per batch-size bucket (untimed)
     seed0 = 1000 + 97 * rank
 
     # synthetic observations: forward model at theta*, plus 5 % noise (untimed set-up)
@@ -349,6 +361,7 @@ def main():
             "scaling": "weak", "vs_baseline": None, "dtype": "f32" if prec == g.FP32C else "f64",
             "data": "synthetic", "config": dict(workload_config(args.precision), parallelism=f"dp{world} (independent TMCMC per GPU)"),
             "tmcmc_samples_per_s": samples_all / (ms_all * 1e-3),
+            "autotuned_threads_per_sample": {str(k): v for k, v in tuned.items()},
             "clocks": clk,
             "e2e": {"value": pairs_e2e_all / e2e_s, "unit": "pair-evals/s",
                     "h2d_bytes_per_step": int(6 * B_STAGE * 8),

@@ -90,7 +90,8 @@ int swimmer_profile(swimmer_handle *h, int mode, double *out);
  * g1(r) = B''(r) and g2(r) = (r B''(r) - B'(r))/r^3 for (Lap - alpha^2) B = G, Lap G =
  * phi_delta (Eq. eqnblob), evaluated through the same per-sample table the forward
  * kernels use.  r[m], g1[m], g2[m]: device arrays; precision selects the FP64 (Chebyshev
- * degree 9) or the FP32 (cubic) table.  For testing the table build (step A1). */
+ * degree 9) or the FP32 (quadratic, built the way FP32 handles build it) table.  For
+ * testing the table build (step A1). */
 int swimmer_kernel_eval(swimmer_handle *h, double alpha, double delta, double r_max, int m,
                         const double *r, double *g1, double *g2, int precision, void *stream);
 
@@ -105,6 +106,15 @@ int swimmer_kernel_eval(swimmer_handle *h, double alpha, double delta, double r_
  * One persistent launch for the whole batch (plus the table build). */
 int forward_batch(swimmer_handle *h, int B, const double *theta, const int *n_pts,
                   double *head_traj, double *mean_speed, int *status, void *stream);
+
+/* Autotuner for the forward kernel's launch shape: for batch sizes B = 1, 2, 4, ...,
+ * b_max it times the kernel (handle's precision, `steps` Euler steps, representative
+ * parameters) with every admissible number of threads per sample (a power of two from
+ * the smallest that covers n_max up to 1024; the extra threads split the source loop)
+ * and stores the fastest per batch-size bucket in the handle.  out_threads (host, may be
+ * NULL) receives one entry per bucket.  Synchronous; allocates and frees temporary device
+ * memory; must not run during stream capture.  Untuned handles use a heuristic. */
+int swimmer_autotune(swimmer_handle *h, int steps, int *out_threads);
 
 /* Batched log-likelihood (Sec. 3.1, Eqs. likelihood/fitness with Sigma = sigma^2 I):
  *   loglik[b] = -(m/2) ln(2 pi sigma^2) - sum_o |D_o - head_o(theta_b)|^2 / (2 sigma^2),

@@ -293,3 +293,16 @@ def swimmer_profile(h: Handle, mode):
     out = (ctypes.c_double * 4)()
     check(lib().swimmer_profile(h.ptr, int(mode), out))
     return tuple(out) if mode == 2 else None
+
+
+def swimmer_autotune(h: Handle, steps=200):
+    """Time the forward kernel's launch shapes per batch-size bucket; returns
+    {batch size: threads per sample} for B = 1, 2, 4, ..., b_max."""
+    out = (ctypes.c_int * 17)()
+    check(lib().swimmer_autotune(h.ptr, int(steps), out))
+    res, B, k = {}, 1, 0
+    while B <= h.cfg.b_max:
+        res[B] = out[k]
+        B <<= 1
+        k += 1
+    return res

@@ -121,6 +121,7 @@ extern "C" int swimmer_init(const swimmer_config *cfg, swimmer_handle **out) {
     CUDA_TRY(cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device));
     const int B = cfg->b_max;
     ALLOC(h->tab64, (size_t)B * TAB64_STRIDE);
+    ALLOC(h->k1_scratch, (size_t)B * K1_SCRATCH);
     ALLOC(h->tab32, (size_t)B * TAB32_STRIDE);
     ALLOC(h->sp, B);
     ALLOC(h->order, B);
@@ -176,7 +177,7 @@ extern "C" int swimmer_init(const swimmer_config *cfg, swimmer_handle **out) {
 extern "C" int swimmer_destroy(swimmer_handle *h) {
     if (!h) return 0;
     cudaDeviceSynchronize();
-    void *ptrs[] = {h->tab64, h->tab32, h->sp, h->order, h->queue, h->speed_tmp, h->w, h->stats,
+    void *ptrs[] = {h->tab64, h->k1_scratch, h->tab32, h->sp, h->order, h->queue, h->speed_tmp, h->w, h->stats,
                     h->idx, h->counts, h->chain_id, h->chain_off, h->chain_len, h->aux,
                     h->cur_theta, h->cur_ll, h->cur_sl, h->prop_theta, h->prop_ll, h->prop_sl,
                     h->out_theta, h->out_ll, h->out_sl, h->prop_status, h->active, h->active2, h->cum, h->info, h->work,
@@ -205,7 +206,7 @@ extern "C" int swimmer_kernel_eval(swimmer_handle *h, double alpha, double delta
     ARG_CHECK(precision == SWIMMER_FP64 || precision == SWIMMER_FP32C, "precision must be 0 or 1");
     cudaStream_t s = (cudaStream_t)stream;
     int rc = launch_set_sample(h, alpha, delta, r_max, s);
-    if (!rc) rc = launch_table_build(h, 1, 1, s);
+    if (!rc) rc = launch_table_build(h, 1, precision == SWIMMER_FP64 ? 2 : 3, s);
     if (!rc && m > 0) rc = launch_kernel_eval(h, m, r, g1, g2, precision, s);
     return rc;
 }
@@ -224,6 +225,71 @@ int run_forward(swimmer_handle *h, int B, const double *theta, const int *n_pts,
     int rc = launch_prepare(h, B, theta, n_pts, s);
     if (!rc) rc = launch_table_build(h, B, h->cfg.precision == SWIMMER_FP64, s);
     if (!rc) rc = launch_forward(h, B, obs, sigma, loglik, head_traj, mean_speed, status, h->cfg.precision, s);
+    return rc;
+}
+
+// Autotuner: for batch sizes B = 1, 2, 4, ... up to b_max, time the forward kernel on
+// `steps` Euler steps with every admissible threads-per-sample and keep the fastest.
+extern "C" int swimmer_autotune(swimmer_handle *h, int steps, int *out_threads) {
+    ARG_CHECK(h != nullptr, "handle is NULL");
+    ARG_CHECK(steps >= 1, "steps must be >= 1");
+    const int bmax = h->cfg.b_max;
+    double *theta = nullptr;
+    int *status = nullptr;
+    CUDA_TRY(cudaMalloc((void **)&theta, sizeof(double) * 3 * bmax));
+    CUDA_TRY(cudaMalloc((void **)&status, sizeof(int) * bmax));
+    {
+        double *ht = (double *)malloc(sizeof(double) * 3 * bmax);
+        for (int b = 0; b < bmax; ++b) {
+            ht[3 * b] = 1.0 + 0.001 * (b % 17);
+            ht[3 * b + 1] = 0.0;
+            ht[3 * b + 2] = 0.1;
+        }
+        cudaMemcpy(theta, ht, sizeof(double) * 3 * bmax, cudaMemcpyHostToDevice);
+        free(ht);
+    }
+    const long long saved_steps = h->cfg.steps, saved_obs = h->cfg.obs_every;
+    h->cfg.steps = steps;
+    h->cfg.obs_every = steps;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    int rc = 0, k = 0;
+    const int prec = h->cfg.precision;
+    int T0 = 32;
+    while (T0 < h->cfg.n_max && T0 < 1024) T0 <<= 1;
+    if (T0 < 128) T0 = 128;
+    for (int B = 1; B <= bmax && !rc; B <<= 1, ++k) {
+        rc = launch_prepare(h, B, theta, nullptr, 0);
+        if (!rc) rc = launch_table_build(h, B, 1, 0);
+        float best = 1e30f;
+        int bestT = T0;
+        for (int T = T0; T <= 1024 && !rc; T <<= 1) {
+            float ms = 0.f;
+            for (int rep = 0; rep < 2 && !rc; ++rep) {  // first run warms up
+                cudaEventRecord(e0, 0);
+                rc = launch_forward(h, B, nullptr, 0.0, nullptr, nullptr, nullptr, status, prec, 0, T);
+                cudaEventRecord(e1, 0);
+                cudaEventSynchronize(e1);
+                cudaEventElapsedTime(&ms, e0, e1);
+            }
+            if (ms < best) {
+                best = ms;
+                bestT = T;
+            }
+        }
+        h->tune_threads[prec == SWIMMER_FP64 ? 0 : 1][k] = bestT;
+        if (out_threads) out_threads[k] = bestT;
+    }
+    // buckets beyond b_max keep the largest measured choice
+    for (int j = k; j < 17; ++j) h->tune_threads[prec == SWIMMER_FP64 ? 0 : 1][j] = h->tune_threads[prec == SWIMMER_FP64 ? 0 : 1][k > 0 ? k - 1 : 0];
+    h->cfg.steps = saved_steps;
+    h->cfg.obs_every = saved_obs;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(theta);
+    cudaFree(status);
+    CUDA_TRY(cudaDeviceSynchronize());
     return rc;
 }
 

@@ -15,15 +15,19 @@ constexpr int F64_SUB_LOG2 = 3;        // 8 panels per octave
 constexpr int F64_SUB = 1 << F64_SUB_LOG2;
 constexpr int F64_DEG = 9;             // Chebyshev degree 9 per panel (10 nodes)
 constexpr int F64_NODES = F64_DEG + 1;
-constexpr int F32_SUB_LOG2 = 4;        // 16 panels per octave
+constexpr int F32_SUB_LOG2 = 6;        // 64 panels per octave (quadratic)
 constexpr int F32_SUB = 1 << F32_SUB_LOG2;
 constexpr int F64_PANELS_MAX = N_OCT_MAX * F64_SUB;
 constexpr int F32_PANELS_MAX = N_OCT_MAX * F32_SUB;
 constexpr int NODES_MAX = F64_PANELS_MAX * F64_NODES;   // 1920
 // FP64 table per sample: [2][F64_PANELS_MAX][F64_NODES] Chebyshev coefficients
 constexpr int TAB64_STRIDE = 2 * F64_PANELS_MAX * F64_NODES;
-// FP32 table per sample: [2][F32_PANELS_MAX] float4 monomial cubic coefficients in f
-constexpr int TAB32_STRIDE = 2 * F32_PANELS_MAX;
+// FP32 table per sample (float4 units): part A [F32_PANELS_MAX] float4 = (g1 c0, g1 c1,
+// g1 c2, g2 c0) then part B [F32_PANELS_MAX] float2 = (g2 c1, g2 c2): monomial quadratic
+// coefficients in the local panel coordinate f in [0, 1)
+constexpr int TAB32_STRIDE = F32_PANELS_MAX + F32_PANELS_MAX / 2;
+constexpr int TAIL_MAX = 64;           // pieces of the integral of K0 phi s beyond the last node
+constexpr int K1_SCRATCH = 2 * NODES_MAX + TAIL_MAX;  // doubles of table-build scratch per sample
 constexpr double R_MAX_OVER_L = 1.25;  // table reach in units of the flagellum length
 constexpr double STRETCH_MAX = 0.20;   // segment stretch beyond which a run counts as diverged
 constexpr int N_PTS_MAX = 1024;
@@ -45,10 +49,13 @@ struct swimmer_handle {
     long long n_launch;
     ProfileEvents *prof;
     unsigned long long *work;  // device counter: pair evaluations executed by the forward kernel
+    // autotuned threads per sample for batch sizes in [2^k, 2^(k+1)), per precision; 0 = heuristic
+    int tune_threads[2][17];
     int device;
     int num_sms;
     // per-sample workspace (b_max samples)
     double *tab64;          // [b_max][TAB64_STRIDE]
+    double *k1_scratch;     // [b_max][K1_SCRATCH] interval integrals of the table build
     float4 *tab32;          // [b_max][TAB32_STRIDE]
     SampleParams *sp;       // [b_max]
     int *order;             // [b_max] processing order (longest first)
@@ -106,8 +113,11 @@ int launch_prepare(swimmer_handle *h, int B, const double *theta, const int *n_p
 int launch_table_build(swimmer_handle *h, int B, int need64, cudaStream_t s);
 int launch_forward(swimmer_handle *h, int B, const double *obs, double sigma, double *loglik,
                    double *head_traj, double *mean_speed, int *status, int precision,
-                   cudaStream_t s);
+                   cudaStream_t s, int threads_override = 0);
+int forward_threads(const swimmer_handle *h, int B, int precision);
 int launch_kernel_eval(swimmer_handle *h, int m, const double *r, double *g1, double *g2,
                        int precision, cudaStream_t s);
 int gl_init();
+// octaves the tables need for the largest sample a handle serves
+int handle_octaves(const swimmer_handle *h);
 int launch_set_sample(swimmer_handle *h, double alpha, double delta, double r_max, cudaStream_t s);

@@ -1,21 +1,27 @@
 // K2: fused persistent forward model + log-likelihood, one CTA per sample at a time.
 //
 // Per time step (Appendix, last paragraph; Sec. 2.1):
-//   A  segment vectors e_k = X_{k+1} - X_k (FP64 differences) and spring tension
-//      2 K_T (|e_k|/ds - 1)/|e_k| (Eq. EFT read as Hookean springs), with the strain taken
-//      from |e|^2/ds^2 - 1 in FP64 so that no cancellation reaches FP32;
-//   B  nonlinear curvature zeta_k (Eq. curva) from central differences, preferred
-//      curvature zeta^_k(t), and c_k d zeta_k / d X_{k-1,k,k+1} with c_k = 2 K_C ds (zeta - zeta^)
-//      (gradient of Eq. EFB);
+//   A  segment vectors e_k = X_{k+1} - X_k and spring tension 2 K_T (|e_k|/ds - 1)/|e_k|
+//      (Eq. EFT read as Hookean springs).  The strain comes from |e|^2/ds^2 - 1 evaluated
+//      without cancellation (FP64 in the FP64 kernel; error-free FP32 transformations on
+//      the double-float positions in the FP32 kernel);
+//   B  (same pass) nonlinear curvature zeta_k (Eq. curva) from central differences,
+//      preferred curvature zeta^_k(t), and c_k d zeta_k / d X_{k-1,k,k+1} with
+//      c_k = 2 K_C ds (zeta - zeta^) (gradient of Eq. EFB); the FP32 kernel uses the
+//      hardware reciprocal square root and, after reduction to [-pi, pi], sine/cosine;
 //   C  point forces F = -dE/dX (Eq. Fenergy) gathered from the stencils;
 //   D  Brinkmanlet pair sum (Eq. BrV) v_i = (1/mu) sum_j [-F_j g1 + (F_j . d) d g2]:
-//      sources (x, y, Fx, Fy) as one float4 / double4 per point in shared memory, the
-//      S threads of a target split the sources and combine with warp shuffles; g1, g2
-//      from the per-sample shared-memory table (cubic in FP32, Chebyshev degree 9 in FP64);
-//      FP32 partial sums of 32 sources are folded into a (hi, lo) pair by TwoSum
-//      (compensated accumulation);
-//   E  forward Euler X += dt v in FP64; every obs_every steps the head point is compared
-//      with the observations and the squared residual accumulated in FP64 (Eq. fitness).
+//      sources (x, y, Fx, Fy) as one float4 / 32-byte record per point in shared memory,
+//      stored twice in a row so that the diagonal walk needs no wrap test; target i meets
+//      source i + d at inner step d, so all lanes of a warp look up nearly the same table
+//      panel (|d| ds apart on a smooth filament) and the loads broadcast; the S threads of
+//      a target split the sources and combine with warp shuffles; g1, g2 from the
+//      per-sample shared-memory table (quadratic in F = 1 + f in FP32, Chebyshev degree 9 in
+//      FP64); FP32 partial sums of 32 sources are folded into a (hi, lo) pair by TwoSum;
+//   E  forward Euler X += dt v: FP64 positions in the FP64 kernel, double-float (hi + lo
+//      FP32, about 48 significant bits) positions updated by TwoSum in the FP32 kernel;
+//      every obs_every steps the head point is compared with the observations and the
+//      squared residual accumulated in FP64 (Eq. fitness).
 // A run stops early, with status DIVERGED, when a velocity is not finite, a point moves
 // more than ds in one step, or a segment stretches beyond STRETCH_MAX.
 #include <math.h>
@@ -45,6 +51,7 @@ struct FwdArgs {
     unsigned long long *work;
     int n_max;
     int threads;
+    int tab_panels;  // panels of the shared-memory table region (handle's octaves x panels/octave)
 };
 
 struct __align__(32) dbl4 {
@@ -64,42 +71,67 @@ struct Types<true> {
     typedef dbl4 R4;
 };
 
-__device__ __forceinline__ void two_sum(float &s, float &e, float b) {
-    float t = s + b;
-    float bp = t - s;
-    e += (s - (t - bp)) + (b - bp);
+// error-free transformations (Knuth TwoSum, Dekker Fast2Sum)
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+    s = a + b;
+    float bp = s - a;
+    e = (a - (s - bp)) + (b - bp);
+}
+__device__ __forceinline__ void fast_two_sum(float a, float b, float &s, float &e) {
+    s = a + b;
+    e = b - (s - a);
+}
+// compensated accumulation: (s, e) += b
+__device__ __forceinline__ void acc_two_sum(float &s, float &e, float b) {
+    float t, err;
+    two_sum(s, b, t, err);
+    e += err;
     s = t;
 }
 
+// table region in shared memory: FP32: float4 part A [P] then float2 part B [P];
+// FP64: Chebyshev coefficients of g1 [P][10] then of g2 [P][10]
 template <bool F64>
-__host__ __device__ size_t smem_bytes(int n_max) {
-    typedef typename Types<F64>::R R;
-    typedef typename Types<F64>::R4 R4;
-    size_t b = 2 * sizeof(double) * n_max + sizeof(R4) * n_max + 9 * sizeof(R) * n_max;
-    b = (b + 15) & ~size_t(15);
-    return b + (F64 ? sizeof(double) * TAB64_STRIDE : sizeof(float4) * TAB32_STRIDE);
+__host__ __device__ size_t table_bytes(int P) {
+    return F64 ? sizeof(double) * 2 * P * F64_NODES : (sizeof(float4) + sizeof(float2)) * P;
 }
 
-__device__ __forceinline__ void kern_f32(const float4 *__restrict__ t1, const float4 *__restrict__ t2, int pmax,
+// positions (16 B/point), sources (2 records/point), seg x/y, tension, 6 bending terms
+template <bool F64>
+__host__ __device__ size_t state_bytes(int n_max) {
+    typedef typename Types<F64>::R R;
+    typedef typename Types<F64>::R4 R4;
+    size_t b = 16 * (size_t)n_max + 2 * sizeof(R4) * n_max + 9 * sizeof(R) * n_max;
+    return (b + 31) & ~size_t(31);
+}
+
+template <bool F64>
+__host__ __device__ size_t smem_bytes(int n_max, int P) {
+    return state_bytes<F64>(n_max) + table_bytes<F64>(P);
+}
+
+// g1, g2 from the FP32 table: quadratic in F = 1 + f in [1, 2), the mantissa of u
+__device__ __forceinline__ void kern_f32(const float4 *__restrict__ tA, const float2 *__restrict__ tB, int pmax,
                                          float u, float &g1, float &g2) {
     unsigned bits = __float_as_uint(u);
     unsigned p = (bits >> (23 - F32_SUB_LOG2)) - (127u << F32_SUB_LOG2);
     p = min(p, (unsigned)pmax);
-    float f = __uint_as_float(0x3f800000u | ((bits << F32_SUB_LOG2) & 0x7fffffu)) - 1.0f;
-    float4 a = t1[p];
-    float4 c = t2[p];
-    g1 = fmaf(f, fmaf(f, fmaf(f, a.w, a.z), a.y), a.x);
-    g2 = fmaf(f, fmaf(f, fmaf(f, c.w, c.z), c.y), c.x);
+    float F = __uint_as_float(0x3f800000u | ((bits << F32_SUB_LOG2) & 0x7fffffu));
+    float4 a = tA[p];
+    float2 c = tB[p];
+    g1 = fmaf(F, fmaf(F, a.z, a.y), a.x);
+    g2 = fmaf(F, fmaf(F, c.y, c.x), a.w);
 }
 
-__device__ __forceinline__ void kern_f64(const double *__restrict__ tab, int pmax, double u, double &g1, double &g2) {
+__device__ __forceinline__ void kern_f64(const double *__restrict__ tab, int P, int pmax, double u, double &g1,
+                                         double &g2) {
     unsigned long long bits = (unsigned long long)__double_as_longlong(u);
     unsigned long long p = (bits >> (52 - F64_SUB_LOG2)) - (1023ull << F64_SUB_LOG2);
     if (p > (unsigned long long)pmax) p = pmax;
     double f = __longlong_as_double(0x3ff0000000000000LL | (long long)((bits << F64_SUB_LOG2) & 0x000fffffffffffffull)) - 1.0;
     double t = 2.0 * f - 1.0, t2 = 2.0 * t;
     const double *c1 = tab + p * F64_NODES;
-    const double *c2 = tab + (F64_PANELS_MAX + p) * F64_NODES;
+    const double *c2 = tab + ((size_t)P + p) * F64_NODES;
     double a1 = 0.0, a2 = 0.0, b1 = 0.0, b2 = 0.0;
 #pragma unroll
     for (int k = F64_DEG; k >= 1; --k) {
@@ -118,17 +150,18 @@ template <bool F64>
 __global__ void __launch_bounds__(1024) forward_kernel(FwdArgs a) {
     typedef typename Types<F64>::R R;
     typedef typename Types<F64>::R4 R4;
-    extern __shared__ __align__(16) unsigned char smraw[];
+    extern __shared__ __align__(32) unsigned char smraw[];
     const int n_max = a.n_max;
+    // positions: FP64 kernel sx, sy (double); FP32 kernel xh, xl, yh, yl (float)
     double *sx = (double *)smraw;
     double *sy = sx + n_max;
-    R4 *src = (R4 *)(sy + n_max);
-    R *segx = (R *)(src + n_max);
+    float *xh = (float *)smraw, *xl = xh + n_max, *yh = xl + n_max, *yl = yh + n_max;
+    R4 *src = (R4 *)(smraw + 16 * (size_t)n_max);  // [2 n_max]
+    R *segx = (R *)(src + 2 * n_max);
     R *segy = segx + n_max;
     R *tens = segy + n_max;
     R *bend = tens + n_max;  // [6][n_max]
-    size_t off = (2 * sizeof(double) * n_max + sizeof(R4) * n_max + 9 * sizeof(R) * n_max + 15) & ~size_t(15);
-    unsigned char *tabraw = smraw + off;
+    unsigned char *tabraw = smraw + state_bytes<F64>(n_max);
     __shared__ int s_work;
     __shared__ double s_red[32];
 
@@ -156,35 +189,49 @@ __global__ void __launch_bounds__(1024) forward_kernel(FwdArgs a) {
             continue;
         }
         // ---- table into shared memory
-        const int npan = p.n_oct * (F64 ? F64_SUB : F32_SUB);
+        const int P = a.tab_panels;
+        const int npan = min(P, p.n_oct * (F64 ? F64_SUB : F32_SUB));
         if (F64) {
             const double *g = a.tab64 + (size_t)b * TAB64_STRIDE;
             double *t = (double *)tabraw;
             for (int i = tid; i < npan * F64_NODES; i += T) {
                 t[i] = g[i];
-                t[F64_PANELS_MAX * F64_NODES + i] = g[F64_PANELS_MAX * F64_NODES + i];
+                t[(size_t)P * F64_NODES + i] = g[F64_PANELS_MAX * F64_NODES + i];
             }
         } else {
             const float4 *g = a.tab32 + (size_t)b * TAB32_STRIDE;
+            const float2 *gb = (const float2 *)(g + F32_PANELS_MAX);
             float4 *t = (float4 *)tabraw;
+            float2 *tb = (float2 *)(t + P);
             for (int i = tid; i < npan; i += T) {
                 t[i] = g[i];
-                t[F32_PANELS_MAX + i] = g[F32_PANELS_MAX + i];
+                tb[i] = gb[i];
             }
         }
-        // ---- initial straight filament X_k = (k ds, 0)
+        // ---- initial straight filament X_k = (k ds, 0), stored relative to (L/2, 0)
         const double ds = p.ds, L = p.length;
-        for (int k = tid; k < n; k += T) {
-            sx[k] = k * ds;
-            sy[k] = 0.0;
-        }
         const double xref = 0.5 * L;
+        for (int k = tid; k < n; k += T) {
+            double x0 = k * ds - xref;
+            if (F64) {
+                sx[k] = x0;
+                sy[k] = 0.0;
+            } else {
+                float h = (float)x0;
+                xh[k] = h;
+                xl[k] = (float)(x0 - (double)h);
+                yh[k] = 0.f;
+                yl[k] = 0.f;
+            }
+        }
         const double inv_ds2 = 1.0 / (ds * ds);
+        const float ds2_hi = (float)(ds * ds), ds2_lo = (float)(ds * ds - (double)ds2_hi);
         const R r_ds = (R)ds, r_inv2ds = (R)(0.5 / ds), r_invds2 = (R)inv_ds2;
         const R kt2 = (R)(2.0 * a.kt), kc2ds = (R)(2.0 * p.kc * ds);
         const R r_amp = (R)p.amp, r_eta = (R)a.eta, r_omega = (R)a.omega, r_L = (R)L;
         const R inv_d2 = (R)(1.0 / (p.delta * p.delta));
         const double dt_mu = a.dt / a.mu;
+        const float dt_mu_f = (float)dt_mu, ds_f = (float)ds;
         // thread -> (target slot, source split)
         int S = 1;
         while (S < 32 && 2 * S * n <= T) S <<= 1;
@@ -199,35 +246,84 @@ __global__ void __launch_bounds__(1024) forward_kernel(FwdArgs a) {
         for (long long step = 0; step < a.steps; ++step) {
             const R tR = (R)(step * a.dt);
             int bad = 0;
-            // ---- A: segments, tension, relative positions
+            // ---- A+B: segments, tension, curvature stencils, relative positions.  Thread k
+            //      forms e_k (tension of segment k) and again e_{k-1} (for the curvature at
+            //      k), which saves a barrier.
             for (int k = tid; k < n; k += T) {
-                if (k + 1 < n) {
-                    double ex = sx[k + 1] - sx[k], ey = sy[k + 1] - sy[k];
-                    double s2 = fma(fma(ex, ex, ey * ey), inv_ds2, -1.0);  // l^2/ds^2 - 1
-                    R s2r = (R)s2;
-                    R strain = s2r / ((R)1 + sqrt((R)1 + s2r));
-                    R ell = r_ds * ((R)1 + strain);
-                    segx[k] = (R)ex;
-                    segy[k] = (R)ey;
-                    tens[k] = kt2 * strain / ell;
-                    if (!(fabs((double)strain) <= STRETCH_MAX)) bad = 1;
+                R qx, qy, epx = 0, epy = 0, emx = 0, emy = 0;
+                if (F64) {
+                    if (k + 1 < n) {
+                        double ex = sx[k + 1] - sx[k], ey = sy[k + 1] - sy[k];
+                        double s2 = fma(fma(ex, ex, ey * ey), inv_ds2, -1.0);  // l^2/ds^2 - 1
+                        R strain = (R)(s2 / (1.0 + sqrt(1.0 + s2)));
+                        R ell = r_ds * ((R)1 + strain);
+                        epx = (R)ex;
+                        epy = (R)ey;
+                        tens[k] = kt2 * strain / ell;
+                        if (!(fabs((double)strain) <= STRETCH_MAX)) bad = 1;
+                    }
+                    if (k >= 1) {
+                        emx = (R)(sx[k] - sx[k - 1]);
+                        emy = (R)(sy[k] - sy[k - 1]);
+                    }
+                    qx = (R)sx[k];
+                    qy = (R)sy[k];
+                } else {
+                    float s, e, lo;
+                    if (k + 1 < n) {
+                        // e = X_{k+1} - X_k as a double-float (hi, lo)
+                        two_sum(xh[k + 1], -xh[k], s, e);
+                        float exh, exl;
+                        fast_two_sum(s, e + (xl[k + 1] - xl[k]), exh, exl);
+                        two_sum(yh[k + 1], -yh[k], s, e);
+                        float eyh, eyl;
+                        fast_two_sum(s, e + (yl[k + 1] - yl[k]), eyh, eyl);
+                        // |e|^2 - ds^2 without cancellation: exact squares of the hi parts
+                        float pxx = exh * exh, qxx = fmaf(exh, exh, -pxx);
+                        float pyy = eyh * eyh, qyy = fmaf(eyh, eyh, -pyy);
+                        float sp, spe;
+                        two_sum(pxx, pyy, sp, spe);
+                        float rest = ((spe + qxx + qyy) + 2.0f * (exh * exl + eyh * eyl)) - ds2_lo;
+                        float s2 = ((sp - ds2_hi) + rest) * (float)inv_ds2;  // l^2/ds^2 - 1
+                        float one = 1.0f + s2;
+                        float root = one * rsqrtf(one);                     // l/ds
+                        float strain = __fdividef(s2, 1.0f + root);        // l/ds - 1
+                        float ell = ds_f * (1.0f + strain);
+                        epx = (R)exh;
+                        epy = (R)eyh;
+                        tens[k] = (R)__fdividef((float)kt2 * strain, ell);
+                        if (!(fabsf(strain) <= (float)STRETCH_MAX)) bad = 1;
+                    }
+                    if (k >= 1) {
+                        two_sum(xh[k], -xh[k - 1], s, e);
+                        lo = e + (xl[k] - xl[k - 1]);
+                        emx = (R)(s + lo);
+                        two_sum(yh[k], -yh[k - 1], s, e);
+                        lo = e + (yl[k] - yl[k - 1]);
+                        emy = (R)(s + lo);
+                    }
+                    qx = (R)(xh[k] + xl[k]);
+                    qy = (R)(yh[k] + yl[k]);
                 }
-                R4 q;
-                q.x = (R)(sx[k] - xref);
-                q.y = (R)sy[k];
-                src[k] = q;
-            }
-            __syncthreads();
-            // ---- B: curvature stencils
-            for (int k = tid; k < n; k += T) {
+                if (k + 1 < n) {
+                    segx[k] = epx;
+                    segy[k] = epy;
+                }
+                src[k].x = qx;
+                src[k].y = qy;
+                src[k + n].x = qx;
+                src[k + n].y = qy;
                 if (k >= 1 && k + 1 < n) {
-                    R emx = segx[k - 1], emy = segy[k - 1], epx = segx[k], epy = segy[k];
                     R A = (emx + epx) * r_inv2ds, Bv = (emy + epy) * r_inv2ds;
                     R C = (epx - emx) * r_invds2, D = (epy - emy) * r_invds2;
                     R S2 = A * A + Bv * Bv;
-                    R rs = (R)1 / sqrt(S2);
+                    R rs;
+                    if (F64)
+                        rs = (R)(1.0 / sqrt((double)S2));
+                    else
+                        rs = (R)rsqrtf((float)S2);
                     R S15 = rs * rs * rs;
-                    R S25 = S15 / S2;
+                    R S25 = S15 * rs * rs;
                     R cross = A * D - Bv * C;
                     R zeta = cross * S15;
                     R s = (R)k * r_ds;
@@ -239,8 +335,11 @@ __global__ void __launch_bounds__(1024) forward_kernel(FwdArgs a) {
                         sn = (R)sd;
                         cs = (R)cd;
                     } else {
+                        // reduce to [-pi, pi], then the fast hardware approximation
+                        float pf = (float)ph;
+                        pf = fmaf(-6.28318530717958648f, rintf(pf * 0.159154943091895336f), pf);
                         float sf, cf;
-                        sincosf((float)ph, &sf, &cf);
+                        __sincosf(pf, &sf, &cf);
                         sn = (R)sf;
                         cs = (R)cf;
                     }
@@ -283,22 +382,26 @@ __global__ void __launch_bounds__(1024) forward_kernel(FwdArgs a) {
                 }
                 src[k].z = fx;
                 src[k].w = fy;
+                src[k + n].z = fx;
+                src[k + n].w = fy;
             }
             __syncthreads();
-            // ---- D: pair sum
+            // ---- D: pair sum along diagonals (source j = tgt + d, d = split, split + S, ...)
             double vxd = 0.0, vyd = 0.0;
+            float vxf = 0.f, vyf = 0.f;
             if (tgt < n) {
                 const R4 me = src[tgt];
                 const R xi = me.x, yi = me.y;
                 if (F64) {
                     const double *tab = (const double *)tabraw;
                     double vx = 0.0, vy = 0.0;
-                    for (int j = split; j < n; j += S) {
-                        R4 q = src[j];
+                    const R4 *sp = src + tgt + split;
+                    for (int d = split; d < n; d += S, sp += S) {
+                        R4 q = *sp;
                         double dx = (double)xi - (double)q.x, dy = (double)yi - (double)q.y;
                         double u = fma(fma(dx, dx, dy * dy), (double)inv_d2, 1.0);
                         double g1, g2;
-                        kern_f64(tab, npan - 1, u, g1, g2);
+                        kern_f64(tab, P, npan - 1, u, g1, g2);
                         double fd = fma((double)q.z, dx, (double)q.w * dy);
                         double wv = fd * g2;
                         vx = fma(wv, dx, fma(-(double)q.z, g1, vx));
@@ -308,16 +411,16 @@ __global__ void __launch_bounds__(1024) forward_kernel(FwdArgs a) {
                     vyd = vy;
                 } else {
                     const float4 *t1 = (const float4 *)tabraw;
-                    const float4 *t2 = t1 + F32_PANELS_MAX;
-                    const float4 *s4 = (const float4 *)src;
+                    const float2 *t2 = (const float2 *)(t1 + P);
+                    const float4 *sp = (const float4 *)src + tgt + split;
                     const float fxi = (float)xi, fyi = (float)yi, fid2 = (float)inv_d2;
                     float hx = 0.f, lx = 0.f, hy = 0.f, ly = 0.f;
-                    for (int j0 = split; j0 < n; j0 += S * CHUNK) {
+                    for (int d0 = split; d0 < n; d0 += S * CHUNK) {
                         float px = 0.f, py = 0.f;
-                        const int jend = min(n, j0 + S * CHUNK);
+                        const int dend = min(n, d0 + S * CHUNK);
 #pragma unroll 4
-                        for (int j = j0; j < jend; j += S) {
-                            float4 q = s4[j];
+                        for (int d = d0; d < dend; d += S, sp += S) {
+                            float4 q = *sp;
                             float dx = fxi - q.x, dy = fyi - q.y;
                             float u = fmaf(fmaf(dx, dx, dy * dy), fid2, 1.0f);
                             float g1, g2;
@@ -327,33 +430,61 @@ __global__ void __launch_bounds__(1024) forward_kernel(FwdArgs a) {
                             px = fmaf(wv, dx, fmaf(-q.z, g1, px));
                             py = fmaf(wv, dy, fmaf(-q.w, g1, py));
                         }
-                        two_sum(hx, lx, px);
-                        two_sum(hy, ly, py);
+                        acc_two_sum(hx, lx, px);
+                        acc_two_sum(hy, ly, py);
                     }
-                    vxd = (double)hx + (double)lx;
-                    vyd = (double)hy + (double)ly;
+                    vxf = hx + lx;
+                    vyf = hy + ly;
                 }
             }
             // combine the S source splits (lanes of one warp)
             for (int o = S >> 1; o >= 1; o >>= 1) {
-                vxd += __shfl_xor_sync(0xffffffffu, vxd, o);
-                vyd += __shfl_xor_sync(0xffffffffu, vyd, o);
+                if (F64) {
+                    vxd += __shfl_xor_sync(0xffffffffu, vxd, o);
+                    vyd += __shfl_xor_sync(0xffffffffu, vyd, o);
+                } else {
+                    vxf += __shfl_xor_sync(0xffffffffu, vxf, o);
+                    vyf += __shfl_xor_sync(0xffffffffu, vyf, o);
+                }
             }
-            // ---- E: Euler step (FP64), divergence, observations
+            // ---- E: Euler step, divergence, observations
             if (owner) {
-                double vx = vxd * dt_mu, vy = vyd * dt_mu;  // displacement this step
-                if (!isfinite(vx) || !isfinite(vy) || fmax(fabs(vx), fabs(vy)) > ds) bad = 1;
-                sx[tgt] += vx;
-                sy[tgt] += vy;
-                if (tgt == n - 1 && (step + 1) % a.obs_every == 0) {
+                const bool head_obs = (tgt == n - 1) && ((step + 1) % a.obs_every == 0);
+                double hxo = 0.0, hyo = 0.0;
+                if (F64) {
+                    double dx = vxd * dt_mu, dy = vyd * dt_mu;  // displacement this step
+                    if (!isfinite(dx) || !isfinite(dy) || fmax(fabs(dx), fabs(dy)) > ds) bad = 1;
+                    sx[tgt] += dx;
+                    sy[tgt] += dy;
+                    hxo = sx[tgt];
+                    hyo = sy[tgt];
+                } else {
+                    float dx = vxf * dt_mu_f, dy = vyf * dt_mu_f;
+                    if (!isfinite(dx) || !isfinite(dy) || fmaxf(fabsf(dx), fabsf(dy)) > ds_f) bad = 1;
+                    float s, e, nh, nl;
+                    two_sum(xh[tgt], dx, s, e);
+                    two_sum(s, xl[tgt] + e, nh, nl);
+                    xh[tgt] = nh;
+                    xl[tgt] = nl;
+                    two_sum(yh[tgt], dy, s, e);
+                    two_sum(s, yl[tgt] + e, nh, nl);
+                    yh[tgt] = nh;
+                    yl[tgt] = nl;
+                    if (head_obs) {
+                        hxo = (double)xh[tgt] + (double)xl[tgt];
+                        hyo = (double)yh[tgt] + (double)yl[tgt];
+                    }
+                }
+                if (head_obs) {
                     long long o = (step + 1) / a.obs_every - 1;
+                    hxo += xref;
                     if (a.obs) {
-                        double rx = a.obs[2 * o] - sx[tgt], ry = a.obs[2 * o + 1] - sy[tgt];
+                        double rx = a.obs[2 * o] - hxo, ry = a.obs[2 * o + 1] - hyo;
                         J = fma(rx, rx, fma(ry, ry, J));
                     }
                     if (a.head_traj) {
-                        a.head_traj[((size_t)b * n_obs + o) * 2] = sx[tgt];
-                        a.head_traj[((size_t)b * n_obs + o) * 2 + 1] = sy[tgt];
+                        a.head_traj[((size_t)b * n_obs + o) * 2] = hxo;
+                        a.head_traj[((size_t)b * n_obs + o) * 2 + 1] = hyo;
                     }
                 }
             }
@@ -366,14 +497,15 @@ __global__ void __launch_bounds__(1024) forward_kernel(FwdArgs a) {
         // ---- outputs
         if (a.speed) {
             double cx = 0.0;
-            for (int k = tid; k < n; k += T) cx += sx[k];
+            for (int k = tid; k < n; k += T) cx += F64 ? sx[k] : (double)xh[k] + (double)xl[k];
             for (int o = 16; o >= 1; o >>= 1) cx += __shfl_xor_sync(0xffffffffu, cx, o);
             if (lane == 0) s_red[tid >> 5] = cx;
             __syncthreads();
             if (tid == 0) {
                 double tot = 0.0;
                 for (int i = 0; i < (T + 31) / 32; ++i) tot += s_red[i];
-                a.speed[b] = status == SWIMMER_OK ? (tot / n - 0.5 * L) / (a.steps * a.dt) : nan("");
+                // the centroid starts at x = L/2, which is 0 in the stored coordinates
+                a.speed[b] = status == SWIMMER_OK ? (tot / n) / (a.steps * a.dt) : nan("");
             }
         }
         if (tid == 0) atomicAdd(a.work, (unsigned long long)n * (unsigned long long)n * (unsigned long long)steps_done);
@@ -397,8 +529,24 @@ __global__ void __launch_bounds__(1024) forward_kernel(FwdArgs a) {
 
 }  // namespace
 
+// Threads per sample: at least one per target; more (a source split of S = threads/n
+// lanes per target, combined by warp shuffles) when the batch is too small to fill the GPU,
+// so that the per-step latency of a lone sample shrinks.  The autotuned choice wins.
+int forward_threads(const swimmer_handle *h, int B, int precision) {
+    int bucket = 0;
+    while ((2 << bucket) <= B && bucket < 16) ++bucket;
+    int tuned = h->tune_threads[precision == SWIMMER_FP64 ? 0 : 1][bucket];
+    int T = 32;
+    while (T < h->cfg.n_max && T < 1024) T <<= 1;
+    if (T < 128) T = 128;
+    if (tuned >= T && tuned <= 1024) return tuned;
+    while (T < 1024 && (long long)B * T * 2 <= (long long)h->num_sms * 1024) T <<= 1;
+    return T;
+}
+
 int launch_forward(swimmer_handle *h, int B, const double *obs, double sigma, double *loglik,
-                   double *head_traj, double *mean_speed, int *status, int precision, cudaStream_t s) {
+                   double *head_traj, double *mean_speed, int *status, int precision, cudaStream_t s,
+                   int threads_override) {
     FwdArgs a;
     a.B = B;
     a.sp = h->sp;
@@ -421,12 +569,11 @@ int launch_forward(swimmer_handle *h, int B, const double *obs, double sigma, do
     a.status = status;
     a.work = h->work;
     a.n_max = h->cfg.n_max;
-    int T = 32;
-    while (T < h->cfg.n_max && T < 1024) T <<= 1;
-    if (T < 128) T = 128;
+    int T = threads_override > 0 ? threads_override : forward_threads(h, B, precision);
     a.threads = T;
     const bool f64 = precision == SWIMMER_FP64;
-    size_t smem = f64 ? smem_bytes<true>(a.n_max) : smem_bytes<false>(a.n_max);
+    a.tab_panels = handle_octaves(h) * (f64 ? F64_SUB : F32_SUB);
+    size_t smem = f64 ? smem_bytes<true>(a.n_max, a.tab_panels) : smem_bytes<false>(a.n_max, a.tab_panels);
     auto kern = f64 ? forward_kernel<true> : forward_kernel<false>;
     CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int per_sm = 0;

@@ -21,8 +21,8 @@
 // nodes, a warp prefix (A1) / suffix (C) sum and a geometric tail for C.
 //
 // Output per sample: FP64 Chebyshev coefficients (8 panels per octave of
-// u = 1 + r^2/delta^2, degree 9) and, derived from them, FP32 cubic coefficients in the
-// local panel coordinate f in [0, 1) (16 panels per octave).
+// u = 1 + r^2/delta^2, degree 9) and, derived from them, FP32 quadratic coefficients in
+// the mantissa F in [1, 2) of u (64 panels per octave).
 #include <math.h>
 #include <stdio.h>
 
@@ -33,8 +33,22 @@ namespace {
 constexpr double PI = 3.14159265358979323846;
 constexpr double EGAMMA = 0.57721566490153286061;
 constexpr int GL_N = 16;
-__constant__ double c_gl_x[GL_N];
+__constant__ double c_gl_x[GL_N];   // 16-point Gauss-Legendre on [-1, 1]
 __constant__ double c_gl_w[GL_N];
+__constant__ double c_gl8_x[8];     // 8-point rule (FP32 handles: the table only feeds FP32)
+__constant__ double c_gl8_w[8];
+constexpr int NSER = 160;
+__constant__ double c_inv_k[NSER];          // 1/k (index 0 unused)
+__constant__ double c_inv_kk[2][NSER];      // 1/((k+1)(k+1+nu)) for nu = 0, 2
+__constant__ double c_cheb_t[F64_NODES];    // ascending Chebyshev nodes of the FP64 panels
+__constant__ double c_dct[F64_NODES][F64_NODES];  // (2/n) cos(pi k (i + 1/2)/n), k = 0 halved
+// FP32 handles: the intermediate FP64 table needs only ~1e-9 (it feeds an FP32 table), so
+// its panels carry degree-5 series fitted at 6 nodes
+constexpr int LITE_NODES = 6;
+__constant__ double c_cheb_t6[LITE_NODES];
+__constant__ double c_dct6[LITE_NODES][LITE_NODES];
+__constant__ double c_node3[3];             // Chebyshev nodes for the FP32 quadratic fit
+__constant__ double c_dct3[3][3];
 
 // ---------------------------------------------------------------------------------
 // Bessel functions
@@ -43,20 +57,20 @@ __constant__ double c_gl_w[GL_N];
 __device__ double bessel_i(int nu, double x) {
     if (x <= 30.0) {
         double y = 0.25 * x * x;
-        double term = 1.0;
-        for (int m = 1; m <= nu; ++m) term /= m;  // 1/nu!
+        double term = nu == 0 ? 1.0 : 0.5;  // 1/nu!
+        const double *inv = c_inv_kk[nu == 0 ? 0 : 1];
         double s = 0.0;
-        for (int k = 0; k < 400; ++k) {
+        for (int k = 0; k < NSER; ++k) {
             s += term;
-            term *= y / ((k + 1.0) * (k + 1.0 + nu));
+            term *= y * inv[k];
             if (term < 1e-18 * s) break;
         }
         return s * (nu == 0 ? 1.0 : y);  // (x/2)^2 = y for nu = 2
     }
     double mu = 4.0 * nu * nu;
-    double s = 1.0, term = 1.0;
+    double s = 1.0, term = 1.0, inv8x = 0.125 / x;
     for (int k = 1; k < 60; ++k) {
-        double a = (mu - (2.0 * k - 1.0) * (2.0 * k - 1.0)) / (k * 8.0 * x);
+        double a = (mu - (2.0 * k - 1.0) * (2.0 * k - 1.0)) * c_inv_k[k] * inv8x;
         double nt = -term * a;
         if (fabs(nt) > fabs(term)) break;
         term = nt;
@@ -72,7 +86,7 @@ __device__ double bessel_i0m1(double x) {
     double y = 0.25 * x * x, term = y, s = 0.0;
     for (int k = 1; k < 60; ++k) {
         s += term;
-        term *= y / ((k + 1.0) * (k + 1.0));
+        term *= y * c_inv_kk[0][k];  // 1/((k+1)^2)
         if (term < 1e-18 * s) break;
     }
     return s;
@@ -87,9 +101,12 @@ __device__ void bessel_k01_scaled(double x, double *k0e, double *k1e) {
     double d = acos(1.0 - 1.0 / x);
     double h = d / 6.5;
     double s0 = 0.5, s1 = 0.5;
+    const double eh = exp(h), emh = 1.0 / eh;
+    double ep = 1.0, em = 1.0;  // e^{m h}, e^{-m h}
     for (int m = 1; m < 4000; ++m) {
-        double t = m * h;
-        double c = cosh(t);
+        ep *= eh;
+        em *= emh;
+        double c = 0.5 * (ep + em);  // cosh(m h)
         double e = exp(-x * (c - 1.0));
         s0 += e;
         s1 += e * c;
@@ -109,8 +126,8 @@ __device__ BesselSet bessel_set(double x) {
         // K0 = -lx I0 + sum_{k>=1} H_k y^k/(k!)^2
         double term = 1.0, hk = 0.0, tail = 0.0;
         for (int k = 1; k < 60; ++k) {
-            term *= y / ((double)k * k);
-            hk += 1.0 / k;
+            term *= y * c_inv_kk[0][k - 1];  // 1/k^2
+            hk += c_inv_k[k];
             tail += hk * term;
             if (term < 1e-19) break;
         }
@@ -121,9 +138,9 @@ __device__ BesselSet bessel_set(double x) {
         double hk0 = 0.0, hk2 = 1.5;  // H_0, H_2
         for (int k = 0; k < 60; ++k) {
             s += (lx - 0.5 * (hk0 + hk2)) * term;
-            term *= y / ((k + 1.0) * (k + 3.0));
-            hk0 += 1.0 / (k + 1.0);
-            hk2 += 1.0 / (k + 3.0);
+            term *= y * c_inv_kk[1][k];  // 1/((k+1)(k+3))
+            hk0 += c_inv_k[k + 1];
+            hk2 += c_inv_k[k + 3];
             if (term < 1e-20) break;
         }
         b.t2k2 = 0.5 + y * s;
@@ -143,7 +160,18 @@ __device__ BesselSet bessel_set(double x) {
 }
 
 __device__ double bessel_k0(double x) {
-    if (x <= 2.0) return bessel_set(x).k0;
+    if (x <= 2.0) {
+        // K0 = -(ln(x/2) + gamma) I0 + sum_{k>=1} H_k y^k/(k!)^2, y = x^2/4 (one pass)
+        double y = 0.25 * x * x, term = 1.0, i0 = 1.0, hk = 0.0, tail = 0.0;
+        for (int k = 1; k < 60; ++k) {
+            term *= y * c_inv_kk[0][k - 1];
+            hk += c_inv_k[k];
+            i0 += term;
+            tail += hk * term;
+            if (term < 1e-19 * i0) break;
+        }
+        return -(log(0.5 * x) + EGAMMA) * i0 + tail;
+    }
     double k0e, k1e;
     bessel_k01_scaled(x, &k0e, &k1e);
     return k0e * exp(-x);
@@ -164,31 +192,32 @@ __device__ double m0_closed(double r, double delta) {
 
 // int_a^b f(s) ds with f = (I0(alpha s)-1) phi s (which = 0) or K0(alpha s) phi s (which = 1),
 // split so that no piece is wider than 0.5/alpha or half the distance scale max(a, delta/4)
-__device__ double panel_integral(int which, double a, double b, double alpha, double delta) {
+__device__ double panel_integral(int which, double a, double b, double alpha, double delta, bool gl8) {
     if (b <= a) return 0.0;
     double w = b - a;
     int n = (int)ceil(fmax(alpha * w / 0.5, w / (0.5 * fmax(a, 0.25 * delta))));
     if (n < 1) n = 1;
     if (n > 4096) n = 4096;
+    const int ng = gl8 ? 8 : GL_N;
+    const double *gx = gl8 ? c_gl8_x : c_gl_x, *gw = gl8 ? c_gl8_w : c_gl_w;
     double hw = 0.5 * w / n, tot = 0.0;
     for (int p = 0; p < n; ++p) {
         double c = a + (2 * p + 1) * hw, acc = 0.0;
-        for (int g = 0; g < GL_N; ++g) {
-            double s = c + hw * c_gl_x[g];
+        for (int g = 0; g < ng; ++g) {
+            double s = c + hw * gx[g];
             double f = (which == 0 ? bessel_i0m1(alpha * s) : bessel_k0(alpha * s)) * blob(s, delta) * s;
-            acc += c_gl_w[g] * f;
+            acc += gw[g] * f;
         }
         tot += acc * hw;
     }
     return tot;
 }
 
-__device__ __forceinline__ double node_u(int m) {
-    // node m -> (octave, panel, ascending Chebyshev index)
-    int panel = m / F64_NODES, ii = m % F64_NODES;
+__device__ __forceinline__ double node_u(int m, int np) {
+    // node m -> (octave, panel, ascending Chebyshev index); np nodes per panel
+    int panel = m / np, ii = m % np;
     int e = panel >> F64_SUB_LOG2, j = panel & (F64_SUB - 1);
-    double t = -cos(PI * (ii + 0.5) / F64_NODES);  // ascending in ii
-    double f = 0.5 * (t + 1.0);
+    double f = 0.5 * ((np == F64_NODES ? c_cheb_t[ii] : c_cheb_t6[ii]) + 1.0);
     return ldexp(1.0 + (j + f) / F64_SUB, e);
 }
 
@@ -218,7 +247,7 @@ __global__ void prepare_kernel(int B, const double *__restrict__ theta, const in
     }
     p.ds = p.length / (p.n - 1);
     p.delta = cfg.delta_over_ds * p.ds;
-    double rho = R_MAX_OVER_L * p.length / p.delta;
+    double rho = R_MAX_OVER_L * (p.n - 1) / cfg.delta_over_ds;  // r_max/delta, as handle_octaves()
     int n_oct = (int)floor(log2(1.0 + rho * rho)) + 1;
     if (n_oct > N_OCT_MAX) {
         n_oct = N_OCT_MAX;
@@ -233,23 +262,79 @@ __global__ void prepare_kernel(int B, const double *__restrict__ theta, const in
 }
 
 // ---------------------------------------------------------------------------------
-// K1: one CTA per sample
+// K1a: interval integrals, one thread per node interval or tail piece (all samples)
 // ---------------------------------------------------------------------------------
 constexpr int K1_THREADS = 256;
+constexpr int K1A_THREADS = 128;
 
+__device__ __forceinline__ int node_count(const SampleParams &p, int NP, int max_oct) {
+    return min(p.n_oct, max_oct) * F64_SUB * NP;
+}
+
+// tail piece k beyond r_last: widths double from the blob scale up to 2/alpha, then stay;
+// the last piece ends at s_end.  Returns false when piece k does not exist.
+__device__ bool tail_piece(int k, double r_last, double s_end, double alpha, double delta, double *lo, double *hi) {
+    double s = r_last;
+    for (int i = 0; i < TAIL_MAX; ++i) {
+        if (s >= s_end) return false;
+        double w = fmin(fmax(s, 0.25 * delta), 2.0 / alpha);
+        double e = (i == TAIL_MAX - 1) ? s_end : fmin(s + w, s_end);
+        if (i == k) {
+            *lo = s;
+            *hi = e;
+            return true;
+        }
+        s = e;
+    }
+    return false;
+}
+
+__global__ void __launch_bounds__(K1A_THREADS)
+table_integrals_kernel(int B, const SampleParams *__restrict__ sp, double *__restrict__ scratch, int gl8,
+                       int max_oct) {
+    const int b = blockIdx.x;
+    const SampleParams p = sp[b];
+    if (p.status != SWIMMER_OK || !(p.alpha > 0.0)) return;
+    const int NP = gl8 ? LITE_NODES : F64_NODES;
+    const int M = node_count(p, NP, max_oct);
+    const int q = blockIdx.y * blockDim.x + threadIdx.x;
+    const double alpha = p.alpha, delta = p.delta;
+    double *IA = scratch + (size_t)b * K1_SCRATCH, *IC = IA + NODES_MAX, *IT = IC + NODES_MAX;
+    if (q < M) {
+        double r = delta * sqrt(node_u(q, NP) - 1.0);
+        double rprev = q ? delta * sqrt(node_u(q - 1, NP) - 1.0) : 0.0;
+        IA[q] = panel_integral(0, rprev, r, alpha, delta, gl8);
+        IC[q] = q + 1 < M ? panel_integral(1, r, delta * sqrt(node_u(q + 1, NP) - 1.0), alpha, delta, gl8) : 0.0;
+    } else if (q < M + TAIL_MAX) {
+        const int k = q - M;
+        double r_last = delta * sqrt(node_u(M - 1, NP) - 1.0);
+        double s_end = fmin(r_last + 60.0 / alpha, 1e6 * delta);
+        double lo, hi;
+        IT[k] = tail_piece(k, r_last, s_end, alpha, delta, &lo, &hi) ? panel_integral(1, lo, hi, alpha, delta, gl8) : 0.0;
+    }
+}
+
+// ---------------------------------------------------------------------------------
+// K1b: per sample (one CTA): prefix/suffix sums, node values, Chebyshev and FP32 fits
+// ---------------------------------------------------------------------------------
 __global__ void __launch_bounds__(K1_THREADS)
-table_build_kernel(int B, const SampleParams *__restrict__ sp, double *__restrict__ tab64,
-                   float4 *__restrict__ tab32) {
+table_build_kernel(int B, SampleParams *__restrict__ sp, const double *__restrict__ scratch,
+                   double *__restrict__ tab64, float4 *__restrict__ tab32, int gl8, int max_oct) {
     extern __shared__ double sm[];
     const int b = blockIdx.x;
     if (b >= B) return;
-    const SampleParams p = sp[b];
-    const int M = p.n_oct * F64_SUB * F64_NODES;
+    SampleParams p = sp[b];
+    if (p.n_oct > max_oct) {  // never beyond the shared-memory node arrays
+        p.n_oct = max_oct;
+        __syncthreads();
+        if (threadIdx.x == 0) sp[b].n_oct = max_oct;
+    }
+    const int NP = gl8 ? LITE_NODES : F64_NODES;  // nodes per FP64 panel
+    const int M = p.n_oct * F64_SUB * NP;
     double *nodeA = sm;            // [M] interval integrals -> A1 prefix
     double *nodeC = sm + M;        // [M] interval integrals -> C suffix
     double *g1s = sm + 2 * M;      // [M]
     double *g2s = sm + 3 * M;      // [M]
-    __shared__ double red[K1_THREADS];
     const int tid = threadIdx.x;
     const double alpha = p.alpha, delta = p.delta;
     const bool stokes = !(alpha > 0.0);
@@ -264,37 +349,17 @@ table_build_kernel(int B, const SampleParams *__restrict__ sp, double *__restric
     }
 
     if (!stokes) {
-        // interval integrals between consecutive nodes
-        double tail = 0.0;
+        const double *IA = scratch + (size_t)b * K1_SCRATCH, *IC = IA + NODES_MAX, *IT = IC + NODES_MAX;
         for (int m = tid; m < M; m += blockDim.x) {
-            double r = delta * sqrt(node_u(m) - 1.0);
-            double rprev = m ? delta * sqrt(node_u(m - 1) - 1.0) : 0.0;
-            nodeA[m] = panel_integral(0, rprev, r, alpha, delta);
-            if (m + 1 < M) nodeC[m] = panel_integral(1, r, delta * sqrt(node_u(m + 1) - 1.0), alpha, delta);
+            nodeA[m] = IA[m];
+            nodeC[m] = IC[m];
         }
-        // geometric tail beyond the last node, spread over the block, fixed-order reduction
-        {
-            double r_last = delta * sqrt(node_u(M - 1) - 1.0);
-            double s_end = fmin(r_last + 60.0 / alpha, 1e6 * delta);
-            // piece k covers [s_k, s_{k+1}], s_{k+1} = s_k + min(max(s_k, delta/4), 0.5/alpha)
-            // computed serially for boundaries (cheap), integrated in parallel
-            double acc = 0.0;
-            double s = r_last;
-            for (int k = 0; s < s_end && k < 100000; ++k) {
-                double w = fmin(fmax(s, 0.25 * delta), 0.5 / alpha);
-                double e = fmin(s + w, s_end);
-                if (k % blockDim.x == tid) acc += panel_integral(1, s, e, alpha, delta);
-                s = e;
-            }
-            red[tid] = acc;
-            __syncthreads();
-            for (int o = blockDim.x / 2; o > 0; o >>= 1) {
-                if (tid < o) red[tid] += red[tid + o];
-                __syncthreads();
-            }
-            tail = red[0];
+        __syncthreads();
+        if (tid == 0) {
+            double tail = 0.0;
+            for (int k = TAIL_MAX - 1; k >= 0; --k) tail += IT[k];  // far (small) pieces first
+            nodeC[M - 1] = tail;
         }
-        if (tid == 0) nodeC[M - 1] = tail;
         __syncthreads();
         // prefix (A1) and suffix (C) sums by warp 0: lanes own contiguous chunks
         if (tid < 32) {
@@ -328,7 +393,7 @@ table_build_kernel(int B, const SampleParams *__restrict__ sp, double *__restric
 
     // kernel function values at the nodes
     for (int m = tid; m < M; m += blockDim.x) {
-        double r = delta * sqrt(node_u(m) - 1.0);
+        double r = delta * sqrt(node_u(m, NP) - 1.0);
         double g1, g2;
         if (stokes) {
             stokes_g(r, delta, &g1, &g2);
@@ -351,52 +416,52 @@ table_build_kernel(int B, const SampleParams *__restrict__ sp, double *__restric
         int f = q / (np64 * F64_NODES);
         int rem = q % (np64 * F64_NODES);
         int panel = rem / F64_NODES, k = rem % F64_NODES;
-        const double *g = (f == 0 ? g1s : g2s) + panel * F64_NODES;
+        const double *g = (f == 0 ? g1s : g2s) + panel * NP;
         double s = 0.0;
-        for (int ii = 0; ii < F64_NODES; ++ii) {
-            int i = F64_NODES - 1 - ii;  // descending Chebyshev index of ascending node ii
-            s += g[ii] * cos(PI * k * (i + 0.5) / F64_NODES);
+        if (NP == F64_NODES) {
+            for (int ii = 0; ii < F64_NODES; ++ii) s += g[ii] * c_dct[k][ii];
+        } else if (k < LITE_NODES) {
+            for (int ii = 0; ii < LITE_NODES; ++ii) s += g[ii] * c_dct6[k][ii];
         }
-        s *= 2.0 / F64_NODES;
-        if (k == 0) s *= 0.5;
         t64[(f * F64_PANELS_MAX + panel) * F64_NODES + k] = s;
     }
     __syncthreads();
 
-    // FP32 cubic per half panel from the FP64 series (Chebyshev fit at 4 nodes, then
-    // monomial coefficients in f in [0, 1))
+    // FP32 quadratic per eighth of an FP64 panel from the FP64 series (Chebyshev fit at 3
+    // nodes, then monomial coefficients in f in [0, 1))
     const int np32 = p.n_oct * F32_SUB;
-    for (int q = tid; q < 2 * np32; q += blockDim.x) {
-        int f = q / np32, panel32 = q % np32;
-        int e = panel32 >> F32_SUB_LOG2, jj = panel32 & (F32_SUB - 1);
-        int panel64 = e * F64_SUB + (jj >> 1);
-        const double *c = t64 + (f * F64_PANELS_MAX + panel64) * F64_NODES;
-        double vals[4];
-        for (int i = 0; i < 4; ++i) {
-            double tl = cos(PI * (i + 0.5) / 4.0);        // in [-1, 1] of the FP32 panel
-            double f32 = 0.5 * (tl + 1.0);
-            double f64 = 0.5 * ((jj & 1) + f32);
-            double t = 2.0 * f64 - 1.0;
-            double b1 = 0.0, b2 = 0.0;
-            for (int k = F64_DEG; k >= 1; --k) {
-                double b0 = 2.0 * t * b1 - b2 + c[k];
-                b2 = b1;
-                b1 = b0;
+    constexpr int SPLIT = F32_SUB / F64_SUB;  // FP32 panels per FP64 panel
+    float2 *t32b = (float2 *)(t32 + F32_PANELS_MAX);
+    for (int q = tid; q < np32; q += blockDim.x) {
+        int e = q >> F32_SUB_LOG2, jj = q & (F32_SUB - 1);
+        int panel64 = e * F64_SUB + jj / SPLIT;
+        double cf[2][3];
+        for (int fn = 0; fn < 2; ++fn) {
+            const double *c = t64 + (fn * F64_PANELS_MAX + panel64) * F64_NODES;
+            double vals[3];
+            for (int i = 0; i < 3; ++i) {
+                double f32 = 0.5 * (c_node3[i] + 1.0);  // node of the FP32 panel
+                double f64 = ((jj % SPLIT) + f32) / SPLIT;
+                double t = 2.0 * f64 - 1.0;
+                double b1 = 0.0, b2 = 0.0;
+                for (int k = F64_DEG; k >= 1; --k) {
+                    double b0 = 2.0 * t * b1 - b2 + c[k];
+                    b2 = b1;
+                    b1 = b0;
+                }
+                vals[i] = t * b1 - b2 + c[0];
             }
-            vals[i] = t * b1 - b2 + c[0];
+            double a[3];
+            for (int k = 0; k < 3; ++k) a[k] = vals[0] * c_dct3[k][0] + vals[1] * c_dct3[k][1] + vals[2] * c_dct3[k][2];
+            // p(t) = a0 + a1 t + a2 (2 t^2 - 1), t = 2 f - 1 = 2 F - 3 with F = 1 + f the
+            // mantissa of u in [1, 2): p = c0 + c1 F + c2 F^2
+            const double m0 = a[0] - a[1] + a[2], m1 = 2.0 * a[1] - 8.0 * a[2], m2 = 8.0 * a[2];  // in f
+            cf[fn][0] = m0 - m1 + m2;
+            cf[fn][1] = m1 - 2.0 * m2;
+            cf[fn][2] = m2;
         }
-        double a[4];
-        for (int k = 0; k < 4; ++k) {
-            double s = 0.0;
-            for (int i = 0; i < 4; ++i) s += vals[i] * cos(PI * k * (i + 0.5) / 4.0);
-            a[k] = s * 0.5 * (k == 0 ? 0.5 : 1.0);
-        }
-        // p(t) = a0 + a1 T1 + a2 T2 + a3 T3, t = 2 f - 1
-        double c0 = a[0] - a[1] + a[2] - a[3];
-        double c1 = 2.0 * a[1] - 8.0 * a[2] + 18.0 * a[3];
-        double c2 = 8.0 * a[2] - 48.0 * a[3];
-        double c3 = 32.0 * a[3];
-        t32[f * F32_PANELS_MAX + panel32] = make_float4((float)c0, (float)c1, (float)c2, (float)c3);
+        t32[q] = make_float4((float)cf[0][0], (float)cf[0][1], (float)cf[0][2], (float)cf[1][0]);
+        t32b[q] = make_float2((float)cf[1][1], (float)cf[1][2]);
     }
 }
 
@@ -458,16 +523,45 @@ __global__ void kernel_eval_kernel(int m, const double *__restrict__ r, double *
             g1[i] = g2[i] = nan("");
             return;
         }
-        float f = __uint_as_float(0x3f800000u | ((bits << F32_SUB_LOG2) & 0x7fffffu)) - 1.0f;
-        float4 a = tab32[panel], c = tab32[F32_PANELS_MAX + panel];
-        g1[i] = fmaf(f, fmaf(f, fmaf(f, a.w, a.z), a.y), a.x);
-        g2[i] = fmaf(f, fmaf(f, fmaf(f, c.w, c.z), c.y), c.x);
+        float F = __uint_as_float(0x3f800000u | ((bits << F32_SUB_LOG2) & 0x7fffffu));
+        float4 a = tab32[panel];
+        float2 c = ((const float2 *)(tab32 + F32_PANELS_MAX))[panel];
+        g1[i] = fmaf(F, fmaf(F, a.z, a.y), a.x);
+        g2[i] = fmaf(F, fmaf(F, c.y, c.x), a.w);
     }
 }
 
 }  // namespace
 
-// Gauss-Legendre nodes/weights on [-1, 1] by Newton's method on P_16 (host, once).
+// Gauss-Legendre nodes/weights on [-1, 1] by Newton's method on P_n (host).
+static void gauss_legendre(int n, double *x, double *w) {
+    for (int i = 0; i < n; ++i) {
+        double z = cos(PI * (i + 0.75) / (n + 0.5)), dp = 1.0;
+        for (int it = 0; it < 100; ++it) {
+            double p0 = 1.0, p1 = z;
+            for (int k = 2; k <= n; ++k) {
+                double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+                p0 = p1;
+                p1 = p2;
+            }
+            dp = n * (z * p1 - p0) / (z * z - 1.0);
+            double dz = p1 / dp;
+            z -= dz;
+            if (fabs(dz) < 1e-16) break;
+        }
+        double p0 = 1.0, p1 = z;
+        for (int k = 2; k <= n; ++k) {
+            double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+            p0 = p1;
+            p1 = p2;
+        }
+        dp = n * (z * p1 - p0) / (z * z - 1.0);
+        x[i] = z;
+        w[i] = 2.0 / ((1.0 - z * z) * dp * dp);
+    }
+}
+
+// constant tables for the table builder (host, once)
 int gl_init() {
     static bool done = false;
     if (done) return 0;
@@ -501,8 +595,53 @@ int gl_init() {
     }
     CUDA_TRY(cudaMemcpyToSymbol(c_gl_x, x, sizeof(x)));
     CUDA_TRY(cudaMemcpyToSymbol(c_gl_w, w, sizeof(w)));
+    {
+        double x8[8], w8[8];
+        gauss_legendre(8, x8, w8);
+        CUDA_TRY(cudaMemcpyToSymbol(c_gl8_x, x8, sizeof(x8)));
+        CUDA_TRY(cudaMemcpyToSymbol(c_gl8_w, w8, sizeof(w8)));
+    }
+    double ik[NSER], ikk[2][NSER];
+    for (int k = 0; k < NSER; ++k) {
+        ik[k] = k ? 1.0 / k : 0.0;
+        ikk[0][k] = 1.0 / ((k + 1.0) * (k + 1.0));
+        ikk[1][k] = 1.0 / ((k + 1.0) * (k + 3.0));
+    }
+    CUDA_TRY(cudaMemcpyToSymbol(c_inv_k, ik, sizeof(ik)));
+    CUDA_TRY(cudaMemcpyToSymbol(c_inv_kk, ikk, sizeof(ikk)));
+    double ct[F64_NODES], dct[F64_NODES][F64_NODES];
+    for (int ii = 0; ii < F64_NODES; ++ii) {
+        int i = F64_NODES - 1 - ii;  // ascending node ii is Chebyshev index i
+        ct[ii] = cos(PI * (i + 0.5) / F64_NODES);
+        for (int k = 0; k < F64_NODES; ++k)
+            dct[k][ii] = (2.0 / F64_NODES) * cos(PI * k * (i + 0.5) / F64_NODES) * (k == 0 ? 0.5 : 1.0);
+    }
+    CUDA_TRY(cudaMemcpyToSymbol(c_cheb_t, ct, sizeof(ct)));
+    CUDA_TRY(cudaMemcpyToSymbol(c_dct, dct, sizeof(dct)));
+    double ct6[LITE_NODES], dct6[LITE_NODES][LITE_NODES];
+    for (int ii = 0; ii < LITE_NODES; ++ii) {
+        int i = LITE_NODES - 1 - ii;
+        ct6[ii] = cos(PI * (i + 0.5) / LITE_NODES);
+        for (int k = 0; k < LITE_NODES; ++k)
+            dct6[k][ii] = (2.0 / LITE_NODES) * cos(PI * k * (i + 0.5) / LITE_NODES) * (k == 0 ? 0.5 : 1.0);
+    }
+    CUDA_TRY(cudaMemcpyToSymbol(c_cheb_t6, ct6, sizeof(ct6)));
+    CUDA_TRY(cudaMemcpyToSymbol(c_dct6, dct6, sizeof(dct6)));
+    double n3[3], d3[3][3];
+    for (int i = 0; i < 3; ++i) {
+        n3[i] = cos(PI * (i + 0.5) / 3.0);
+        for (int k = 0; k < 3; ++k) d3[k][i] = (2.0 / 3.0) * cos(PI * k * (i + 0.5) / 3.0) * (k == 0 ? 0.5 : 1.0);
+    }
+    CUDA_TRY(cudaMemcpyToSymbol(c_node3, n3, sizeof(n3)));
+    CUDA_TRY(cudaMemcpyToSymbol(c_dct3, d3, sizeof(d3)));
     done = true;
     return 0;
+}
+
+int handle_octaves(const swimmer_handle *h) {
+    double rho = R_MAX_OVER_L * (h->cfg.n_max - 1) / h->cfg.delta_over_ds;  // r_max/delta
+    int n_oct = (int)floor(log2(1.0 + rho * rho)) + 1;
+    return n_oct > N_OCT_MAX ? N_OCT_MAX : n_oct;
 }
 
 int launch_prepare(swimmer_handle *h, int B, const double *theta, const int *n_pts, cudaStream_t s) {
@@ -513,16 +652,24 @@ int launch_prepare(swimmer_handle *h, int B, const double *theta, const int *n_p
 }
 
 int launch_table_build(swimmer_handle *h, int B, int need64, cudaStream_t s) {
-    (void)need64;
-    size_t smem = 4 * (size_t)NODES_MAX * sizeof(double);
+    // node arrays for the handle's octaves (kernel_eval may need the full range)
+    // need64: 0 = FP32 handle build, 1 = FP64 build, 2/3 = the same over the full range
+    const int oct = need64 >= 2 ? N_OCT_MAX : handle_octaves(h);
+    const bool lite = need64 == 0 || need64 == 3;
+    const int M = oct * F64_SUB * (lite ? LITE_NODES : F64_NODES);
+    size_t smem = 4 * (size_t)M * sizeof(double);
     static bool attr = false;
     if (!attr) {
-        CUDA_TRY(cudaFuncSetAttribute(table_build_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        CUDA_TRY(cudaFuncSetAttribute(table_build_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)(4 * (size_t)NODES_MAX * sizeof(double))));
         attr = true;
     }
-    table_build_kernel<<<B, K1_THREADS, smem, s>>>(B, h->sp, h->tab64, h->tab32);
+    dim3 ga(B, (M + TAIL_MAX + K1A_THREADS - 1) / K1A_THREADS);
+    table_integrals_kernel<<<ga, K1A_THREADS, 0, s>>>(B, h->sp, h->k1_scratch, lite ? 1 : 0, oct);
     CUDA_TRY(cudaGetLastError());
-    prof_count(h, 1);
+    table_build_kernel<<<B, K1_THREADS, smem, s>>>(B, h->sp, h->k1_scratch, h->tab64, h->tab32, lite ? 1 : 0, oct);
+    CUDA_TRY(cudaGetLastError());
+    prof_count(h, 2);
     return 0;
 }
 
