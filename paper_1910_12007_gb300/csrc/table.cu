@@ -561,10 +561,17 @@ static void gauss_legendre(int n, double *x, double *w) {
     }
 }
 
-// constant tables for the table builder (host, once)
+// constant tables for the table builder (host; constant memory is per device, so once
+// per device)
 int gl_init() {
-    static bool done = false;
-    if (done) return 0;
+    static bool done[256] = {};
+    int dev = 0;
+    CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 256) {
+        set_error("device ordinal %d out of range", dev);
+        return SWIMMER_E_ARG;
+    }
+    if (done[dev]) return 0;
     double x[GL_N], w[GL_N];
     for (int i = 0; i < GL_N; ++i) {
         double z = cos(PI * (i + 0.75) / (GL_N + 0.5));
@@ -634,7 +641,7 @@ int gl_init() {
     }
     CUDA_TRY(cudaMemcpyToSymbol(c_node3, n3, sizeof(n3)));
     CUDA_TRY(cudaMemcpyToSymbol(c_dct3, d3, sizeof(d3)));
-    done = true;
+    done[dev] = true;
     return 0;
 }
 
@@ -658,12 +665,8 @@ int launch_table_build(swimmer_handle *h, int B, int need64, cudaStream_t s) {
     const bool lite = need64 == 0 || need64 == 3;
     const int M = oct * F64_SUB * (lite ? LITE_NODES : F64_NODES);
     size_t smem = 4 * (size_t)M * sizeof(double);
-    static bool attr = false;
-    if (!attr) {
-        CUDA_TRY(cudaFuncSetAttribute(table_build_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)(4 * (size_t)NODES_MAX * sizeof(double))));
-        attr = true;
-    }
+    CUDA_TRY(cudaFuncSetAttribute(table_build_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)(4 * (size_t)NODES_MAX * sizeof(double))));
     dim3 ga(B, (M + TAIL_MAX + K1A_THREADS - 1) / K1A_THREADS);
     table_integrals_kernel<<<ga, K1A_THREADS, 0, s>>>(B, h->sp, h->k1_scratch, lite ? 1 : 0, oct);
     CUDA_TRY(cudaGetLastError());
