@@ -95,6 +95,24 @@ int swimmer_profile(swimmer_handle *h, int mode, double *out);
 int swimmer_kernel_eval(swimmer_handle *h, double alpha, double delta, double r_max, int m,
                         const double *r, double *g1, double *g2, int precision, void *stream);
 
+/* Allocation-free variant of swimmer_kernel_eval, for callers that cannot allocate device
+ * memory (for example code running while another component's stream capture is open, where
+ * allocation fails, or services whose device-memory budget is fixed at start-up).  No
+ * handle: the table build of the one sample runs on scratch held in file-scope device
+ * arrays (about 98 KB, kept by every GPU that loads the library until the process exits).
+ * The paper has no counterpart; this is an interface convenience.
+ *   - Same arguments and results as swimmer_kernel_eval; r, g1, g2 stay caller-owned.
+ *   - Limit: r_max/delta < 4000 (24 octaves of u), alpha * r_max <= 600; larger sizes are
+ *     rejected with SWIMMER_E_ARG and a message.
+ *   - Allocates nothing (no cudaMalloc, cudaFree or allocating library routine).
+ *   - The first call on a device does a one-time set-up on that device (device addresses of
+ *     the arrays, constant tables, kernel attributes); make that first call before any
+ *     stream capture.
+ *   - Every call on a device shares the arrays, which keep the last call's contents; calls
+ *     that overlap on the GPU (different streams, no ordering) race and give wrong results. */
+int swimmer_kernel_eval_noalloc(double alpha, double delta, double r_max, int m, const double *r,
+                                double *g1, double *g2, int precision, void *stream);
+
 /* Batched forward model (Sec. 2; Appendix): for each sample b, B in 1..b_max,
  *   theta[b*3 + 0..2]   (alpha, log10 K_C, a),
  *   n_pts[b]            points (3..n_max) or n_pts == NULL for n_max everywhere,

@@ -306,3 +306,16 @@ def swimmer_autotune(h: Handle, steps=200):
         B <<= 1
         k += 1
     return res
+
+
+def swimmer_kernel_eval_noalloc(alpha, delta, r_max, r: torch.Tensor, precision=FP64, g1=None, g2=None,
+                                stream=None):
+    """Like swimmer_kernel_eval, without a handle: the library allocates nothing (its scratch
+    is static device memory shared by all calls on the device).  Pass preallocated g1/g2
+    to keep the whole call allocation-free on the Python side too."""
+    _dev(r, torch.float64)
+    g1 = torch.empty_like(r) if g1 is None else g1
+    g2 = torch.empty_like(r) if g2 is None else g2
+    check(lib().swimmer_kernel_eval_noalloc(float(alpha), float(delta), float(r_max), r.numel(), _ptr(r),
+                                            _ptr(g1), _ptr(g2), int(precision), _stream(stream)))
+    return g1, g2

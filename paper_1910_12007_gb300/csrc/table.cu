@@ -26,6 +26,8 @@
 #include <math.h>
 #include <stdio.h>
 
+#include <mutex>
+
 #include "common.cuh"
 
 namespace {
@@ -686,5 +688,83 @@ int launch_kernel_eval(swimmer_handle *h, int m, const double *r, double *g1, do
                        int precision, cudaStream_t s) {
     kernel_eval_kernel<<<(m + 127) / 128, 128, 0, s>>>(m, r, g1, g2, h->sp, h->tab64, h->tab32, precision);
     CUDA_TRY(cudaGetLastError());
+    return 0;
+}
+
+// ---------------------------------------------------------------------------------
+// Allocation-free kernel-function evaluation
+// ---------------------------------------------------------------------------------
+// Some callers may not allocate device memory at all: code that runs while someone else's
+// stream capture is open (allocation inside a capture region fails), or services that fix
+// their device-memory budget at start-up and must not grow it per request.  For them the
+// table build of one sample (the kernels above that use scratch memory) runs on scratch
+// that lives in file-scope device arrays: every GPU that loads this library holds these
+// ~98 KB until the process exits, and every call on a device shares them.
+namespace {
+__device__ __align__(256) double g_noalloc_scratch[K1_SCRATCH];
+__device__ __align__(256) double g_noalloc_tab64[TAB64_STRIDE];
+__device__ __align__(256) float4 g_noalloc_tab32[TAB32_STRIDE];
+__device__ __align__(256) SampleParams g_noalloc_sp[1];
+
+struct NoallocPtrs {
+    double *scratch, *tab64;
+    float4 *tab32;
+    SampleParams *sp;
+    bool ready;
+};
+NoallocPtrs g_noalloc[256];
+std::mutex g_noalloc_mutex;
+
+// once per device, with that device current: the device addresses of the arrays (their names
+// are host-side stand-ins in host code), constant tables and kernel attributes
+int noalloc_setup(int dev, NoallocPtrs *out) {
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    NoallocPtrs &p = g_noalloc[dev];
+    if (!p.ready) {
+        int rc = gl_init();
+        if (rc) return rc;
+        CUDA_TRY(cudaGetSymbolAddress((void **)&p.scratch, g_noalloc_scratch));
+        CUDA_TRY(cudaGetSymbolAddress((void **)&p.tab64, g_noalloc_tab64));
+        CUDA_TRY(cudaGetSymbolAddress((void **)&p.tab32, g_noalloc_tab32));
+        CUDA_TRY(cudaGetSymbolAddress((void **)&p.sp, g_noalloc_sp));
+        CUDA_TRY(cudaFuncSetAttribute(table_build_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)(4 * (size_t)NODES_MAX * sizeof(double))));
+        p.ready = true;
+    }
+    *out = p;
+    return 0;
+}
+}  // namespace
+
+extern "C" int swimmer_kernel_eval_noalloc(double alpha, double delta, double r_max, int m, const double *r,
+                                           double *g1, double *g2, int precision, void *stream) {
+    ARG_CHECK(m >= 0, "m must be >= 0");
+    ARG_CHECK(m == 0 || (r && g1 && g2), "r, g1, g2 must be device pointers");
+    ARG_CHECK(alpha >= 0.0 && delta > 0.0 && r_max > 0.0, "need alpha >= 0, delta > 0, r_max > 0");
+    ARG_CHECK(r_max / delta < 4000.0, "r_max/delta = %g beyond the maximum 4000 of the static tables",
+              r_max / delta);
+    ARG_CHECK(alpha * r_max <= X_MAX, "alpha * r_max beyond %g", X_MAX);
+    ARG_CHECK(precision == SWIMMER_FP64 || precision == SWIMMER_FP32C, "precision must be 0 or 1");
+    int dev = 0;
+    CUDA_TRY(cudaGetDevice(&dev));
+    ARG_CHECK(dev >= 0 && dev < 256, "device ordinal %d out of range", dev);
+    NoallocPtrs p;
+    int rc = noalloc_setup(dev, &p);
+    if (rc) return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    const bool lite = precision != SWIMMER_FP64;  // as FP32 handles build their table
+    const int M = N_OCT_MAX * F64_SUB * (lite ? LITE_NODES : F64_NODES);
+    set_sample_kernel<<<1, 1, 0, s>>>(p.sp, alpha, delta, r_max);
+    CUDA_TRY(cudaGetLastError());
+    dim3 ga(1, (M + TAIL_MAX + K1A_THREADS - 1) / K1A_THREADS);
+    table_integrals_kernel<<<ga, K1A_THREADS, 0, s>>>(1, p.sp, p.scratch, lite ? 1 : 0, N_OCT_MAX);
+    CUDA_TRY(cudaGetLastError());
+    table_build_kernel<<<1, K1_THREADS, 4 * (size_t)M * sizeof(double), s>>>(1, p.sp, p.scratch, p.tab64, p.tab32,
+                                                                           lite ? 1 : 0, N_OCT_MAX);
+    CUDA_TRY(cudaGetLastError());
+    if (m > 0) {
+        kernel_eval_kernel<<<(m + 127) / 128, 128, 0, s>>>(m, r, g1, g2, p.sp, p.tab64, p.tab32, precision);
+        CUDA_TRY(cudaGetLastError());
+    }
     return 0;
 }
