@@ -115,8 +115,10 @@ class ClockSampler:
 
 
 def kernel_traffic():
-    """DRAM bytes per forward-kernel launch from the committed ncu summary, if it was
-    captured on the current kernel source (else None)."""
+    """DRAM bytes per forward run (sample) of the forward kernel from the committed ncu
+    summary, if it was captured on the current kernel source (else None).  The kernel's DRAM
+    traffic is the per-sample table plus the observation rows: it scales with the samples a
+    launch processes, not with the time steps."""
     src = os.path.join(ROOT, "paper_1910_12007_gb300", "csrc", "forward.cu")
     path = os.path.join(ROOT, "profiles", "forward_kernel_traffic.json")
     try:
@@ -126,7 +128,7 @@ def kernel_traffic():
             rec = json.load(f)
         if rec.get("forward_cu_sha256") != digest:
             return None
-        return rec["dram_bytes_per_pair_eval"]
+        return rec["dram_bytes_per_sample"]
     except Exception:
         return None
 
@@ -369,7 +371,8 @@ def main():
             "gpu_launches": int(launches),
             "roofline": {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
                          "frac": achieved / fp32_peak,
-                         "traffic": (traffic_pp * pairs / max(k2_launches, 1)) if traffic_pp else None,
+                         "traffic": (traffic_pp * pairs / (N_PTS * N_PTS * STEPS) / max(k2_launches, 1))
+                         if traffic_pp else None,
                          "kernel": "forward_kernel<fp32c>" if prec == g.FP32C else "forward_kernel<fp64>",
                          "launches": int(k2_launches), "avg_launch_ms": k2_avg_ms,
                          "peak_note": f"FP32 {sm_count} SMs x 128 lanes x 2 x {max_mhz:.0f} MHz ({peak_src} max clock)"},

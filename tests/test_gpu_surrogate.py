@@ -1,0 +1,86 @@
+"""The learned surrogate end to end on the GPU: trained by the library's own MLP kernels on
+forward runs the forward kernel generates, then used as a delayed-acceptance screen inside
+TMCMC.  Delayed acceptance keeps the exact target, so the posterior must agree with plain
+TMCMC; the gain is the number of exact forward-model runs it saves."""
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import synthetic
+
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+import paper_1910_12007_gb300 as g  # noqa: E402
+from paper_1910_12007_gb300 import surrogate as sg  # noqa: E402
+
+DEV = torch.device("cuda:0")
+LO = (0.0, -1.0, 0.05)
+HI = (10.0, 1.0, 0.2)
+TRUTH = (1.0, 0.0, 0.1)
+
+
+def _cfg(b_max):
+    return g.SwimmerConfig(n_max=12, b_max=b_max, length=1.0, dt=2e-4, steps=4000, obs_every=100,
+                           precision=g.FP32C)
+
+
+@pytest.fixture(scope="module")
+def trained():
+    h = g.swimmer_init(_cfg(1024))
+    th_train = torch.tensor(synthetic.prior_samples(31, LO, HI, 6144), device=DEV)
+    sur = sg.train(h, th_train, LO, HI, epochs=120, batch=512, lr=2e-3, seed=3)
+    th_val = torch.tensor(synthetic.prior_samples(32, LO, HI, 512), device=DEV)
+    traj, status = sg.generate_training_set(h, th_val)
+    err = sg.validation_error(sur, traj, th_val, status)
+    h.close()
+    return sur, err
+
+
+def test_surrogate_learns_the_forward_model(trained):
+    sur, err = trained
+    assert sur.losses[-1] < 0.05 * sur.losses[0]
+    # relative to the spread of the head trajectories over the prior
+    assert err < 0.08, err
+
+
+def _run(sur, use_surrogate, B=512, seed=11):
+    cfg = _cfg(B)
+    h = g.swimmer_init(cfg)
+    truth_traj, _, _ = g.forward_batch(h, torch.tensor([TRUTH], device=DEV))
+    xi = truth_traj[0].cpu().numpy()
+    sigma = 0.05 * float(np.mean(np.abs(xi)))
+    D = xi + sigma * synthetic.normals(1234, synthetic.NOISE, 0, xi.size).reshape(xi.shape)
+    obs = torch.tensor(D, device=DEV)
+    if use_surrogate:
+        sur.attach(h)
+    th0 = torch.tensor(synthetic.prior_samples(seed, LO, HI, B), device=DEV)
+    log = []
+    st = g.tmcmc_run(h, th0, obs, sigma, LO, HI, lambda j: synthetic.stage_randoms(seed, j, B, 3),
+                     use_surrogate=use_surrogate, log=log)
+    torch.cuda.synchronize()
+    out = st.theta.cpu().numpy(), log
+    h.close()
+    return out
+
+
+def test_delayed_acceptance_matches_plain_and_saves_forward_runs(trained):
+    sur, _ = trained
+    th_plain, log_plain = _run(sur, False)
+    th_da, log_da = _run(sur, True)
+    assert log_plain[-1]["q"] == 1.0 and log_da[-1]["q"] == 1.0
+    m_p, s_p = th_plain.mean(0), th_plain.std(0)
+    m_d, s_d = th_da.mean(0), th_da.std(0)
+    # same target: moments agree to Monte-Carlo accuracy of two correlated 512-sample runs
+    assert np.all(np.abs(m_d - m_p) <= 0.02 * np.abs(m_p) + 0.5 * s_p), (m_d, m_p, s_p)
+    assert np.all(np.abs(s_d - s_p) <= 0.5 * s_p), (s_d, s_p)
+    exact_plain = sum(s["n_exact"] for s in log_plain)
+    exact_da = sum(s["n_exact"] for s in log_da)
+    screened = sum(s["n_screened"] for s in log_da)
+    assert screened > 0
+    assert exact_da < 0.8 * exact_plain, (exact_da, exact_plain)
