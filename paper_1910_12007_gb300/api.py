@@ -319,3 +319,38 @@ def swimmer_kernel_eval_noalloc(alpha, delta, r_max, r: torch.Tensor, precision=
     check(lib().swimmer_kernel_eval_noalloc(float(alpha), float(delta), float(r_max), r.numel(), _ptr(r),
                                             _ptr(g1), _ptr(g2), int(precision), _stream(stream)))
     return g1, g2
+
+
+class ForwardGraph:
+    """``forward_batch`` (or ``loglik_batch`` when ``obs`` is given) captured once in a CUDA
+    graph and replayed: the table build, the work-queue reset and the persistent forward
+    launch become one graph launch.  Write new parameters into ``self.theta`` (and sizes
+    into ``self.n_pts``) in place, then ``replay()``; results land in the tensors of
+    ``self.out``.  Capture happens after one eager call, so one-time set-up never runs
+    inside the capture."""
+
+    def __init__(self, h: Handle, theta, n_pts=None, want_traj=False, obs=None, sigma=None):
+        self.h = h
+        self.theta = theta.clone()
+        self.n_pts = n_pts.clone() if n_pts is not None else None
+        B = theta.shape[0]
+        dev = theta.device
+        if obs is None:
+            traj = torch.empty((B, h.cfg.n_obs, 2), dtype=torch.float64, device=dev) if want_traj else None
+            self.out = (traj, torch.empty(B, dtype=torch.float64, device=dev),
+                        torch.empty(B, dtype=torch.int32, device=dev))
+            call = lambda: forward_batch(h, self.theta, self.n_pts, want_traj, out=self.out)
+        else:
+            self.obs = obs
+            self.out = (torch.empty(B, dtype=torch.float64, device=dev), torch.empty(B, dtype=torch.int32, device=dev))
+            call = lambda: loglik_batch(h, self.theta, obs, sigma, n_pts=self.n_pts, out=self.out)
+        call()
+        torch.cuda.synchronize()
+        self.graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(self.graph):
+            call()
+        torch.cuda.synchronize()
+
+    def replay(self):
+        self.graph.replay()
+        return self.out

@@ -263,6 +263,39 @@ __global__ void prepare_kernel(int B, const double *__restrict__ theta, const in
     order[b] = b;
 }
 
+// Longest-first processing order for batches of uneven size (largest n first, the classic
+// LPT rule for the persistent work queue): counting sort by n in one CTA.  Samples with a
+// bad status go last (they do no work).
+constexpr int SORT_THREADS = 1024;
+__global__ void __launch_bounds__(SORT_THREADS) order_kernel(int B, const SampleParams *__restrict__ sp,
+                                                           int *__restrict__ order) {
+    __shared__ int cnt[N_PTS_MAX + 2];
+    __shared__ int start[N_PTS_MAX + 2];
+    const int tid = threadIdx.x;
+    for (int i = tid; i < N_PTS_MAX + 2; i += SORT_THREADS) cnt[i] = 0;
+    __syncthreads();
+    // key: bucket N_PTS_MAX + 1 - n for good samples (descending n), bucket N_PTS_MAX + 1 last
+    for (int b = tid; b < B; b += SORT_THREADS) {
+        const SampleParams p = sp[b];
+        int key = p.status == SWIMMER_OK ? N_PTS_MAX + 1 - min(max(p.n, 0), N_PTS_MAX) : N_PTS_MAX + 1;
+        atomicAdd(&cnt[key], 1);
+    }
+    __syncthreads();
+    if (tid == 0) {
+        int acc = 0;
+        for (int k = 0; k < N_PTS_MAX + 2; ++k) {
+            start[k] = acc;
+            acc += cnt[k];
+        }
+    }
+    __syncthreads();
+    for (int b = tid; b < B; b += SORT_THREADS) {
+        const SampleParams p = sp[b];
+        int key = p.status == SWIMMER_OK ? N_PTS_MAX + 1 - min(max(p.n, 0), N_PTS_MAX) : N_PTS_MAX + 1;
+        order[atomicAdd(&start[key], 1)] = b;
+    }
+}
+
 // ---------------------------------------------------------------------------------
 // K1a: interval integrals, one thread per node interval or tail piece (all samples)
 // ---------------------------------------------------------------------------------
@@ -657,6 +690,11 @@ int launch_prepare(swimmer_handle *h, int B, const double *theta, const int *n_p
     prepare_kernel<<<(B + 127) / 128, 128, 0, s>>>(B, theta, n_pts, h->cfg, h->sp, h->order);
     CUDA_TRY(cudaGetLastError());
     prof_count(h, 1);
+    if (n_pts) {  // uneven sizes: longest first
+        order_kernel<<<1, SORT_THREADS, 0, s>>>(B, h->sp, h->order);
+        CUDA_TRY(cudaGetLastError());
+        prof_count(h, 1);
+    }
     return 0;
 }
 
