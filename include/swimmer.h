@@ -80,10 +80,11 @@ const char *swimmer_last_error(void);
 
 /* Opt-in profiling.  mode 1: time every forward-kernel (K2) launch with CUDA events
  * recorded on its stream and count all kernel launches of this handle; mode 0: stop;
- * mode 2: wait for the recorded events, write out[4] = {total K2 milliseconds, K2
+ * mode 2: wait for the recorded events, write out[5] = {total K2 milliseconds, K2
  * launches, kernel launches, pair evaluations K2 executed (sum of n^2 x steps run, so
- * skipped and early-stopped samples count what they did)} (host array) and reset.
- * Synchronous. */
+ * skipped and early-stopped samples count what they did), the part of those a
+ * one-step-at-a-time TMCMC also performs (pre-fetched runs off the realized chain paths
+ * excluded)} (host array) and reset.  Synchronous. */
 int swimmer_profile(swimmer_handle *h, int mode, double *out);
 
 /* Kernel functions of the regularized Brinkmanlet (Sec. 2.1, Eq. BrV):
@@ -162,9 +163,10 @@ typedef struct tmcmc_state {
     double sigma_prop[9];  /* scaled covariance b^2 Sigma_j (row-major) */
     int unique;            /* number of distinct resampled samples (chains) */
     int max_chain;         /* longest chain */
-    int n_exact;           /* forward-model evaluations this stage */
+    int n_exact;           /* forward-model runs executed this stage (pre-fetched runs included) */
     int n_screened;        /* surrogate evaluations this stage (delayed acceptance) */
     int n_accept;          /* accepted proposals this stage */
+    int n_exact_path;      /* forward-model runs the chains used (what one-step-at-a-time needs) */
     double *surr_loglik;   /* device [B] surrogate log-likelihoods (delayed acceptance) */
 } tmcmc_state;
 
@@ -177,7 +179,10 @@ typedef struct tmcmc_state {
  *   normals:  device [B][3] proposal normals (chain c, step s uses row off_c + s).
  *   use_surrogate: 1 = delayed acceptance through the surrogate set with
  *             swimmer_surrogate_set (requires st->surr_loglik), 0 = plain.
- * Synchronizes `stream` once (the chain lengths decide the launches); updates st. */
+ * While few chains are alive, one launch pre-fetches the forward runs of a chain's next
+ * steps for both outcomes of each pending accept decision (depth up to 5), so several chain
+ * steps resolve per launch with results identical to the one-step-at-a-time chain.
+ * Synchronizes `stream` twice (chain lengths decide the launches; counters at the end). */
 int tmcmc_stage(swimmer_handle *h, tmcmc_state *st, const double *uniforms, const double *normals,
                 int use_surrogate, void *stream);
 

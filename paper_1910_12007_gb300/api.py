@@ -191,7 +191,8 @@ class TmcmcState:
     def summary(self):
         c = self.c
         return dict(stage=c.stage, q=c.q, log_s=c.log_s, mu=list(c.mu), unique=c.unique,
-                    max_chain=c.max_chain, n_exact=c.n_exact, n_screened=c.n_screened, n_accept=c.n_accept)
+                    max_chain=c.max_chain, n_exact=c.n_exact, n_screened=c.n_screened, n_accept=c.n_accept,
+                    n_exact_path=c.n_exact_path)
 
 
 def tmcmc_stage(h: Handle, st: TmcmcState, uniforms, normals, use_surrogate=False, stream=None):
@@ -288,9 +289,9 @@ def surrogate_loglik_batch(h: Handle, theta, obs, sigma, stream=None):
 
 def swimmer_profile(h: Handle, mode):
     """mode 1: start timing forward-kernel launches (CUDA events on their stream) and
-    counting kernel launches; mode 2: return (k2_ms, k2_launches, launches, k2_samples) and
-    reset; mode 0: stop."""
-    out = (ctypes.c_double * 4)()
+    counting kernel launches; mode 2: return (k2_ms, k2_launches, launches,
+    executed_pair_evals, useful_pair_evals) and reset; mode 0: stop."""
+    out = (ctypes.c_double * 5)()
     check(lib().swimmer_profile(h.ptr, int(mode), out))
     return tuple(out) if mode == 2 else None
 

@@ -54,12 +54,13 @@ extern "C" int swimmer_profile(swimmer_handle *h, int mode, double *out) {
             ms += t;
             samples += p->samples[i];
         }
-        unsigned long long work = 0;
-        CUDA_TRY(cudaMemcpy(&work, h->work, sizeof(work), cudaMemcpyDeviceToHost));
+        unsigned long long work[2] = {0, 0};
+        CUDA_TRY(cudaMemcpy(work, h->work, sizeof(work), cudaMemcpyDeviceToHost));
         out[0] = ms;
         out[1] = (double)p->used;
         out[2] = (double)h->n_launch;
-        out[3] = (double)work;
+        out[3] = (double)work[0];
+        out[4] = (double)work[1];
         p->used = 0;
         h->n_launch = 0;
         CUDA_TRY(cudaMemset(h->work, 0, sizeof(work)));
@@ -69,7 +70,7 @@ extern "C" int swimmer_profile(swimmer_handle *h, int mode, double *out) {
     p->used = 0;
     h->n_launch = 0;
     CUDA_TRY(cudaDeviceSynchronize());
-    CUDA_TRY(cudaMemset(h->work, 0, sizeof(unsigned long long)));
+    CUDA_TRY(cudaMemset(h->work, 0, 2 * sizeof(unsigned long long)));
     return 0;
 }
 
@@ -149,8 +150,9 @@ extern "C" int swimmer_init(const swimmer_config *cfg, swimmer_handle **out) {
     ALLOC(h->active2, B);
     ALLOC(h->cum, B);
     ALLOC(h->info, 128);
-    ALLOC(h->work, 1);
-    CUDA_TRY(cudaMemset(h->work, 0, sizeof(unsigned long long)));
+    ALLOC(h->work, 2);
+    CUDA_TRY(cudaMemset(h->work, 0, 2 * sizeof(unsigned long long)));
+    ALLOC(h->run_work, B);
     ALLOC(h->surr_norm, 2 * SWIMMER_MLP_OUT);
     ALLOC(h->surr_params, SWIMMER_MLP_NPARAM);
     ALLOC(h->surr_x, (size_t)B * SWIMMER_MLP_IN);
@@ -180,7 +182,7 @@ extern "C" int swimmer_destroy(swimmer_handle *h) {
     void *ptrs[] = {h->tab64, h->k1_scratch, h->tab32, h->sp, h->order, h->queue, h->speed_tmp, h->w, h->stats,
                     h->idx, h->counts, h->chain_id, h->chain_off, h->chain_len, h->aux,
                     h->cur_theta, h->cur_ll, h->cur_sl, h->prop_theta, h->prop_ll, h->prop_sl,
-                    h->out_theta, h->out_ll, h->out_sl, h->prop_status, h->active, h->active2, h->cum, h->info, h->work,
+                    h->out_theta, h->out_ll, h->out_sl, h->prop_status, h->active, h->active2, h->cum, h->info, h->work, h->run_work,
                     h->surr_norm, h->surr_params, h->surr_x, h->surr_y, h->surr_ws};
     for (void *p : ptrs)
         if (p) cudaFree(p);
@@ -221,10 +223,12 @@ static int check_batch(swimmer_handle *h, int B, const double *theta, const int 
 
 int run_forward(swimmer_handle *h, int B, const double *theta, const int *n_pts, const double *obs,
                 double sigma, double *loglik, double *head_traj, double *mean_speed, int *status,
-                cudaStream_t s) {
+                cudaStream_t s, int speculative) {
     int rc = launch_prepare(h, B, theta, n_pts, s);
     if (!rc) rc = launch_table_build(h, B, h->cfg.precision == SWIMMER_FP64, s);
-    if (!rc) rc = launch_forward(h, B, obs, sigma, loglik, head_traj, mean_speed, status, h->cfg.precision, s);
+    if (!rc)
+        rc = launch_forward(h, B, obs, sigma, loglik, head_traj, mean_speed, status, h->cfg.precision, s, 0,
+                            speculative);
     return rc;
 }
 
@@ -298,7 +302,7 @@ extern "C" int forward_batch(swimmer_handle *h, int B, const double *theta, cons
     int rc = check_batch(h, B, theta, status);
     if (rc) return rc;
     return run_forward(h, B, theta, n_pts, nullptr, 0.0, nullptr, head_traj, mean_speed, status,
-                       (cudaStream_t)stream);
+                       (cudaStream_t)stream, 0);
 }
 
 extern "C" int loglik_batch(swimmer_handle *h, int B, const double *theta, const int *n_pts,
@@ -309,5 +313,5 @@ extern "C" int loglik_batch(swimmer_handle *h, int B, const double *theta, const
     ARG_CHECK(loglik != nullptr, "loglik is NULL");
     ARG_CHECK(sigma > 0.0, "sigma must be > 0");
     ARG_CHECK(h->cfg.steps / h->cfg.obs_every >= 1, "no observation within steps");
-    return run_forward(h, B, theta, n_pts, obs, sigma, loglik, nullptr, nullptr, status, (cudaStream_t)stream);
+    return run_forward(h, B, theta, n_pts, obs, sigma, loglik, nullptr, nullptr, status, (cudaStream_t)stream, 0);
 }

@@ -48,7 +48,9 @@ struct swimmer_handle {
     int profile;
     long long n_launch;
     ProfileEvents *prof;
-    unsigned long long *work;  // device counter: pair evaluations executed by the forward kernel
+    unsigned long long *work;  // device counters: [0] pair evaluations executed by the forward
+                               // kernel, [1] those a one-step-at-a-time TMCMC would also run
+    unsigned long long *run_work;  // [b_max] pair evaluations of each run of the last launch
     // autotuned threads per sample for batch sizes in [2^k, 2^(k+1)), per precision; 0 = heuristic
     int tune_threads[2][17];
     int device;
@@ -113,7 +115,7 @@ int launch_prepare(swimmer_handle *h, int B, const double *theta, const int *n_p
 int launch_table_build(swimmer_handle *h, int B, int need64, cudaStream_t s);
 int launch_forward(swimmer_handle *h, int B, const double *obs, double sigma, double *loglik,
                    double *head_traj, double *mean_speed, int *status, int precision,
-                   cudaStream_t s, int threads_override = 0);
+                   cudaStream_t s, int threads_override = 0, int speculative = 0);
 int forward_threads(const swimmer_handle *h, int B, int precision);
 int launch_kernel_eval(swimmer_handle *h, int m, const double *r, double *g1, double *g2,
                        int precision, cudaStream_t s);

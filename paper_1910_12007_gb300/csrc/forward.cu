@@ -48,7 +48,9 @@ struct FwdArgs {
     double *head_traj;
     double *speed;
     int *status;
-    unsigned long long *work;
+    unsigned long long *work;      // [0] executed, [1] useful pair evaluations
+    unsigned long long *run_work;  // per-run pair evaluations (speculative launches)
+    int speculative;               // 1: the caller decides later which runs were useful
     int n_max;
     int threads;
     int tab_panels;  // panels of the shared-memory table region (handle's octaves x panels/octave)
@@ -182,6 +184,7 @@ __global__ void __launch_bounds__(1024) forward_kernel(FwdArgs a) {
                 a.status[b] = p.status;
                 if (a.loglik) a.loglik[b] = -INFINITY;
                 if (a.speed) a.speed[b] = nan("");
+                if (a.speculative) a.run_work[b] = 0;
             }
             if (a.head_traj)
                 for (long long o = tid; o < 2 * n_obs; o += T) a.head_traj[(size_t)b * 2 * n_obs + o] = nan("");
@@ -508,7 +511,14 @@ __global__ void __launch_bounds__(1024) forward_kernel(FwdArgs a) {
                 a.speed[b] = status == SWIMMER_OK ? (tot / n) / (a.steps * a.dt) : nan("");
             }
         }
-        if (tid == 0) atomicAdd(a.work, (unsigned long long)n * (unsigned long long)n * (unsigned long long)steps_done);
+        if (tid == 0) {
+            unsigned long long wk = (unsigned long long)n * (unsigned long long)n * (unsigned long long)steps_done;
+            atomicAdd(a.work, wk);
+            if (a.speculative)
+                a.run_work[b] = wk;
+            else
+                atomicAdd(a.work + 1, wk);
+        }
         if (owner && tgt == n - 1) {
             a.status[b] = status;
             if (a.loglik) {
@@ -546,7 +556,7 @@ int forward_threads(const swimmer_handle *h, int B, int precision) {
 
 int launch_forward(swimmer_handle *h, int B, const double *obs, double sigma, double *loglik,
                    double *head_traj, double *mean_speed, int *status, int precision, cudaStream_t s,
-                   int threads_override) {
+                   int threads_override, int speculative) {
     FwdArgs a;
     a.B = B;
     a.sp = h->sp;
@@ -568,6 +578,8 @@ int launch_forward(swimmer_handle *h, int B, const double *obs, double sigma, do
     a.speed = mean_speed;
     a.status = status;
     a.work = h->work;
+    a.run_work = h->run_work;
+    a.speculative = speculative;
     a.n_max = h->cfg.n_max;
     int T = threads_override > 0 ? threads_override : forward_threads(h, B, precision);
     a.threads = T;

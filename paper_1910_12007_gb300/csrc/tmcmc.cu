@@ -22,7 +22,7 @@
 
 int run_forward(swimmer_handle *h, int B, const double *theta, const int *n_pts, const double *obs,
                 double sigma, double *loglik, double *head_traj, double *mean_speed, int *status,
-                cudaStream_t s);
+                cudaStream_t s, int speculative);
 int run_surrogate_loglik(swimmer_handle *h, int B, const double *theta, const double *obs, double sigma,
                          double *loglik, cudaStream_t s);
 
@@ -308,71 +308,142 @@ __global__ void __launch_bounds__(T1) chains_kernel(int B, const int *__restrict
     }
 }
 
-__global__ void propose_kernel(int active, int s, const int *__restrict__ order, const int *__restrict__ chain_off,
-                               const double *__restrict__ cur_theta, const double *__restrict__ st,
-                               const double *__restrict__ normals, double lo0, double lo1, double lo2, double hi0,
-                               double hi1, double hi2, double *__restrict__ prop) {
-    int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= active) return;
-    int c = order[k];
-    int pos = chain_off[c] + s;
-    const double *L = st + S_L;
-    double z0 = normals[3 * pos], z1 = normals[3 * pos + 1], z2 = normals[3 * pos + 2];
-    double t0 = cur_theta[3 * c] + L[0] * z0 + L[1] * z1 + L[2] * z2;
-    double t1 = cur_theta[3 * c + 1] + L[3] * z0 + L[4] * z1 + L[5] * z2;
-    double t2 = cur_theta[3 * c + 2] + L[6] * z0 + L[7] * z1 + L[8] * z2;
-    bool in = t0 >= lo0 && t0 <= hi0 && t1 >= lo1 && t1 <= hi1 && t2 >= lo2 && t2 <= hi2;
-    // outside the prior box: NaN alpha makes the forward launch skip it (rejected)
-    prop[3 * k] = in ? t0 : nan("");
-    prop[3 * k + 1] = t1;
-    prop[3 * k + 2] = t2;
+// ---------------------------------------------------------------------------------
+// Metropolis chain steps with pre-fetching.  A chain at step s will either move to its
+// proposal or stay; the proposal of step s+1 is base + L z[row s+1] for whichever base that
+// decision leaves.  Evaluating the forward model for every node of the decision tree of depth
+// k (2^(k+1) - 1 candidates) in one batched launch lets one launch resolve k + 1 chain steps
+// exactly as the sequential chain would (the random inputs of each row are fixed in
+// advance).  Node q of a tree: level l = floor(log2(q + 1)), decision bits b = q + 1 - 2^l,
+// first decision most significant.  k = 0 is the plain one-step-per-launch chain.
+// ---------------------------------------------------------------------------------
+__device__ __forceinline__ int node_level(int q) { return 31 - __clz(q + 1); }
+
+__device__ __forceinline__ void add_step(const double *L, const double *z, const double *base, double *out) {
+    out[0] = base[0] + L[0] * z[0] + L[1] * z[1] + L[2] * z[2];
+    out[1] = base[1] + L[3] * z[0] + L[4] * z[1] + L[5] * z[2];
+    out[2] = base[2] + L[6] * z[0] + L[7] * z[1] + L[8] * z[2];
 }
 
-// delayed acceptance step 1: keep proposals that pass the surrogate screen, mark others
-__global__ void screen_kernel(int active, int s, const int *__restrict__ order, const int *__restrict__ chain_off,
-                             const double *__restrict__ cur_sl, const double *__restrict__ prop_sl,
-                             const double *__restrict__ st, const double *__restrict__ u1,
-                             double *__restrict__ prop, int *__restrict__ counter) {
-    int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= active) return;
-    int c = order[k];
-    int pos = chain_off[c] + s;
-    double qn = st[S_QN];
-    bool valid = !isnan(prop[3 * k]);
-    bool pass = valid && log(u1[pos]) < qn * (prop_sl[k] - cur_sl[c]);
-    if (!pass) prop[3 * k] = nan("");
-    if (pass) atomicAdd(counter, 1);
-}
-
-__global__ void accept_kernel(int active, int s, int delayed, const int *__restrict__ order,
-                              const int *__restrict__ chain_off, double *__restrict__ cur_theta,
-                              double *__restrict__ cur_ll, double *__restrict__ cur_sl,
-                              const double *__restrict__ prop, const double *__restrict__ prop_ll,
-                              const double *__restrict__ prop_sl, const int *__restrict__ prop_status,
-                              const double *__restrict__ st, const double *__restrict__ u_acc,
-                              double *__restrict__ out_theta, double *__restrict__ out_ll,
-                              double *__restrict__ out_sl, int *__restrict__ counter) {
-    int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= active) return;
-    int c = order[k];
-    int pos = chain_off[c] + s;
-    double qn = st[S_QN];
-    bool valid = !isnan(prop[3 * k]) && prop_status[k] == SWIMMER_OK;
-    double thr = qn * (prop_ll[k] - cur_ll[c]);
-    if (delayed) thr -= qn * (prop_sl[k] - cur_sl[c]);
-    if (valid && log(u_acc[pos]) < thr) {
-        cur_theta[3 * c] = prop[3 * k];
-        cur_theta[3 * c + 1] = prop[3 * k + 1];
-        cur_theta[3 * c + 2] = prop[3 * k + 2];
-        cur_ll[c] = prop_ll[k];
-        if (delayed) cur_sl[c] = prop_sl[k];
-        atomicAdd(counter, 1);
+struct Box {
+    double lo[3], hi[3];
+    __device__ bool in(const double *t) const {
+        return t[0] >= lo[0] && t[0] <= hi[0] && t[1] >= lo[1] && t[1] <= hi[1] && t[2] >= lo[2] && t[2] <= hi[2];
     }
-    out_theta[3 * pos] = cur_theta[3 * c];
-    out_theta[3 * pos + 1] = cur_theta[3 * c + 1];
-    out_theta[3 * pos + 2] = cur_theta[3 * c + 2];
-    out_ll[pos] = cur_ll[c];
-    out_sl[pos] = cur_sl[c];
+};
+
+// candidates of all nodes: prop[(slot*NC + q)*3].  Unreachable nodes (an accepted decision on
+// the path whose candidate lies outside the prior box), nodes beyond the chain's length and
+// candidates outside the box get a NaN alpha, which the forward launch skips.
+__global__ void spec_propose_kernel(int A, int s, int k, const int *__restrict__ order, const int *__restrict__ chain_off,
+                                    const int *__restrict__ chain_len, const double *__restrict__ cur_theta,
+                                    const double *__restrict__ st, const double *__restrict__ normals, Box box,
+                                    double *__restrict__ prop, int *__restrict__ counter) {
+    const int NC = (2 << k) - 1;
+    int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= A * NC) return;
+    const int slot = idx / NC, q = idx % NC;
+    const int c = order[slot];
+    const int l = node_level(q), b = q + 1 - (1 << l);
+    const int off = chain_off[c];
+    const double *L = st + S_L;
+    double base[3] = {cur_theta[3 * c], cur_theta[3 * c + 1], cur_theta[3 * c + 2]};
+    bool ok = s + l < chain_len[c];
+    double cand[3];
+    for (int i = 0; i < l && ok; ++i) {
+        add_step(L, normals + 3 * (off + s + i), base, cand);
+        if ((b >> (l - 1 - i)) & 1) {
+            if (!box.in(cand)) ok = false;  // that acceptance cannot happen
+            base[0] = cand[0];
+            base[1] = cand[1];
+            base[2] = cand[2];
+        }
+    }
+    add_step(L, normals + 3 * (off + s + l), base, cand);
+    ok = ok && box.in(cand);
+    prop[3 * idx] = ok ? cand[0] : nan("");
+    prop[3 * idx + 1] = cand[1];
+    prop[3 * idx + 2] = cand[2];
+    if (ok) atomicAdd(counter, 1);
+}
+
+// surrogate log-likelihood of the base state of node (l, b): the candidate of the deepest
+// accepted decision on the path, else the chain's current state
+__device__ __forceinline__ double base_value(int slot, int NC, int l, int b, const double *node_val, double cur) {
+    for (int i = l - 1; i >= 0; --i)
+        if ((b >> (l - 1 - i)) & 1) {
+            int qi = (1 << i) - 1 + (b >> (l - i));
+            return node_val[slot * NC + qi];
+        }
+    return cur;
+}
+
+// delayed acceptance step 1 for every node: proposals failing the surrogate screen against
+// their base are marked NaN (not run)
+__global__ void spec_screen_kernel(int A, int s, int k, const int *__restrict__ order, const int *__restrict__ chain_off,
+                                   const double *__restrict__ cur_sl, const double *__restrict__ prop_sl,
+                                   const double *__restrict__ st, const double *__restrict__ u1, double *__restrict__ prop,
+                                   int *__restrict__ counter) {
+    const int NC = (2 << k) - 1;
+    int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= A * NC) return;
+    const int slot = idx / NC, q = idx % NC;
+    const int c = order[slot];
+    const int l = node_level(q), b = q + 1 - (1 << l);
+    const int pos = chain_off[c] + s + l;
+    if (isnan(prop[3 * idx])) return;
+    double bsl = base_value(slot, NC, l, b, prop_sl, cur_sl[c]);
+    bool pass = log(u1[pos]) < st[S_QN] * (prop_sl[idx] - bsl);
+    if (!pass) prop[3 * idx] = nan("");
+    else atomicAdd(counter, 1);
+}
+
+// walk each chain's tree along the decisions it actually takes
+__global__ void spec_resolve_kernel(int A, int s, int k, int delayed, const int *__restrict__ order,
+                                    const int *__restrict__ chain_off, const int *__restrict__ chain_len,
+                                    double *__restrict__ cur_theta, double *__restrict__ cur_ll,
+                                    double *__restrict__ cur_sl, const double *__restrict__ prop,
+                                    const double *__restrict__ prop_ll, const double *__restrict__ prop_sl,
+                                    const int *__restrict__ prop_status, const double *__restrict__ st,
+                                    const double *__restrict__ u_acc, double *__restrict__ out_theta,
+                                    double *__restrict__ out_ll, double *__restrict__ out_sl, int *__restrict__ counter,
+                                    const unsigned long long *__restrict__ run_work,
+                                    unsigned long long *__restrict__ useful) {
+    const int NC = (2 << k) - 1;
+    int slot = blockIdx.x * blockDim.x + threadIdx.x;
+    if (slot >= A) return;
+    const int c = order[slot];
+    const double qn = st[S_QN];
+    int b = 0, acc = 0, ran = 0;
+    unsigned long long work = 0;
+    for (int l = 0; l <= k && s + l < chain_len[c]; ++l) {
+        const int idx = slot * NC + (1 << l) - 1 + b;
+        const int pos = chain_off[c] + s + l;
+        bool run = !isnan(prop[3 * idx]);  // the one-step chain would have run this proposal
+        ran += run;
+        if (run) work += run_work[idx];
+        bool valid = run && prop_status[idx] == SWIMMER_OK;
+        double thr = qn * (prop_ll[idx] - cur_ll[c]);
+        if (delayed) thr -= qn * (prop_sl[idx] - cur_sl[c]);
+        bool accept = valid && log(u_acc[pos]) < thr;
+        if (accept) {
+            cur_theta[3 * c] = prop[3 * idx];
+            cur_theta[3 * c + 1] = prop[3 * idx + 1];
+            cur_theta[3 * c + 2] = prop[3 * idx + 2];
+            cur_ll[c] = prop_ll[idx];
+            if (delayed) cur_sl[c] = prop_sl[idx];
+            ++acc;
+        }
+        out_theta[3 * pos] = cur_theta[3 * c];
+        out_theta[3 * pos + 1] = cur_theta[3 * c + 1];
+        out_theta[3 * pos + 2] = cur_theta[3 * c + 2];
+        out_ll[pos] = cur_ll[c];
+        out_sl[pos] = cur_sl[c];
+        b = 2 * b + (accept ? 1 : 0);
+    }
+    if (acc) atomicAdd(counter, acc);
+    if (ran) atomicAdd(counter + 3, ran);
+    if (work) atomicAdd(useful, work);
 }
 
 }  // namespace
@@ -432,9 +503,19 @@ extern "C" int tmcmc_stage(swimmer_handle *h, tmcmc_state *st, const double *uni
     int alive[64];
     for (int i = 0; i < cap - 2; ++i) alive[i] = h->host_pinned[2 + i];
     const double qn = hs[S_QN];
-    CUDA_TRY(cudaMemsetAsync(h->info + cap, 0, 2 * sizeof(int), s));  // accept / screen counters
-    int n_exact = 0, n_screened = 0;
-    for (int step = 0; step < maxlen; ++step) {
+    // counters: accepted, screen passes (runs with delayed acceptance), proposals run (plain),
+    // runs on the realized chain paths
+    CUDA_TRY(cudaMemsetAsync(h->info + cap, 0, 4 * sizeof(int), s));
+    int n_screened = 0;
+    Box box;
+    for (int a = 0; a < 3; ++a) {
+        box.lo[a] = st->prior_lo[a];
+        box.hi[a] = st->prior_hi[a];
+    }
+    // pre-fetch depth: resolve several chain steps per launch while few chains are alive,
+    // keeping each launch within about two samples per SM (and within b_max)
+    const int spec_cap = min(h->cfg.b_max, 2 * h->num_sms);
+    for (int step = 0; step < maxlen;) {
         int active;
         if (step < cap - 2) {
             active = alive[step];
@@ -446,36 +527,42 @@ extern "C" int tmcmc_stage(swimmer_handle *h, tmcmc_state *st, const double *uni
             for (int c = 0; c < U; ++c) active += h->host_pinned[c] > step;
         }
         if (active <= 0) break;
-        int grid = (active + 127) / 128;
-        propose_kernel<<<grid, 128, 0, s>>>(active, step, h->chain_id, h->chain_off, h->cur_theta, h->stats, normals,
-                                            st->prior_lo[0], st->prior_lo[1], st->prior_lo[2], st->prior_hi[0],
-                                            st->prior_hi[1], st->prior_hi[2], h->prop_theta);
+        int k = 0;
+        while (k < 5 && step + k + 1 < maxlen && active * ((4 << k) - 1) <= spec_cap) ++k;
+        const int NC = (2 << k) - 1, n = active * NC;
+        const int grid = (n + 127) / 128;
+        spec_propose_kernel<<<grid, 128, 0, s>>>(active, step, k, h->chain_id, h->chain_off, h->chain_len,
+                                                 h->cur_theta, h->stats, normals, box, h->prop_theta,
+                                                 h->info + cap + 2);
         CUDA_TRY(cudaGetLastError());
-        prof_count(h, 2 + (use_surrogate ? 1 : 0));
+        prof_count(h, 2);
         if (use_surrogate) {
-            int rc = run_surrogate_loglik(h, active, h->prop_theta, st->obs, st->sigma, h->prop_sl, s);
+            int rc = run_surrogate_loglik(h, n, h->prop_theta, st->obs, st->sigma, h->prop_sl, s);
             if (rc) return rc;
-            n_screened += active;
-            screen_kernel<<<grid, 128, 0, s>>>(active, step, h->chain_id, h->chain_off, h->cur_sl, h->prop_sl,
-                                               h->stats, uniforms + B, h->prop_theta, h->info + cap + 1);
+            n_screened += n;
+            spec_screen_kernel<<<grid, 128, 0, s>>>(active, step, k, h->chain_id, h->chain_off, h->cur_sl,
+                                                    h->prop_sl, h->stats, uniforms + B, h->prop_theta,
+                                                    h->info + cap + 1);
             CUDA_TRY(cudaGetLastError());
+            prof_count(h, 1);
         }
-        int rc = run_forward(h, active, h->prop_theta, nullptr, st->obs, st->sigma, h->prop_ll, nullptr, nullptr,
-                             h->prop_status, s);
+        int rc = run_forward(h, n, h->prop_theta, nullptr, st->obs, st->sigma, h->prop_ll, nullptr, nullptr,
+                             h->prop_status, s, 1);
         if (rc) return rc;
-        if (!use_surrogate) n_exact += active;
-        accept_kernel<<<grid, 128, 0, s>>>(active, step, use_surrogate, h->chain_id, h->chain_off, h->cur_theta,
-                                           h->cur_ll, h->cur_sl, h->prop_theta, h->prop_ll, h->prop_sl,
-                                           h->prop_status, h->stats, uniforms + (use_surrogate ? 2 * B : B),
-                                           h->out_theta, h->out_ll, h->out_sl, h->info + cap);
+        spec_resolve_kernel<<<(active + 127) / 128, 128, 0, s>>>(
+            active, step, k, use_surrogate, h->chain_id, h->chain_off, h->chain_len, h->cur_theta, h->cur_ll,
+            h->cur_sl, h->prop_theta, h->prop_ll, h->prop_sl, h->prop_status, h->stats,
+            uniforms + (use_surrogate ? 2 * B : B), h->out_theta, h->out_ll, h->out_sl, h->info + cap, h->run_work,
+            h->work + 1);
         CUDA_TRY(cudaGetLastError());
+        step += k + 1;
     }
     CUDA_TRY(cudaMemcpyAsync(st->theta, h->out_theta, 3 * sizeof(double) * B, cudaMemcpyDeviceToDevice, s));
     CUDA_TRY(cudaMemcpyAsync(st->loglik, h->out_ll, sizeof(double) * B, cudaMemcpyDeviceToDevice, s));
     if (use_surrogate)
         CUDA_TRY(cudaMemcpyAsync(st->surr_loglik, h->out_sl, sizeof(double) * B, cudaMemcpyDeviceToDevice, s));
     CUDA_TRY(cudaMemsetAsync(st->status, 0, sizeof(int) * B, s));
-    CUDA_TRY(cudaMemcpyAsync(h->host_pinned, h->info + cap, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaMemcpyAsync(h->host_pinned, h->info + cap, 4 * sizeof(int), cudaMemcpyDeviceToHost, s));
     CUDA_TRY(cudaStreamSynchronize(s));
     st->q = qn;
     st->stage += 1;
@@ -486,6 +573,7 @@ extern "C" int tmcmc_stage(swimmer_handle *h, tmcmc_state *st, const double *uni
     st->max_chain = maxlen;
     st->n_accept = h->host_pinned[0];
     st->n_screened = n_screened;
-    st->n_exact = use_surrogate ? h->host_pinned[1] : n_exact;
+    st->n_exact = use_surrogate ? h->host_pinned[1] : h->host_pinned[2];
+    st->n_exact_path = h->host_pinned[3];
     return 0;
 }
