@@ -38,8 +38,17 @@ THETA_TRUE = (1.0, 0.0, 0.1)
 PRIOR_LO = (0.0, -1.0, 0.05)
 PRIOR_HI = (10.0, 1.0, 0.2)
 NOISE = 0.05
-FLOPS_PER_PAIR = 27  # FP32 flops of one pair term: difference 2, r^2 3, u 2, quadratic table 8,
-                    # F.d 3, (F.d)g2 1, velocity update 8
+# FP32 flops of one unordered pair {i, j} in the symmetric pair sum: difference 2, r^2 3, u 2,
+# quadratic table 8 (shared by both directions), then per direction F.d 3, (F.d) g2 1 and the
+# velocity update 8
+FLOPS_PER_UNORDERED_PAIR = 39
+
+
+def pair_sum_flops(ordered_pairs, unordered_per_ordered):
+    """FP32 flops of the pair sum for `ordered_pairs` pair evaluations (n^2 per sample and
+    step, self terms included) of which `unordered_per_ordered` are distinct unordered pairs
+    (n (n - 1) / 2 per n^2)."""
+    return FLOPS_PER_UNORDERED_PAIR * ordered_pairs * unordered_per_ordered
 
 
 def workload_config(precision_name):
@@ -240,9 +249,15 @@ def main():
         cfg.steps = 200
         h = g.swimmer_init(cfg)
         th = torch.tensor(synthetic.prior_samples(5, PRIOR_LO, (10.0, 0.2, 0.2), B_STAGE), device=dev)
-        for _ in range(2):
+        for rep in range(2):
+            g.swimmer_profile(h, 1)
             g.forward_batch(h, th, want_traj=False)
+            k2_ms, _, _, pairs, _ = g.swimmer_profile(h, 2)
+        g.swimmer_profile(h, 0)
         torch.cuda.synchronize()
+        print(json.dumps({"profile_case": f"{B_STAGE} samples x N={N_PTS} x {cfg.steps} steps",
+                          "k2_ms": k2_ms, "pair_evals_per_s": pairs / (k2_ms * 1e-3),
+                          "tflops": pair_sum_flops(pairs, (N_PTS - 1) / (2.0 * N_PTS)) / (k2_ms * 1e-3) / 1e12}))
         h.close()
         return 0
     h = g.swimmer_init(cfg)
@@ -365,7 +380,8 @@ def main():
         fp32_peak = sm_count * 128 * 2 * max_mhz * 1e6 / 1e12  # TFLOP/s
         k2_avg_ms = k2_ms / max(k2_launches, 1)
         # the kernel's rate counts every pair it executes (pre-fetched runs included)
-        achieved = FLOPS_PER_PAIR * pairs_exec / (k2_ms * 1e-3) / 1e12 if k2_ms > 0 else 0.0
+        upo = (N_PTS - 1) / (2.0 * N_PTS)
+        achieved = pair_sum_flops(pairs_exec, upo) / (k2_ms * 1e-3) / 1e12 if k2_ms > 0 else 0.0
         traffic_pp = kernel_traffic()
         value = pairs_all / (ms_all * 1e-3)
         line = {
@@ -459,7 +475,12 @@ def forward_workload(args, rank, world, local_rank):
     peaks, _ = load_peaks()
     sm = torch.cuda.get_device_properties(dev).multi_processor_count
     fp32_peak = sm * 128 * 2 * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
-    achieved = FLOPS_PER_PAIR * pairs / (ms * 1e-3) / 1e12
+    if ns is not None:
+        nn = ns.astype(np.float64)
+        upo = float((nn * (nn - 1) / 2).sum() / (nn ** 2).sum())
+    else:
+        upo = (1024 - 1) / (2.0 * 1024)
+    achieved = pair_sum_flops(pairs, upo) / (ms * 1e-3) / 1e12
     line = {"metric": METRIC, "value": pairs / (ms * 1e-3), "unit": "pair-evals/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32" if prec == g.FP32C else "f64",

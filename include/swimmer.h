@@ -87,6 +87,13 @@ const char *swimmer_last_error(void);
  * excluded)} (host array) and reset.  Synchronous. */
 int swimmer_profile(swimmer_handle *h, int mode, double *out);
 
+/* The K2 launches recorded since profiling started or was last reset (mode 2 of
+ * swimmer_profile), oldest first: ms[i] = device time of launch i (CUDA events),
+ * samples[i] = its batch size, for i < min(cap, recorded); *count = recorded.  Host
+ * arrays of cap entries (may be NULL when cap = 0).  Waits for the events; resets nothing.
+ * Diagnostic only (not part of the method). */
+int swimmer_profile_launches(swimmer_handle *h, int cap, double *ms, int *samples, int *count);
+
 /* Kernel functions of the regularized Brinkmanlet (Sec. 2.1, Eq. BrV):
  * g1(r) = B''(r) and g2(r) = (r B''(r) - B'(r))/r^3 for (Lap - alpha^2) B = G, Lap G =
  * phi_delta (Eq. eqnblob), evaluated through the same per-sample table the forward

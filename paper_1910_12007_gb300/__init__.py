@@ -7,5 +7,6 @@ fully resolved hydrodynamics" (arXiv 1910.12007).  The compute path is the CUDA 
 from .api import (FP32C, FP64, MLP_NPARAM, ForwardGraph, Handle, SwimmerConfig, TmcmcState, forward_batch,  # noqa: F401
                   loglik_batch, mlp_adam, mlp_backward, mlp_forward, mlp_workspace, surrogate_loglik_batch,
                   swimmer_destroy, swimmer_init, swimmer_kernel_eval, swimmer_surrogate_set, tmcmc_analyze,
-                  swimmer_autotune, swimmer_kernel_eval_noalloc, swimmer_profile, tmcmc_resample, tmcmc_run,
+                  swimmer_autotune, swimmer_kernel_eval_noalloc, swimmer_profile,
+                  swimmer_profile_launches, tmcmc_resample, tmcmc_run,
                   tmcmc_stage)

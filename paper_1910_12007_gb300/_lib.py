@@ -37,6 +37,7 @@ SIGNATURES = [
     ("swimmer_destroy", c_int, [c_void_p]),
     ("swimmer_last_error", ctypes.c_char_p, []),
     ("swimmer_profile", c_int, [c_void_p, c_int, c_void_p]),
+    ("swimmer_profile_launches", c_int, [c_void_p, c_int, c_void_p, c_void_p, c_void_p]),
     ("swimmer_kernel_eval", c_int, [c_void_p, c_double, c_double, c_double, c_int, c_void_p, c_void_p, c_void_p, c_int, c_void_p]),
     ("swimmer_kernel_eval_noalloc", c_int, [c_double, c_double, c_double, c_int, c_void_p, c_void_p, c_void_p, c_int, c_void_p]),
     ("forward_batch", c_int, [c_void_p, c_int, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),

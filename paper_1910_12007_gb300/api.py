@@ -296,6 +296,18 @@ def swimmer_profile(h: Handle, mode):
     return tuple(out) if mode == 2 else None
 
 
+def swimmer_profile_launches(h: Handle):
+    """(ms, samples) of every forward-kernel launch recorded since profiling started or was
+    last reset, oldest first (diagnostic; resets nothing)."""
+    count = ctypes.c_int(0)
+    check(lib().swimmer_profile_launches(h.ptr, 0, None, None, ctypes.byref(count)))
+    n = count.value
+    ms = (ctypes.c_double * max(n, 1))()
+    samples = (ctypes.c_int * max(n, 1))()
+    check(lib().swimmer_profile_launches(h.ptr, n, ms, samples, ctypes.byref(count)))
+    return [(ms[i], samples[i]) for i in range(n)]
+
+
 def swimmer_autotune(h: Handle, steps=200):
     """Time the forward kernel's launch shapes per batch-size bucket; returns
     {batch size: threads per sample} for B = 1, 2, 4, ..., b_max."""

@@ -40,6 +40,23 @@ void prof_k2_end(swimmer_handle *h, cudaStream_t s) {
     p->used += 1;
 }
 
+extern "C" int swimmer_profile_launches(swimmer_handle *h, int cap, double *ms, int *samples, int *count) {
+    ARG_CHECK(h != nullptr, "handle is NULL");
+    ARG_CHECK(cap >= 0, "cap must be >= 0");
+    ARG_CHECK(cap == 0 || (ms != nullptr && samples != nullptr), "ms or samples is NULL");
+    ARG_CHECK(count != nullptr, "count is NULL");
+    ProfileEvents *p = h->prof;
+    for (size_t i = 0; i < p->used && i < (size_t)cap; ++i) {
+        CUDA_TRY(cudaEventSynchronize(p->stop[i]));
+        float t = 0.f;
+        CUDA_TRY(cudaEventElapsedTime(&t, p->start[i], p->stop[i]));
+        ms[i] = t;
+        samples[i] = p->samples[i];
+    }
+    *count = (int)p->used;
+    return 0;
+}
+
 extern "C" int swimmer_profile(swimmer_handle *h, int mode, double *out) {
     ARG_CHECK(h != nullptr, "handle is NULL");
     ARG_CHECK(mode >= 0 && mode <= 2, "mode must be 0, 1 or 2");
@@ -120,6 +137,7 @@ extern "C" int swimmer_init(const swimmer_config *cfg, swimmer_handle **out) {
     h->prof = new ProfileEvents();
     CUDA_TRY(cudaGetDevice(&h->device));
     CUDA_TRY(cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device));
+    CUDA_TRY(cudaDeviceGetAttribute(&h->max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device));
     const int B = cfg->b_max;
     ALLOC(h->tab64, (size_t)B * TAB64_STRIDE);
     ALLOC(h->k1_scratch, (size_t)B * K1_SCRATCH);
@@ -269,6 +287,7 @@ extern "C" int swimmer_autotune(swimmer_handle *h, int steps, int *out_threads) 
         float best = 1e30f;
         int bestT = T0;
         for (int T = T0; T <= 1024 && !rc; T <<= 1) {
+            if (!forward_fits(h, T, prec)) break;
             float ms = 0.f;
             for (int rep = 0; rep < 2 && !rc; ++rep) {  // first run warms up
                 cudaEventRecord(e0, 0);

@@ -55,6 +55,7 @@ struct swimmer_handle {
     int tune_threads[2][17];
     int device;
     int num_sms;
+    int max_smem;  // opt-in shared memory per block (bytes)
     // per-sample workspace (b_max samples)
     double *tab64;          // [b_max][TAB64_STRIDE]
     double *k1_scratch;     // [b_max][K1_SCRATCH] interval integrals of the table build
@@ -117,6 +118,7 @@ int launch_forward(swimmer_handle *h, int B, const double *obs, double sigma, do
                    double *head_traj, double *mean_speed, int *status, int precision,
                    cudaStream_t s, int threads_override = 0, int speculative = 0);
 int forward_threads(const swimmer_handle *h, int B, int precision);
+bool forward_fits(const swimmer_handle *h, int threads, int precision);
 int launch_kernel_eval(swimmer_handle *h, int m, const double *r, double *g1, double *g2,
                        int precision, cudaStream_t s);
 int gl_init();

@@ -10,14 +10,20 @@
 //      c_k = 2 K_C ds (zeta - zeta^) (gradient of Eq. EFB); the FP32 kernel uses the
 //      hardware reciprocal square root and, after reduction to [-pi, pi], sine/cosine;
 //   C  point forces F = -dE/dX (Eq. Fenergy) gathered from the stencils;
-//   D  Brinkmanlet pair sum (Eq. BrV) v_i = (1/mu) sum_j [-F_j g1 + (F_j . d) d g2]:
-//      sources (x, y, Fx, Fy) as one float4 / 32-byte record per point in shared memory,
-//      stored twice in a row so that the diagonal walk needs no wrap test; target i meets
-//      source i + d at inner step d, so all lanes of a warp look up nearly the same table
-//      panel (|d| ds apart on a smooth filament) and the loads broadcast; the S threads of
-//      a target split the sources and combine with warp shuffles; g1, g2 from the
-//      per-sample shared-memory table (quadratic in F = 1 + f in FP32, Chebyshev degree 9 in
-//      FP64); FP32 partial sums of 32 sources are folded into a (hi, lo) pair by TwoSum;
+//   D  Brinkmanlet pair sum (Eq. BrV) v_i = (1/mu) sum_j [-F_j g1 + (F_j . d) d g2],
+//      d = X_i - X_j, with g1, g2 from the per-sample shared-memory table (quadratic in
+//      F = 1 + f in FP32, Chebyshev degree 9 in FP64).
+//      FP32: every unordered pair once.  g1, g2 and (F . d) d are even in d, so one table
+//      lookup serves v_i and v_j.  The points form blocks of 32; a warp takes a block pair
+//      (I, J) along diagonals: lane l holds target I*32 + l and meets source
+//      J*32 + (l + d) mod 32 at step d, so all lanes look up nearly the same table panel
+//      (|d| ds apart on a smooth filament) and the loads broadcast, while the source-side
+//      sums travel one lane per step with warp shuffles.  Sources (x, y, Fx, Fy) are one
+//      float4 per point, each block stored twice in a row so that the walk needs no wrap
+//      test.  Per-warp partial sums are combined in a fixed order with TwoSum, so results
+//      do not depend on scheduling.
+//      FP64: target i meets source i + d at step d (the point list stored twice), the S
+//      threads of a target splitting the sources and combining with warp shuffles;
 //   E  forward Euler X += dt v: FP64 positions in the FP64 kernel, double-float (hi + lo
 //      FP32, about 48 significant bits) positions updated by TwoSum in the FP32 kernel;
 //      every obs_every steps the head point is compared with the observations and the
@@ -31,7 +37,6 @@
 namespace {
 
 constexpr double PI = 3.14159265358979323846;
-constexpr int CHUNK = 32;  // sources per compensated partial sum
 
 struct FwdArgs {
     int B;
@@ -98,18 +103,34 @@ __host__ __device__ size_t table_bytes(int P) {
     return F64 ? sizeof(double) * 2 * P * F64_NODES : (sizeof(float4) + sizeof(float2)) * P;
 }
 
-// positions (16 B/point), sources (2 records/point), seg x/y, tension, 6 bending terms
+__host__ __device__ inline size_t align32(size_t b) { return (b + 31) & ~size_t(31); }
+
+// Warps of a CTA that take part in the FP32 pair sum: one per pair unit at most (a sample of
+// n points has ceil(n/32)^2 units of 16 diagonal steps).
+__host__ __device__ inline int pair_warps(int n_max, int threads) {
+    const int nbm = (n_max + 31) / 32;
+    const int W = threads / 32;
+    return W < nbm * nbm ? W : nbm * nbm;
+}
+
+// Per-step state in shared memory.
+// FP64: positions sx, sy [n_max] (double); sources (x, y, Fx, Fy) [2 n_max] (the point list
+//   twice in a row); tension vectors tx, ty [n_max]; six bending terms [6][n_max].
+// FP32: positions xh, xl, yh, yl [n_max]; sources per block of 32 points, each block stored
+//   twice in a row ([nbm][64] float4); tension vectors and bending terms [8][n_max], which
+//   during the pair sum hold the per-warp partial velocities [pair warps][nbm * 32] (float2)
+//   instead, the region growing when those need more room.
 template <bool F64>
-__host__ __device__ size_t state_bytes(int n_max) {
-    typedef typename Types<F64>::R R;
-    typedef typename Types<F64>::R4 R4;
-    size_t b = 16 * (size_t)n_max + 2 * sizeof(R4) * n_max + 9 * sizeof(R) * n_max;
-    return (b + 31) & ~size_t(31);
+__host__ __device__ size_t state_bytes(int n_max, int threads) {
+    if (F64) return align32(16 * (size_t)n_max) + 2 * 32 * (size_t)n_max + 8 * 8 * (size_t)n_max;
+    const size_t nbm = (n_max + 31) / 32;
+    size_t forces = 32 * (size_t)n_max, part = 256 * nbm * (size_t)pair_warps(n_max, threads);
+    return align32(16 * (size_t)n_max) + 1024 * nbm + align32(forces > part ? forces : part);
 }
 
 template <bool F64>
-__host__ __device__ size_t smem_bytes(int n_max, int P) {
-    return state_bytes<F64>(n_max) + table_bytes<F64>(P);
+__host__ __device__ size_t smem_bytes(int n_max, int P, int threads) {
+    return state_bytes<F64>(n_max, threads) + table_bytes<F64>(P);
 }
 
 // g1, g2 from the FP32 table: quadratic in F = 1 + f in [1, 2), the mantissa of u
@@ -158,12 +179,13 @@ __global__ void __launch_bounds__(1024) forward_kernel(FwdArgs a) {
     double *sx = (double *)smraw;
     double *sy = sx + n_max;
     float *xh = (float *)smraw, *xl = xh + n_max, *yh = xl + n_max, *yl = yh + n_max;
-    R4 *src = (R4 *)(smraw + 16 * (size_t)n_max);  // [2 n_max]
-    R *segx = (R *)(src + 2 * n_max);
-    R *segy = segx + n_max;
-    R *tens = segy + n_max;
-    R *bend = tens + n_max;  // [6][n_max]
-    unsigned char *tabraw = smraw + state_bytes<F64>(n_max);
+    const int nbm = (n_max + 31) >> 5;
+    R4 *src = (R4 *)(smraw + align32(16 * (size_t)n_max));  // FP64 [2 n_max]; FP32 [nbm][64]
+    R *tvx = (R *)(src + (F64 ? 2 * n_max : 64 * nbm));    // tension vectors, then bending
+    R *tvy = tvx + n_max;
+    R *bend = tvy + n_max;  // [6][n_max]
+    float2 *part = (float2 *)tvx;  // FP32 pair sum: per-warp partial velocities
+    unsigned char *tabraw = smraw + state_bytes<F64>(n_max, blockDim.x);
     __shared__ int s_work;
     __shared__ double s_red[32];
 
@@ -227,6 +249,14 @@ __global__ void __launch_bounds__(1024) forward_kernel(FwdArgs a) {
                 yl[k] = 0.f;
             }
         }
+        if (!F64) {  // pad the last block with force-free sources at the origin
+            const int npad = ((n + 31) >> 5) << 5;
+            for (int k = n + tid; k < npad; k += T) {
+                const int ks = ((k >> 5) << 6) + (k & 31);
+                src[ks] = R4{0, 0, 0, 0};
+                src[ks + 32] = R4{0, 0, 0, 0};
+            }
+        }
         const double inv_ds2 = 1.0 / (ds * ds);
         const float ds2_hi = (float)(ds * ds), ds2_lo = (float)(ds * ds - (double)ds2_hi);
         const R r_ds = (R)ds, r_inv2ds = (R)(0.5 / ds), r_invds2 = (R)inv_ds2;
@@ -235,16 +265,27 @@ __global__ void __launch_bounds__(1024) forward_kernel(FwdArgs a) {
         const R inv_d2 = (R)(1.0 / (p.delta * p.delta));
         const double dt_mu = a.dt / a.mu;
         const float dt_mu_f = (float)dt_mu, ds_f = (float)ds;
-        // thread -> (target slot, source split)
+        // FP64 pair sum: thread -> (target, source split of S lanes)
         int S = 1;
         while (S < 32 && 2 * S * n <= T) S <<= 1;
         const int slot = tid / S, split = tid % S;
         const int tgt = slot;  // one target per slot
         const bool owner = (split == 0) && (tgt < n);
+        // FP32 pair sum: ceil(n/32)^2 units of 16 steps over the pair warps
+        const int nb = (n + 31) >> 5, n_units = nb * nb;
+        const int n_pw = pair_warps(n_max, T);
+        // the thread that updates the head point n - 1 (observations, log-likelihood)
+        const bool head_thread = F64 ? (owner && tgt == n - 1) : (tid == (n - 1) % T);
         double J = 0.0;
         int status = SWIMMER_OK;
         long long steps_done = a.steps;
         __syncthreads();
+        float g10 = 0.f;  // FP32: g1 at r = 0 (self term)
+        if (!F64) {
+            float g2unused;
+            kern_f32((const float4 *)tabraw, (const float2 *)((const float4 *)tabraw + P), npan - 1, 1.0f, g10,
+                     g2unused);
+        }
 
         for (long long step = 0; step < a.steps; ++step) {
             const R tR = (R)(step * a.dt);
@@ -253,7 +294,7 @@ __global__ void __launch_bounds__(1024) forward_kernel(FwdArgs a) {
             //      forms e_k (tension of segment k) and again e_{k-1} (for the curvature at
             //      k), which saves a barrier.
             for (int k = tid; k < n; k += T) {
-                R qx, qy, epx = 0, epy = 0, emx = 0, emy = 0;
+                R qx, qy, epx = 0, epy = 0, emx = 0, emy = 0, tk = 0;
                 if (F64) {
                     if (k + 1 < n) {
                         double ex = sx[k + 1] - sx[k], ey = sy[k + 1] - sy[k];
@@ -262,7 +303,7 @@ __global__ void __launch_bounds__(1024) forward_kernel(FwdArgs a) {
                         R ell = r_ds * ((R)1 + strain);
                         epx = (R)ex;
                         epy = (R)ey;
-                        tens[k] = kt2 * strain / ell;
+                        tk = kt2 * strain / ell;
                         if (!(fabs((double)strain) <= STRETCH_MAX)) bad = 1;
                     }
                     if (k >= 1) {
@@ -294,7 +335,7 @@ __global__ void __launch_bounds__(1024) forward_kernel(FwdArgs a) {
                         float ell = ds_f * (1.0f + strain);
                         epx = (R)exh;
                         epy = (R)eyh;
-                        tens[k] = (R)__fdividef((float)kt2 * strain, ell);
+                        tk = (R)__fdividef((float)kt2 * strain, ell);
                         if (!(fabsf(strain) <= (float)STRETCH_MAX)) bad = 1;
                     }
                     if (k >= 1) {
@@ -308,14 +349,16 @@ __global__ void __launch_bounds__(1024) forward_kernel(FwdArgs a) {
                     qx = (R)(xh[k] + xl[k]);
                     qy = (R)(yh[k] + yl[k]);
                 }
-                if (k + 1 < n) {
-                    segx[k] = epx;
-                    segy[k] = epy;
+                if (k + 1 < n) {  // tension force vector of segment k
+                    tvx[k] = tk * epx;
+                    tvy[k] = tk * epy;
                 }
-                src[k].x = qx;
-                src[k].y = qy;
-                src[k + n].x = qx;
-                src[k + n].y = qy;
+                const int ks = F64 ? k : ((k >> 5) << 6) + (k & 31);  // first copy of point k
+                const int kd = F64 ? k + n : ks + 32;                 // second copy
+                src[ks].x = qx;
+                src[ks].y = qy;
+                src[kd].x = qx;
+                src[kd].y = qy;
                 if (k >= 1 && k + 1 < n) {
                     R A = (emx + epx) * r_inv2ds, Bv = (emy + epy) * r_inv2ds;
                     R C = (epx - emx) * r_invds2, D = (epy - emy) * r_invds2;
@@ -364,12 +407,12 @@ __global__ void __launch_bounds__(1024) forward_kernel(FwdArgs a) {
             for (int k = tid; k < n; k += T) {
                 R fx = 0, fy = 0;
                 if (k + 1 < n) {
-                    fx += tens[k] * segx[k];
-                    fy += tens[k] * segy[k];
+                    fx += tvx[k];
+                    fy += tvy[k];
                 }
                 if (k >= 1) {
-                    fx -= tens[k - 1] * segx[k - 1];
-                    fy -= tens[k - 1] * segy[k - 1];
+                    fx -= tvx[k - 1];
+                    fy -= tvy[k - 1];
                 }
                 if (k >= 2) {
                     fx -= bend[4 * n_max + k - 1];
@@ -383,25 +426,27 @@ __global__ void __launch_bounds__(1024) forward_kernel(FwdArgs a) {
                     fx -= bend[0 * n_max + k + 1];
                     fy -= bend[1 * n_max + k + 1];
                 }
-                src[k].z = fx;
-                src[k].w = fy;
-                src[k + n].z = fx;
-                src[k + n].w = fy;
+                const int ks = F64 ? k : ((k >> 5) << 6) + (k & 31);
+                const int kd = F64 ? k + n : ks + 32;
+                src[ks].z = fx;
+                src[ks].w = fy;
+                src[kd].z = fx;
+                src[kd].w = fy;
             }
             __syncthreads();
-            // ---- D: pair sum along diagonals (source j = tgt + d, d = split, split + S, ...)
+            // ---- D: pair sum
             double vxd = 0.0, vyd = 0.0;
-            float vxf = 0.f, vyf = 0.f;
-            if (tgt < n) {
-                const R4 me = src[tgt];
-                const R xi = me.x, yi = me.y;
-                if (F64) {
+            if (F64) {
+                // FP64: target tgt meets source tgt + d at step d (d = split, split + S, ...)
+                if (tgt < n) {
+                    const R4 me = src[tgt];
+                    const double xi = (double)me.x, yi = (double)me.y;
                     const double *tab = (const double *)tabraw;
                     double vx = 0.0, vy = 0.0;
                     const R4 *sp = src + tgt + split;
                     for (int d = split; d < n; d += S, sp += S) {
                         R4 q = *sp;
-                        double dx = (double)xi - (double)q.x, dy = (double)yi - (double)q.y;
+                        double dx = xi - (double)q.x, dy = yi - (double)q.y;
                         double u = fma(fma(dx, dx, dy * dy), (double)inv_d2, 1.0);
                         double g1, g2;
                         kern_f64(tab, P, npan - 1, u, g1, g2);
@@ -412,70 +457,131 @@ __global__ void __launch_bounds__(1024) forward_kernel(FwdArgs a) {
                     }
                     vxd = vx;
                     vyd = vy;
-                } else {
-                    const float4 *t1 = (const float4 *)tabraw;
-                    const float2 *t2 = (const float2 *)(t1 + P);
-                    const float4 *sp = (const float4 *)src + tgt + split;
-                    const float fxi = (float)xi, fyi = (float)yi, fid2 = (float)inv_d2;
-                    float hx = 0.f, lx = 0.f, hy = 0.f, ly = 0.f;
-                    for (int d0 = split; d0 < n; d0 += S * CHUNK) {
-                        float px = 0.f, py = 0.f;
-                        const int dend = min(n, d0 + S * CHUNK);
-#pragma unroll 4
-                        for (int d = d0; d < dend; d += S, sp += S) {
-                            float4 q = *sp;
-                            float dx = fxi - q.x, dy = fyi - q.y;
-                            float u = fmaf(fmaf(dx, dx, dy * dy), fid2, 1.0f);
-                            float g1, g2;
-                            kern_f32(t1, t2, npan - 1, u, g1, g2);
-                            float fd = fmaf(q.z, dx, q.w * dy);
-                            float wv = fd * g2;
-                            px = fmaf(wv, dx, fmaf(-q.z, g1, px));
-                            py = fmaf(wv, dy, fmaf(-q.w, g1, py));
-                        }
-                        acc_two_sum(hx, lx, px);
-                        acc_two_sum(hy, ly, py);
-                    }
-                    vxf = hx + lx;
-                    vyf = hy + ly;
                 }
-            }
-            // combine the S source splits (lanes of one warp)
-            for (int o = S >> 1; o >= 1; o >>= 1) {
-                if (F64) {
+                // combine the S source splits (lanes of one warp)
+                for (int o = S >> 1; o >= 1; o >>= 1) {
                     vxd += __shfl_xor_sync(0xffffffffu, vxd, o);
                     vyd += __shfl_xor_sync(0xffffffffu, vyd, o);
-                } else {
-                    vxf += __shfl_xor_sync(0xffffffffu, vxf, o);
-                    vyf += __shfl_xor_sync(0xffffffffu, vyf, o);
+                }
+            } else if ((tid >> 5) < n_pw) {
+                // FP32: each unordered pair {i, j} once.  g1(r) and g2(r) are even in
+                // d = X_i - X_j and (F . d) d is even too, so one table lookup gives both
+                // v_i += -F_j g1 + (F_j . d) d g2 and v_j += -F_i g1 + (F_i . d) d g2.
+                // Unit (I, J, d0): lane l takes target I*32 + l and, at step d = d0 .. d0+15,
+                // source J*32 + (l + d) mod 32.  The source-side sum rotates one lane down
+                // per step, so lane l always holds the sum of the source it meets.
+                // Diagonal units (I = J) run d = 1 .. 16 (at d = 16 only lanes < 16, since
+                // lanes l and l + 16 meet the same pair); off-diagonal blocks run d = 0 .. 31
+                // as two units.  Each warp adds its units' sums into its own partial array,
+                // in a fixed order, so the result does not depend on scheduling.
+                const float4 *s4 = (const float4 *)src;
+                const float4 *t1 = (const float4 *)tabraw;
+                const float2 *t2 = (const float2 *)(t1 + P);
+                const float fid2 = (float)inv_d2;
+                const int warp = tid >> 5;
+                float2 *mypart = part + warp * (nb << 5);
+                for (int k = lane; k < (nb << 5); k += 32) mypart[k] = make_float2(0.f, 0.f);
+                const int nxt = (lane + 1) & 31;
+                const float half_mask = lane < 16 ? 1.f : 0.f;
+                for (int un = warp; un < n_units; un += n_pw) {
+                    int I, Jb, d0;
+                    if (un < nb) {
+                        I = Jb = un;
+                        d0 = 1;
+                    } else {
+                        // off-diagonal block pairs in circulant order: {r, r + k} for
+                        // k = 1 .. (nb - 1) / 2, then {r, r + nb / 2} for r < nb / 2 (even nb)
+                        const int v = (un - nb) >> 1, half = (nb - 1) >> 1, full = nb * half;
+                        d0 = ((un - nb) & 1) << 4;
+                        if (v < full) {
+                            const int kk = v / nb;
+                            I = v - kk * nb;
+                            Jb = I + kk + 1;
+                            if (Jb >= nb) Jb -= nb;
+                        } else {
+                            I = v - full;
+                            Jb = I + (nb >> 1);
+                        }
+                    }
+                    const bool diag = I == Jb;
+                    const float4 me = s4[(I << 6) + lane];
+                    const float4 *sp = s4 + (Jb << 6) + lane + d0;
+                    float vx = 0.f, vy = 0.f, ax = 0.f, ay = 0.f;
+#pragma unroll
+                    for (int s = 0; s < 16; ++s) {
+                        const float4 q = sp[s];
+                        const float dx = me.x - q.x, dy = me.y - q.y;
+                        const float u = fmaf(fmaf(dx, dx, dy * dy), fid2, 1.0f);
+                        float g1, g2;
+                        kern_f32(t1, t2, npan - 1, u, g1, g2);
+                        if (s == 15 && diag) {
+                            g1 *= half_mask;
+                            g2 *= half_mask;
+                        }
+                        const float wj = fmaf(q.z, dx, q.w * dy) * g2;
+                        const float wi = fmaf(me.z, dx, me.w * dy) * g2;
+                        vx = fmaf(wj, dx, fmaf(-q.z, g1, vx));
+                        vy = fmaf(wj, dy, fmaf(-q.w, g1, vy));
+                        ax = fmaf(wi, dx, fmaf(-me.z, g1, ax));
+                        ay = fmaf(wi, dy, fmaf(-me.w, g1, ay));
+                        ax = __shfl_sync(0xffffffffu, ax, nxt);
+                        ay = __shfl_sync(0xffffffffu, ay, nxt);
+                    }
+                    // lane l now holds the sum of source J*32 + (l + d0 + 16) mod 32
+                    const int from = (lane - d0 - 16) & 31;
+                    ax = __shfl_sync(0xffffffffu, ax, from);
+                    ay = __shfl_sync(0xffffffffu, ay, from);
+                    if (diag) {
+                        vx += ax;
+                        vy += ay;
+                    }
+                    float2 pv = mypart[(I << 5) + lane];
+                    pv.x += vx;
+                    pv.y += vy;
+                    mypart[(I << 5) + lane] = pv;
+                    if (!diag) {
+                        float2 pa = mypart[(Jb << 5) + lane];
+                        pa.x += ax;
+                        pa.y += ay;
+                        mypart[(Jb << 5) + lane] = pa;
+                    }
                 }
             }
+            if (!F64) __syncthreads();
             // ---- E: Euler step, divergence, observations
-            if (owner) {
-                const bool head_obs = (tgt == n - 1) && ((step + 1) % a.obs_every == 0);
+            for (int k = F64 ? (owner ? tgt : n) : tid; k < n; k += F64 ? n : T) {
+                const bool head_obs = (k == n - 1) && ((step + 1) % a.obs_every == 0);
                 double hxo = 0.0, hyo = 0.0;
                 if (F64) {
                     double dx = vxd * dt_mu, dy = vyd * dt_mu;  // displacement this step
                     if (!isfinite(dx) || !isfinite(dy) || fmax(fabs(dx), fabs(dy)) > ds) bad = 1;
-                    sx[tgt] += dx;
-                    sy[tgt] += dy;
-                    hxo = sx[tgt];
-                    hyo = sy[tgt];
+                    sx[k] += dx;
+                    sy[k] += dy;
+                    hxo = sx[k];
+                    hyo = sy[k];
                 } else {
-                    float dx = vxf * dt_mu_f, dy = vyf * dt_mu_f;
+                    // v_k = self term + the pair warps' partial sums, compensated
+                    const float4 me = ((const float4 *)src)[((k >> 5) << 6) + (k & 31)];
+                    float hx = -me.z * g10, lx = 0.f, hy = -me.w * g10, ly = 0.f;
+                    for (int w = 0; w < n_pw; ++w) {
+                        const float2 pv = part[w * (nb << 5) + k];
+                        acc_two_sum(hx, lx, pv.x);
+                        acc_two_sum(hy, ly, pv.y);
+                    }
+                    float dx = (hx + lx) * dt_mu_f, dy = (hy + ly) * dt_mu_f;
                     if (!isfinite(dx) || !isfinite(dy) || fmaxf(fabsf(dx), fabsf(dy)) > ds_f) bad = 1;
                     float s, e, nh, nl;
-                    two_sum(xh[tgt], dx, s, e);
-                    two_sum(s, xl[tgt] + e, nh, nl);
-                    xh[tgt] = nh;
-                    xl[tgt] = nl;
-                    two_sum(yh[tgt], dy, s, e);
-                    two_sum(s, yl[tgt] + e, nh, nl);
-                    yh[tgt] = nh;
-                    yl[tgt] = nl;
+                    two_sum(xh[k], dx, s, e);
+                    two_sum(s, xl[k] + e, nh, nl);
+                    xh[k] = nh;
+                    xl[k] = nl;
+                    two_sum(yh[k], dy, s, e);
+                    two_sum(s, yl[k] + e, nh, nl);
+                    yh[k] = nh;
+                    yl[k] = nl;
                     if (head_obs) {
-                        hxo = (double)xh[tgt] + (double)xl[tgt];
-                        hyo = (double)yh[tgt] + (double)yl[tgt];
+                        hxo = (double)xh[k] + (double)xl[k];
+                        hyo = (double)yh[k] + (double)yl[k];
                     }
                 }
                 if (head_obs) {
@@ -519,7 +625,7 @@ __global__ void __launch_bounds__(1024) forward_kernel(FwdArgs a) {
             else
                 atomicAdd(a.work + 1, wk);
         }
-        if (owner && tgt == n - 1) {
+        if (head_thread) {
             a.status[b] = status;
             if (a.loglik) {
                 double s2 = a.sigma * a.sigma;
@@ -539,9 +645,16 @@ __global__ void __launch_bounds__(1024) forward_kernel(FwdArgs a) {
 
 }  // namespace
 
-// Threads per sample: at least one per target; more (a source split of S = threads/n
-// lanes per target, combined by warp shuffles) when the batch is too small to fill the GPU,
-// so that the per-step latency of a lone sample shrinks.  The autotuned choice wins.
+// Threads per sample: at least one per target (FP64) or one warp per pair unit (FP32);
+// more when the batch is too small to fill the GPU, so that the per-step latency of a lone
+// sample shrinks, as long as the shared memory fits.  The autotuned choice wins.
+bool forward_fits(const swimmer_handle *h, int threads, int precision) {
+    const bool f64 = precision == SWIMMER_FP64;
+    const int P = handle_octaves(h) * (f64 ? F64_SUB : F32_SUB);
+    size_t smem = f64 ? smem_bytes<true>(h->cfg.n_max, P, threads) : smem_bytes<false>(h->cfg.n_max, P, threads);
+    return smem + 1024 <= (size_t)h->max_smem;  // static shared memory of the kernel
+}
+
 int forward_threads(const swimmer_handle *h, int B, int precision) {
     int bucket = 0;
     while ((2 << bucket) <= B && bucket < 16) ++bucket;
@@ -550,7 +663,13 @@ int forward_threads(const swimmer_handle *h, int B, int precision) {
     while (T < h->cfg.n_max && T < 1024) T <<= 1;
     if (T < 128) T = 128;
     if (tuned >= T && tuned <= 1024) return tuned;
-    while (T < 1024 && (long long)B * T * 2 <= (long long)h->num_sms * 1024) T <<= 1;
+    int cap = 1024;
+    if (precision != SWIMMER_FP64) {  // warps beyond the pair units only help the O(N) phases
+        const int nbm = (h->cfg.n_max + 31) / 32;
+        while (cap > T && cap / 2 >= 32 * nbm * nbm) cap /= 2;
+    }
+    while (T < cap && (long long)B * T * 2 <= (long long)h->num_sms * 1024 && forward_fits(h, 2 * T, precision))
+        T <<= 1;
     return T;
 }
 
@@ -585,9 +704,11 @@ int launch_forward(swimmer_handle *h, int B, const double *obs, double sigma, do
     a.threads = T;
     const bool f64 = precision == SWIMMER_FP64;
     a.tab_panels = handle_octaves(h) * (f64 ? F64_SUB : F32_SUB);
-    size_t smem = f64 ? smem_bytes<true>(a.n_max, a.tab_panels) : smem_bytes<false>(a.n_max, a.tab_panels);
+    size_t smem = f64 ? smem_bytes<true>(a.n_max, a.tab_panels, T) : smem_bytes<false>(a.n_max, a.tab_panels, T);
     auto kern = f64 ? forward_kernel<true> : forward_kernel<false>;
     CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                  cudaSharedmemCarveoutMaxShared));
     int per_sm = 0;
     CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, T, smem));
     if (per_sm < 1) {
