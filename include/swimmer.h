@@ -136,11 +136,20 @@ int forward_batch(swimmer_handle *h, int B, const double *theta, const int *n_pt
 /* Autotuner for the forward kernel's launch shape: for batch sizes B = 1, 2, 4, ...,
  * b_max it times the kernel (handle's precision, `steps` Euler steps, representative
  * parameters) with every admissible number of threads per sample (a power of two from
- * the smallest that covers n_max up to 1024; the extra threads split the source loop)
- * and stores the fastest per batch-size bucket in the handle.  out_threads (host, may be
- * NULL) receives one entry per bucket.  Synchronous; allocates and frees temporary device
- * memory; must not run during stream capture.  Untuned handles use a heuristic. */
+ * the smallest that covers n_max up to 1024 or the shared-memory limit; the extra threads
+ * take more pair units in FP32 and split the source loop in FP64) and stores the fastest
+ * per batch-size bucket in the handle.  out_threads (host, may be NULL) receives one entry
+ * per bucket.  Synchronous; allocates and frees temporary device memory; must not run
+ * during stream capture.  Untuned handles use a heuristic. */
 int swimmer_autotune(swimmer_handle *h, int steps, int *out_threads);
+
+/* Read (set = 0) or replace (set = 1) the handle's launch-shape table for one precision
+ * (SWIMMER_FP64 or SWIMMER_FP32C): threads[k] = threads per sample for batches of
+ * 2^k <= B < 2^(k+1), k = 0..16 (host array of 17).  0 means "use the heuristic".  Set
+ * entries must be 0 or a power of two from 32 to 1024 whose shared memory fits the
+ * device, else SWIMMER_E_ARG and nothing changes.  Lets a caller keep autotuned shapes
+ * across handles or processes. */
+int swimmer_tuning(swimmer_handle *h, int precision, int *threads, int set);
 
 /* Batched log-likelihood (Sec. 3.1, Eqs. likelihood/fitness with Sigma = sigma^2 I):
  *   loglik[b] = -(m/2) ln(2 pi sigma^2) - sum_o |D_o - head_o(theta_b)|^2 / (2 sigma^2),
@@ -192,6 +201,14 @@ typedef struct tmcmc_state {
  * Synchronizes `stream` twice (chain lengths decide the launches; counters at the end). */
 int tmcmc_stage(swimmer_handle *h, tmcmc_state *st, const double *uniforms, const double *normals,
                 int use_surrogate, void *stream);
+
+/* The decision tree tmcmc_stage pre-fetches for each live chain (host only, no device
+ * work): the root plus M - 1 nodes chosen best-first by the probability that a chain
+ * accepting each proposal with probability p_accept follows the path to them, depth below
+ * depth_cap (1..31).  nodes (host, 4 M ints): per node {parent (-1 for the root),
+ * 2 depth + (1 if it is its parent's accept child), accept child, reject child} (-1 when
+ * absent); *count = nodes built (fewer than M when the depth cap runs out). */
+int tmcmc_tree_template(int M, double p_accept, int depth_cap, int *nodes, int *count);
 
 /* Stage pieces, exposed for testing (Algorithm 1 'Analyze' and 'Resample'):
  * tmcmc_analyze: from loglik[B] (device), theta[B][3] (device) and q (host) compute on the

@@ -8,5 +8,5 @@ from .api import (FP32C, FP64, MLP_NPARAM, ForwardGraph, Handle, SwimmerConfig, 
                   loglik_batch, mlp_adam, mlp_backward, mlp_forward, mlp_workspace, surrogate_loglik_batch,
                   swimmer_destroy, swimmer_init, swimmer_kernel_eval, swimmer_surrogate_set, tmcmc_analyze,
                   swimmer_autotune, swimmer_kernel_eval_noalloc, swimmer_profile,
-                  swimmer_profile_launches, tmcmc_resample, tmcmc_run,
+                  swimmer_profile_launches, swimmer_tuning, tmcmc_resample, tmcmc_tree_template, tmcmc_run,
                   tmcmc_stage)

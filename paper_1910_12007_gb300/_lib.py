@@ -42,8 +42,10 @@ SIGNATURES = [
     ("swimmer_kernel_eval_noalloc", c_int, [c_double, c_double, c_double, c_int, c_void_p, c_void_p, c_void_p, c_int, c_void_p]),
     ("forward_batch", c_int, [c_void_p, c_int, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     ("swimmer_autotune", c_int, [c_void_p, c_int, c_void_p]),
+    ("swimmer_tuning", c_int, [c_void_p, c_int, c_void_p, c_int]),
     ("loglik_batch", c_int, [c_void_p, c_int, c_void_p, c_void_p, c_void_p, c_double, c_void_p, c_void_p, c_void_p]),
     ("tmcmc_stage", c_int, [c_void_p, P(TmcmcStateC), c_void_p, c_void_p, c_int, c_void_p]),
+    ("tmcmc_tree_template", c_int, [c_int, c_double, c_int, c_void_p, c_void_p]),
     ("tmcmc_analyze", c_int, [c_void_p, c_int, c_void_p, c_void_p, c_double, c_void_p, c_void_p, c_void_p]),
     ("tmcmc_resample", c_int, [c_void_p, c_int, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     ("mlp_workspace_bytes", ctypes.c_size_t, [c_int]),

@@ -195,6 +195,16 @@ class TmcmcState:
                     n_exact_path=c.n_exact_path)
 
 
+def tmcmc_tree_template(M, p_accept, depth_cap):
+    """The pre-fetch decision tree (host only): list of (parent, depth, is_accept_child,
+    accept_child, reject_child) for up to M nodes, root first."""
+    buf = (ctypes.c_int * (4 * M))()
+    count = ctypes.c_int(0)
+    check(lib().tmcmc_tree_template(int(M), float(p_accept), int(depth_cap), buf, ctypes.byref(count)))
+    return [(buf[4 * v], buf[4 * v + 1] >> 1, buf[4 * v + 1] & 1, buf[4 * v + 2], buf[4 * v + 3])
+            for v in range(count.value)]
+
+
 def tmcmc_stage(h: Handle, st: TmcmcState, uniforms, normals, use_surrogate=False, stream=None):
     """One TMCMC stage on the device; uniforms [3, B], normals [B, 3] (FP64, device)."""
     _dev(uniforms, torch.float64)
@@ -319,6 +329,23 @@ def swimmer_autotune(h: Handle, steps=200):
         B <<= 1
         k += 1
     return res
+
+
+def swimmer_tuning(h: Handle, precision=None, threads=None):
+    """Get (threads=None) or set the launch-shape table of one precision: a list of 17
+    threads-per-sample entries, entry k for batches 2^k <= B < 2^(k+1), 0 = heuristic."""
+    prec = h.cfg.precision if precision is None else precision
+    buf = (ctypes.c_int * 17)()
+    if threads is None:
+        check(lib().swimmer_tuning(h.ptr, int(prec), buf, 0))
+        return list(buf)
+    vals = list(threads)
+    if len(vals) != 17:
+        raise ValueError("threads needs 17 entries")
+    for k, v in enumerate(vals):
+        buf[k] = int(v)
+    check(lib().swimmer_tuning(h.ptr, int(prec), buf, 1))
+    return vals
 
 
 def swimmer_kernel_eval_noalloc(alpha, delta, r_max, r: torch.Tensor, precision=FP64, g1=None, g2=None,

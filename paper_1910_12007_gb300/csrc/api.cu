@@ -164,8 +164,10 @@ extern "C" int swimmer_init(const swimmer_config *cfg, swimmer_handle **out) {
     ALLOC(h->out_ll, B);
     ALLOC(h->out_sl, B);
     ALLOC(h->prop_status, B);
-    ALLOC(h->active, B);
-    ALLOC(h->active2, B);
+    ALLOC(h->live, B);
+    ALLOC(h->chain_pos, B);
+    ALLOC(h->tmpl, B);
+    h->p_accept = 0.8;
     ALLOC(h->cum, B);
     ALLOC(h->info, 128);
     ALLOC(h->work, 2);
@@ -178,7 +180,8 @@ extern "C" int swimmer_init(const swimmer_config *cfg, swimmer_handle **out) {
     {
         cudaError_t e1 = cudaMallocHost((void **)&h->host_pinned, (B + 128) * sizeof(int));
         cudaError_t e2 = cudaMallocHost((void **)&h->host_pinned_d, 64 * sizeof(double));
-        if (e1 != cudaSuccess || e2 != cudaSuccess) {
+        cudaError_t e3 = cudaMallocHost((void **)&h->host_tmpl, B * sizeof(int4));
+        if (e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess) {
             set_error("cudaMallocHost failed");
             swimmer_destroy(h);
             return SWIMMER_E_CUDA;
@@ -200,12 +203,13 @@ extern "C" int swimmer_destroy(swimmer_handle *h) {
     void *ptrs[] = {h->tab64, h->k1_scratch, h->tab32, h->sp, h->order, h->queue, h->speed_tmp, h->w, h->stats,
                     h->idx, h->counts, h->chain_id, h->chain_off, h->chain_len, h->aux,
                     h->cur_theta, h->cur_ll, h->cur_sl, h->prop_theta, h->prop_ll, h->prop_sl,
-                    h->out_theta, h->out_ll, h->out_sl, h->prop_status, h->active, h->active2, h->cum, h->info, h->work, h->run_work,
+                    h->out_theta, h->out_ll, h->out_sl, h->prop_status, h->live, h->chain_pos, h->tmpl, h->cum, h->info, h->work, h->run_work,
                     h->surr_norm, h->surr_params, h->surr_x, h->surr_y, h->surr_ws};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (h->host_pinned) cudaFreeHost(h->host_pinned);
     if (h->host_pinned_d) cudaFreeHost(h->host_pinned_d);
+    if (h->host_tmpl) cudaFreeHost(h->host_tmpl);
     if (h->prof) {
         for (cudaEvent_t e : h->prof->start) cudaEventDestroy(e);
         for (cudaEvent_t e : h->prof->stop) cudaEventDestroy(e);
@@ -252,6 +256,24 @@ int run_forward(swimmer_handle *h, int B, const double *theta, const int *n_pts,
 
 // Autotuner: for batch sizes B = 1, 2, 4, ... up to b_max, time the forward kernel on
 // `steps` Euler steps with every admissible threads-per-sample and keep the fastest.
+extern "C" int swimmer_tuning(swimmer_handle *h, int precision, int *threads, int set) {
+    ARG_CHECK(h != nullptr, "handle is NULL");
+    ARG_CHECK(threads != nullptr, "threads is NULL");
+    ARG_CHECK(precision == SWIMMER_FP64 || precision == SWIMMER_FP32C, "precision must be FP64 or FP32C");
+    int *tab = h->tune_threads[precision == SWIMMER_FP64 ? 0 : 1];
+    if (!set) {
+        for (int k = 0; k < 17; ++k) threads[k] = tab[k];
+        return 0;
+    }
+    for (int k = 0; k < 17; ++k) {
+        const int t = threads[k];
+        ARG_CHECK(t == 0 || (t >= 32 && t <= 1024 && (t & (t - 1)) == 0), "threads[%d] = %d is not 0 or a power of two in [32, 1024]", k, t);
+        ARG_CHECK(t == 0 || forward_fits(h, t, precision), "threads[%d] = %d needs more shared memory than the device has", k, t);
+    }
+    for (int k = 0; k < 17; ++k) tab[k] = threads[k];
+    return 0;
+}
+
 extern "C" int swimmer_autotune(swimmer_handle *h, int steps, int *out_threads) {
     ARG_CHECK(h != nullptr, "handle is NULL");
     ARG_CHECK(steps >= 1, "steps must be >= 1");

@@ -69,7 +69,10 @@ struct swimmer_handle {
     double *stats;          // [64]
     int *idx, *counts, *chain_id, *chain_off, *chain_len, *aux;  // [b_max] each, aux [b_max+64]
     double *cur_theta, *cur_ll, *cur_sl, *prop_theta, *prop_ll, *prop_sl, *out_theta, *out_ll, *out_sl;
-    int *prop_status, *active, *active2;
+    int *prop_status, *live, *chain_pos;  // [b_max] each
+    int4 *tmpl;                           // device [b_max]: pre-fetch template tree
+    int4 *host_tmpl;                      // pinned host [b_max]
+    double p_accept;                      // running Metropolis acceptance rate estimate
     unsigned long long *cum;  // [b_max] fixed-point prefix sums
     int *info;              // [128] device counters / host-visible summary
     int *host_pinned;       // pinned host scratch (b_max + 128 ints)
@@ -119,6 +122,7 @@ int launch_forward(swimmer_handle *h, int B, const double *obs, double sigma, do
                    cudaStream_t s, int threads_override = 0, int speculative = 0);
 int forward_threads(const swimmer_handle *h, int B, int precision);
 bool forward_fits(const swimmer_handle *h, int threads, int precision);
+int forward_slots(const swimmer_handle *h, int precision);
 int launch_kernel_eval(swimmer_handle *h, int m, const double *r, double *g1, double *g2,
                        int precision, cudaStream_t s);
 int gl_init();

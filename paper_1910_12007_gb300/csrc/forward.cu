@@ -655,6 +655,25 @@ bool forward_fits(const swimmer_handle *h, int threads, int precision) {
     return smem + 1024 <= (size_t)h->max_smem;  // static shared memory of the kernel
 }
 
+// Samples the forward kernel runs at once on the device (resident CTAs at the launch shape
+// of a large batch); at least one per SM.
+int forward_slots(const swimmer_handle *h, int precision) {
+    const bool f64 = precision == SWIMMER_FP64;
+    const int T = forward_threads(h, 1 << 30, precision);
+    const int P = handle_octaves(h) * (f64 ? F64_SUB : F32_SUB);
+    size_t smem = f64 ? smem_bytes<true>(h->cfg.n_max, P, T) : smem_bytes<false>(h->cfg.n_max, P, T);
+    auto kern = f64 ? forward_kernel<true> : forward_kernel<false>;
+    int per_sm = 0;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
+        cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared) !=
+            cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, T, smem) != cudaSuccess || per_sm < 1) {
+        cudaGetLastError();  // clear the error state a failed query leaves
+        per_sm = 1;
+    }
+    return per_sm * h->num_sms;
+}
+
 int forward_threads(const swimmer_handle *h, int B, int precision) {
     int bucket = 0;
     while ((2 << bucket) <= B && bucket < 16) ++bucket;

@@ -18,6 +18,9 @@
 //   with min(1, exp(q (l' - l) - q (l~' - l~))).
 #include <math.h>
 
+#include <algorithm>
+#include <vector>
+
 #include "common.cuh"
 
 int run_forward(swimmer_handle *h, int B, const double *theta, const int *n_pts, const double *obs,
@@ -309,15 +312,18 @@ __global__ void __launch_bounds__(T1) chains_kernel(int B, const int *__restrict
 }
 
 // ---------------------------------------------------------------------------------
-// Metropolis chain steps with pre-fetching.  A chain at step s will either move to its
-// proposal or stay; the proposal of step s+1 is base + L z[row s+1] for whichever base that
-// decision leaves.  Evaluating the forward model for every node of the decision tree of depth
-// k (2^(k+1) - 1 candidates) in one batched launch lets one launch resolve k + 1 chain steps
-// exactly as the sequential chain would (the random inputs of each row are fixed in
-// advance).  Node q of a tree: level l = floor(log2(q + 1)), decision bits b = q + 1 - 2^l,
-// first decision most significant.  k = 0 is the plain one-step-per-launch chain.
+// Metropolis chain steps with pre-fetching.  A chain at step s either moves to its proposal
+// or stays; the proposal of step s+1 is base + L z[row s+1] for whichever base that decision
+// leaves.  Evaluating the forward model for several nodes of this decision tree in one
+// batched launch lets one launch resolve several chain steps exactly as the sequential
+// chain would (the random inputs of every row are fixed in advance).  The host picks the
+// nodes: a template tree shared by all live chains, grown best-first by the probability
+// that the chain's actual path reaches a node (acceptance rate estimated from the stage so
+// far).  Template node v: x = parent (-1 for the root), y = 2 depth + (1 if v is the
+// parent's accept child), z = accept child, w = reject child (-1 when absent).  Chains
+// advance by different numbers of steps; chain_pos holds each chain's progress.
 // ---------------------------------------------------------------------------------
-__device__ __forceinline__ int node_level(int q) { return 31 - __clz(q + 1); }
+constexpr int TREE_DEPTH_MAX = 31;
 
 __device__ __forceinline__ void add_step(const double *L, const double *z, const double *base, double *out) {
     out[0] = base[0] + L[0] * z[0] + L[1] * z[1] + L[2] * z[2];
@@ -332,34 +338,86 @@ struct Box {
     }
 };
 
-// candidates of all nodes: prop[(slot*NC + q)*3].  Unreachable nodes (an accepted decision on
-// the path whose candidate lies outside the prior box), nodes beyond the chain's length and
-// candidates outside the box get a NaN alpha, which the forward launch skips.
-__global__ void spec_propose_kernel(int A, int s, int k, const int *__restrict__ order, const int *__restrict__ chain_off,
-                                    const int *__restrict__ chain_len, const double *__restrict__ cur_theta,
-                                    const double *__restrict__ st, const double *__restrict__ normals, Box box,
+// path of template node v from the root: path[0] = root, path[depth] = v
+__device__ __forceinline__ int tree_path(const int4 *__restrict__ tmpl, int v, int *path) {
+    const int depth = tmpl[v].y >> 1;
+    for (int d = depth, u = v; d >= 0; --d) {
+        path[d] = u;
+        u = tmpl[u].x;
+    }
+    return depth;
+}
+
+// live chains (chain_pos < chain_len) in the longest-first order, their number, the
+// largest remaining length, and the stage's accepted / decided steps so far
+__global__ void __launch_bounds__(T1) live_kernel(int U, const int *__restrict__ order, const int *__restrict__ chain_len,
+                                                  const int *__restrict__ chain_pos, int *__restrict__ live,
+                                                  const int *__restrict__ counter, int *__restrict__ host_info) {
+    __shared__ unsigned long long sm[64];
+    __shared__ int s_rem, s_dec;
+    const int tid = threadIdx.x;
+    if (tid == 0) {
+        s_rem = 0;
+        s_dec = 0;
+    }
+    const int chunk = (U + T1 - 1) / T1;
+    const int lo = min(U, tid * chunk), hi = min(U, lo + chunk);
+    unsigned long long cnt = 0;
+    int rem = 0, dec = 0;
+    for (int i = lo; i < hi; ++i) {
+        const int c = order[i];
+        const int r = chain_len[c] - chain_pos[c];
+        cnt += r > 0;
+        rem = max(rem, r);
+        dec += chain_pos[c];
+    }
+    unsigned long long total;
+    unsigned long long at = block_exscan(cnt, sm, &total);
+    atomicMax(&s_rem, rem);
+    atomicAdd(&s_dec, dec);
+    for (int i = lo; i < hi; ++i) {
+        const int c = order[i];
+        if (chain_len[c] > chain_pos[c]) live[at++] = c;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        host_info[0] = (int)total;
+        host_info[1] = s_rem;
+        host_info[2] = counter[0];  // accepted so far
+        host_info[3] = s_dec;       // decided so far
+    }
+}
+
+// candidates of every (live chain, template node): prop[(slot*M + v)*3].  Unreachable nodes
+// (an accepted decision on the path whose candidate lies outside the prior box), nodes
+// beyond the chain's length and candidates outside the box get a NaN alpha, which the
+// forward launch skips.
+__global__ void tree_propose_kernel(int A, int M, const int *__restrict__ live, const int *__restrict__ chain_off,
+                                    const int *__restrict__ chain_len, const int *__restrict__ chain_pos,
+                                    const double *__restrict__ cur_theta, const double *__restrict__ st,
+                                    const double *__restrict__ normals, Box box, const int4 *__restrict__ tmpl,
                                     double *__restrict__ prop, int *__restrict__ counter) {
-    const int NC = (2 << k) - 1;
     int idx = blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= A * NC) return;
-    const int slot = idx / NC, q = idx % NC;
-    const int c = order[slot];
-    const int l = node_level(q), b = q + 1 - (1 << l);
-    const int off = chain_off[c];
+    if (idx >= A * M) return;
+    const int slot = idx / M, v = idx % M;
+    const int c = live[slot];
+    const int row = chain_off[c] + chain_pos[c];  // normals row of the chain's next step
+    int path[TREE_DEPTH_MAX + 1];
+    const int depth = tree_path(tmpl, v, path);
     const double *L = st + S_L;
     double base[3] = {cur_theta[3 * c], cur_theta[3 * c + 1], cur_theta[3 * c + 2]};
-    bool ok = s + l < chain_len[c];
+    bool ok = chain_pos[c] + depth < chain_len[c];
     double cand[3];
-    for (int i = 0; i < l && ok; ++i) {
-        add_step(L, normals + 3 * (off + s + i), base, cand);
-        if ((b >> (l - 1 - i)) & 1) {
-            if (!box.in(cand)) ok = false;  // that acceptance cannot happen
+    for (int i = 0; i < depth && ok; ++i) {
+        add_step(L, normals + 3 * (row + i), base, cand);
+        if (tmpl[path[i + 1]].y & 1) {  // the path accepts at depth i
+            if (!box.in(cand)) ok = false;
             base[0] = cand[0];
             base[1] = cand[1];
             base[2] = cand[2];
         }
     }
-    add_step(L, normals + 3 * (off + s + l), base, cand);
+    add_step(L, normals + 3 * (row + depth), base, cand);
     ok = ok && box.in(cand);
     prop[3 * idx] = ok ? cand[0] : nan("");
     prop[3 * idx + 1] = cand[1];
@@ -367,65 +425,68 @@ __global__ void spec_propose_kernel(int A, int s, int k, const int *__restrict__
     if (ok) atomicAdd(counter, 1);
 }
 
-// surrogate log-likelihood of the base state of node (l, b): the candidate of the deepest
-// accepted decision on the path, else the chain's current state
-__device__ __forceinline__ double base_value(int slot, int NC, int l, int b, const double *node_val, double cur) {
-    for (int i = l - 1; i >= 0; --i)
-        if ((b >> (l - 1 - i)) & 1) {
-            int qi = (1 << i) - 1 + (b >> (l - i));
-            return node_val[slot * NC + qi];
-        }
-    return cur;
-}
-
-// delayed acceptance step 1 for every node: proposals failing the surrogate screen against
-// their base are marked NaN (not run)
-__global__ void spec_screen_kernel(int A, int s, int k, const int *__restrict__ order, const int *__restrict__ chain_off,
-                                   const double *__restrict__ cur_sl, const double *__restrict__ prop_sl,
-                                   const double *__restrict__ st, const double *__restrict__ u1, double *__restrict__ prop,
-                                   int *__restrict__ counter) {
-    const int NC = (2 << k) - 1;
+// delayed acceptance step 1: along the path of each node, every decision is screened by the
+// surrogate against its base (the candidate of the deepest accepted decision above it, else
+// the chain's state).  A node is not run when its own candidate fails the screen or when its
+// path accepts a candidate that fails it (that path cannot happen).
+__global__ void tree_screen_kernel(int A, int M, const int *__restrict__ live, const int *__restrict__ chain_off,
+                                   const int *__restrict__ chain_pos, const double *__restrict__ cur_sl,
+                                   const double *__restrict__ prop_sl, const double *__restrict__ st,
+                                   const double *__restrict__ u1, const int4 *__restrict__ tmpl,
+                                   double *__restrict__ prop, int *__restrict__ counter) {
     int idx = blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= A * NC) return;
-    const int slot = idx / NC, q = idx % NC;
-    const int c = order[slot];
-    const int l = node_level(q), b = q + 1 - (1 << l);
-    const int pos = chain_off[c] + s + l;
+    if (idx >= A * M) return;
     if (isnan(prop[3 * idx])) return;
-    double bsl = base_value(slot, NC, l, b, prop_sl, cur_sl[c]);
-    bool pass = log(u1[pos]) < st[S_QN] * (prop_sl[idx] - bsl);
+    const int slot = idx / M, v = idx % M;
+    const int c = live[slot];
+    const int row = chain_off[c] + chain_pos[c];
+    const double qn = st[S_QN];
+    int path[TREE_DEPTH_MAX + 1];
+    const int depth = tree_path(tmpl, v, path);
+    double bsl = cur_sl[c];
+    bool reach = true;
+    for (int i = 0; i < depth && reach; ++i) {
+        const double a_sl = prop_sl[slot * M + path[i]];
+        if (tmpl[path[i + 1]].y & 1) {
+            if (!(log(u1[row + i]) < qn * (a_sl - bsl))) reach = false;
+            bsl = a_sl;
+        }
+    }
+    const bool pass = reach && log(u1[row + depth]) < qn * (prop_sl[idx] - bsl);
     if (!pass) prop[3 * idx] = nan("");
     else atomicAdd(counter, 1);
 }
 
-// walk each chain's tree along the decisions it actually takes
-__global__ void spec_resolve_kernel(int A, int s, int k, int delayed, const int *__restrict__ order,
+// walk each live chain down the template along the decisions it actually takes
+__global__ void tree_resolve_kernel(int A, int M, int delayed, const int *__restrict__ live,
                                     const int *__restrict__ chain_off, const int *__restrict__ chain_len,
-                                    double *__restrict__ cur_theta, double *__restrict__ cur_ll,
-                                    double *__restrict__ cur_sl, const double *__restrict__ prop,
-                                    const double *__restrict__ prop_ll, const double *__restrict__ prop_sl,
-                                    const int *__restrict__ prop_status, const double *__restrict__ st,
-                                    const double *__restrict__ u_acc, double *__restrict__ out_theta,
+                                    int *__restrict__ chain_pos, double *__restrict__ cur_theta,
+                                    double *__restrict__ cur_ll, double *__restrict__ cur_sl,
+                                    const double *__restrict__ prop, const double *__restrict__ prop_ll,
+                                    const double *__restrict__ prop_sl, const int *__restrict__ prop_status,
+                                    const double *__restrict__ st, const double *__restrict__ u_acc,
+                                    const int4 *__restrict__ tmpl, double *__restrict__ out_theta,
                                     double *__restrict__ out_ll, double *__restrict__ out_sl, int *__restrict__ counter,
                                     const unsigned long long *__restrict__ run_work,
                                     unsigned long long *__restrict__ useful) {
-    const int NC = (2 << k) - 1;
     int slot = blockIdx.x * blockDim.x + threadIdx.x;
     if (slot >= A) return;
-    const int c = order[slot];
+    const int c = live[slot];
     const double qn = st[S_QN];
-    int b = 0, acc = 0, ran = 0;
+    const int len = chain_len[c];
+    int p = chain_pos[c];
+    int v = 0, acc = 0, ran = 0;
     unsigned long long work = 0;
-    for (int l = 0; l <= k && s + l < chain_len[c]; ++l) {
-        const int idx = slot * NC + (1 << l) - 1 + b;
-        const int pos = chain_off[c] + s + l;
-        bool run = !isnan(prop[3 * idx]);  // the one-step chain would have run this proposal
+    while (v >= 0 && p < len) {
+        const int idx = slot * M + v;
+        const int pos = chain_off[c] + p;
+        const bool run = !isnan(prop[3 * idx]);  // the one-step chain would have run this proposal
         ran += run;
         if (run) work += run_work[idx];
-        bool valid = run && prop_status[idx] == SWIMMER_OK;
+        const bool valid = run && prop_status[idx] == SWIMMER_OK;
         double thr = qn * (prop_ll[idx] - cur_ll[c]);
         if (delayed) thr -= qn * (prop_sl[idx] - cur_sl[c]);
-        bool accept = valid && log(u_acc[pos]) < thr;
+        const bool accept = valid && log(u_acc[pos]) < thr;
         if (accept) {
             cur_theta[3 * c] = prop[3 * idx];
             cur_theta[3 * c + 1] = prop[3 * idx + 1];
@@ -439,14 +500,71 @@ __global__ void spec_resolve_kernel(int A, int s, int k, int delayed, const int 
         out_theta[3 * pos + 2] = cur_theta[3 * c + 2];
         out_ll[pos] = cur_ll[c];
         out_sl[pos] = cur_sl[c];
-        b = 2 * b + (accept ? 1 : 0);
+        ++p;
+        v = accept ? tmpl[v].z : tmpl[v].w;
     }
+    chain_pos[c] = p;
     if (acc) atomicAdd(counter, acc);
     if (ran) atomicAdd(counter + 3, ran);
     if (work) atomicAdd(useful, work);
 }
 
+// Best-first decision tree of M nodes (host): the root, then repeatedly the candidate child
+// with the largest probability of lying on the chain's path, an accepted step having
+// probability p.  Depth < depth_cap.  Ties go to the earlier candidate.
+int build_template(int M, double p, int depth_cap, int4 *t) {
+    struct Cand {
+        double prob;
+        int parent, accept, seq;
+    };
+    std::vector<Cand> heap;
+    auto less = [](const Cand &a, const Cand &b) { return a.prob < b.prob || (a.prob == b.prob && a.seq > b.seq); };
+    std::vector<double> prob(M);
+    int seq = 0;
+    t[0] = make_int4(-1, 0, -1, -1);
+    prob[0] = 1.0;
+    auto push_children = [&](int v) {
+        if ((t[v].y >> 1) + 1 >= depth_cap) return;
+        heap.push_back({prob[v] * p, v, 1, seq++});
+        std::push_heap(heap.begin(), heap.end(), less);
+        heap.push_back({prob[v] * (1.0 - p), v, 0, seq++});
+        std::push_heap(heap.begin(), heap.end(), less);
+    };
+    push_children(0);
+    int n = 1;
+    while (n < M && !heap.empty()) {
+        std::pop_heap(heap.begin(), heap.end(), less);
+        Cand cd = heap.back();
+        heap.pop_back();
+        const int depth = (t[cd.parent].y >> 1) + 1;
+        t[n] = make_int4(cd.parent, 2 * depth + cd.accept, -1, -1);
+        prob[n] = cd.prob;
+        if (cd.accept) t[cd.parent].z = n;
+        else t[cd.parent].w = n;
+        push_children(n);
+        ++n;
+    }
+    return n;
+}
+
 }  // namespace
+
+extern "C" int tmcmc_tree_template(int M, double p_accept, int depth_cap, int *nodes, int *count) {
+    ARG_CHECK(M >= 1, "M must be >= 1");
+    ARG_CHECK(p_accept > 0.0 && p_accept < 1.0, "p_accept must be in (0, 1)");
+    ARG_CHECK(depth_cap >= 1 && depth_cap <= TREE_DEPTH_MAX, "depth_cap must be in [1, %d]", TREE_DEPTH_MAX);
+    ARG_CHECK(nodes != nullptr && count != nullptr, "NULL output");
+    std::vector<int4> t(M);
+    const int n = build_template(M, p_accept, depth_cap, t.data());
+    for (int v = 0; v < n; ++v) {
+        nodes[4 * v] = t[v].x;
+        nodes[4 * v + 1] = t[v].y;
+        nodes[4 * v + 2] = t[v].z;
+        nodes[4 * v + 3] = t[v].w;
+    }
+    *count = n;
+    return 0;
+}
 
 extern "C" int tmcmc_analyze(swimmer_handle *h, int B, const double *theta, const double *loglik, double q,
                              double *out_w, double *stats, void *stream) {
@@ -500,8 +618,6 @@ extern "C" int tmcmc_stage(swimmer_handle *h, tmcmc_state *st, const double *uni
         return SWIMMER_E_STATE;
     }
     const int U = h->host_pinned[0], maxlen = h->host_pinned[1];
-    int alive[64];
-    for (int i = 0; i < cap - 2; ++i) alive[i] = h->host_pinned[2 + i];
     const double qn = hs[S_QN];
     // counters: accepted, screen passes (runs with delayed acceptance), proposals run (plain),
     // runs on the realized chain paths
@@ -512,36 +628,38 @@ extern "C" int tmcmc_stage(swimmer_handle *h, tmcmc_state *st, const double *uni
         box.lo[a] = st->prior_lo[a];
         box.hi[a] = st->prior_hi[a];
     }
-    // pre-fetch depth: resolve several chain steps per launch while few chains are alive,
-    // keeping each launch within about two samples per SM (and within b_max)
-    const int spec_cap = min(h->cfg.b_max, 2 * h->num_sms);
-    for (int step = 0; step < maxlen;) {
-        int active;
-        if (step < cap - 2) {
-            active = alive[step];
-        } else {
-            // rare: a chain longer than the host-visible table; count on the host
-            CUDA_TRY(cudaMemcpyAsync(h->host_pinned, h->chain_len, sizeof(int) * U, cudaMemcpyDeviceToHost, s));
-            CUDA_TRY(cudaStreamSynchronize(s));
-            active = 0;
-            for (int c = 0; c < U; ++c) active += h->host_pinned[c] > step;
-        }
-        if (active <= 0) break;
-        int k = 0;
-        while (k < 5 && step + k + 1 < maxlen && active * ((4 << k) - 1) <= spec_cap) ++k;
-        const int NC = (2 << k) - 1, n = active * NC;
+    // pre-fetching: each launch runs up to `slots` forward models (as many as the GPU holds
+    // at once), a best-first template tree of M = slots / live nodes per live chain
+    const int slots = min(h->cfg.b_max, forward_slots(h, h->cfg.precision));
+    CUDA_TRY(cudaMemsetAsync(h->chain_pos, 0, sizeof(int) * U, s));
+    for (int launch = 0;; ++launch) {
+        live_kernel<<<1, T1, 0, s>>>(U, h->chain_id, h->chain_len, h->chain_pos, h->live, h->info + cap,
+                                     h->info + cap + 8);
+        CUDA_TRY(cudaGetLastError());
+        prof_count(h, 1);
+        CUDA_TRY(cudaMemcpyAsync(h->host_pinned, h->info + cap + 8, 4 * sizeof(int), cudaMemcpyDeviceToHost, s));
+        CUDA_TRY(cudaStreamSynchronize(s));
+        const int A = h->host_pinned[0], max_rem = h->host_pinned[1];
+        if (A <= 0) break;
+        // acceptance rate: this stage's decisions so far, shrunk towards the previous stages'
+        const double acc_sofar = h->host_pinned[2], dec_sofar = h->host_pinned[3];
+        const double p_acc = (acc_sofar + 20.0 * h->p_accept) / (dec_sofar + 20.0);
+        const int want = max(1, slots / A);
+        const int M = build_template(want, p_acc, min(max_rem, TREE_DEPTH_MAX), h->host_tmpl);
+        CUDA_TRY(cudaMemcpyAsync(h->tmpl, h->host_tmpl, sizeof(int4) * M, cudaMemcpyHostToDevice, s));
+        const int n = A * M;
         const int grid = (n + 127) / 128;
-        spec_propose_kernel<<<grid, 128, 0, s>>>(active, step, k, h->chain_id, h->chain_off, h->chain_len,
-                                                 h->cur_theta, h->stats, normals, box, h->prop_theta,
+        tree_propose_kernel<<<grid, 128, 0, s>>>(A, M, h->live, h->chain_off, h->chain_len, h->chain_pos,
+                                                 h->cur_theta, h->stats, normals, box, h->tmpl, h->prop_theta,
                                                  h->info + cap + 2);
         CUDA_TRY(cudaGetLastError());
-        prof_count(h, 2);
+        prof_count(h, 1);
         if (use_surrogate) {
             int rc = run_surrogate_loglik(h, n, h->prop_theta, st->obs, st->sigma, h->prop_sl, s);
             if (rc) return rc;
             n_screened += n;
-            spec_screen_kernel<<<grid, 128, 0, s>>>(active, step, k, h->chain_id, h->chain_off, h->cur_sl,
-                                                    h->prop_sl, h->stats, uniforms + B, h->prop_theta,
+            tree_screen_kernel<<<grid, 128, 0, s>>>(A, M, h->live, h->chain_off, h->chain_pos, h->cur_sl,
+                                                    h->prop_sl, h->stats, uniforms + B, h->tmpl, h->prop_theta,
                                                     h->info + cap + 1);
             CUDA_TRY(cudaGetLastError());
             prof_count(h, 1);
@@ -549,13 +667,13 @@ extern "C" int tmcmc_stage(swimmer_handle *h, tmcmc_state *st, const double *uni
         int rc = run_forward(h, n, h->prop_theta, nullptr, st->obs, st->sigma, h->prop_ll, nullptr, nullptr,
                              h->prop_status, s, 1);
         if (rc) return rc;
-        spec_resolve_kernel<<<(active + 127) / 128, 128, 0, s>>>(
-            active, step, k, use_surrogate, h->chain_id, h->chain_off, h->chain_len, h->cur_theta, h->cur_ll,
+        tree_resolve_kernel<<<(A + 127) / 128, 128, 0, s>>>(
+            A, M, use_surrogate, h->live, h->chain_off, h->chain_len, h->chain_pos, h->cur_theta, h->cur_ll,
             h->cur_sl, h->prop_theta, h->prop_ll, h->prop_sl, h->prop_status, h->stats,
-            uniforms + (use_surrogate ? 2 * B : B), h->out_theta, h->out_ll, h->out_sl, h->info + cap, h->run_work,
-            h->work + 1);
+            uniforms + (use_surrogate ? 2 * B : B), h->tmpl, h->out_theta, h->out_ll, h->out_sl, h->info + cap,
+            h->run_work, h->work + 1);
         CUDA_TRY(cudaGetLastError());
-        step += k + 1;
+        prof_count(h, 1);
     }
     CUDA_TRY(cudaMemcpyAsync(st->theta, h->out_theta, 3 * sizeof(double) * B, cudaMemcpyDeviceToDevice, s));
     CUDA_TRY(cudaMemcpyAsync(st->loglik, h->out_ll, sizeof(double) * B, cudaMemcpyDeviceToDevice, s));
@@ -575,5 +693,6 @@ extern "C" int tmcmc_stage(swimmer_handle *h, tmcmc_state *st, const double *uni
     st->n_screened = n_screened;
     st->n_exact = use_surrogate ? h->host_pinned[1] : h->host_pinned[2];
     st->n_exact_path = h->host_pinned[3];
+    if (B > 0) h->p_accept = 0.5 * h->p_accept + 0.5 * (double)st->n_accept / (double)B;
     return 0;
 }
