@@ -213,9 +213,9 @@ def main():
                          "x N=1024 x 4e4 steps; surrogate: delayed-acceptance vs plain TMCMC, 4096 samples/stage")
     args = ap.parse_args()
 
-    rank = int(os.environ.get("RANK", "0"))
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    from paper_1910_12007_gb300 import ranks
+
+    rank, world, local_rank = ranks.rank_env()
     if args.impl == "reference":
         return reference_arm(args, rank)
 
@@ -262,7 +262,7 @@ def main():
         return 0
     h = g.swimmer_init(cfg)
     tuned = g.swimmer_autotune(h, steps=400)  # launch shape per batch-size bucket (untimed)
-    seed0 = 1000 + 97 * rank
+    seed0 = ranks.rank_seed(1000, rank)  # independent TMCMC per rank
 
     # synthetic observations: forward model at theta*, plus 5 % noise (untimed set-up)
     th_true = torch.tensor([THETA_TRUE], dtype=torch.float64, device=dev)
@@ -365,13 +365,8 @@ def main():
     g.swimmer_profile(h, 0)
 
     # ---- aggregate over ranks (max time, summed work)
-    tot = torch.tensor([pairs, stages * B_STAGE, pairs_e2e, pairs_exec], dtype=torch.float64, device=dev)
-    tmax = torch.tensor([ms_total, t3 - t2], dtype=torch.float64, device=dev)
-    if dist is not None:
-        dist.all_reduce(tot, op=dist.ReduceOp.SUM)
-        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
-    pairs_all, samples_all, pairs_e2e_all, pairs_exec_all = tot.tolist()
-    ms_all, e2e_s = tmax.tolist()
+    (pairs_all, samples_all, pairs_e2e_all, pairs_exec_all), (ms_all, e2e_s) = ranks.totals(
+        dist, [pairs, stages * B_STAGE, pairs_e2e, pairs_exec], [ms_total, t3 - t2], device=dev)
 
     if rank == 0:
         peaks, peak_src = load_peaks()
@@ -428,15 +423,22 @@ def forward_workload(args, rank, world, local_rank):
     import paper_1910_12007_gb300 as g
     import synthetic
 
+    from paper_1910_12007_gb300 import ranks
+
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=dev)
     prec = g.FP64 if args.precision == "fp64" else g.FP32C
     if args.workload == "uneven":
         B, steps, ds = 4096, 10000, 1.0 / 255
         n_choices = [64, 128, 256, 512]
         dt = 1e-4 / 512  # dt * lambda_max <= 1 at ds = 1/255, K_C = 1
         cfg = g.SwimmerConfig(n_max=512, b_max=B, ds_fixed=ds, dt=dt, steps=steps, obs_every=steps, precision=prec)
-        ns = synthetic.choice_n(2000 + rank, n_choices, B).astype(np.int32)
+        ns = synthetic.choice_n(ranks.rank_seed(2000, rank), n_choices, B).astype(np.int32)
         lo, hi = PRIOR_LO, (10.0, 0.0, 0.2)
         desc = ("4096 samples, N uniform in {64,128,256,512} at fixed ds=1/255 (L=(N-1)ds), 1e4 steps, "
                 "dt=1e-4/512, one graph-captured persistent launch, longest first")
@@ -449,7 +451,7 @@ def forward_workload(args, rank, world, local_rank):
         desc = "256 samples x N=1024 x 4e4 steps, alpha in [0,50], dt=1e-4/2^15"
     h = g.swimmer_init(cfg)
     tuned = g.swimmer_autotune(h, steps=50)
-    th = torch.tensor(synthetic.prior_samples(3000 + rank, lo, hi, B), device=dev)
+    th = torch.tensor(synthetic.prior_samples(ranks.rank_seed(3000, rank), lo, hi, B), device=dev)
     nsd = torch.tensor(ns, device=dev) if ns is not None else None
     graph = g.ForwardGraph(h, th, nsd)
     for _ in range(args.warmup):
@@ -457,6 +459,9 @@ def forward_workload(args, rank, world, local_rank):
     torch.cuda.synchronize()
     g.swimmer_profile(h, 1)
     clocks = ClockSampler(local_rank)
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
     clocks.start()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record()
@@ -464,6 +469,8 @@ def forward_workload(args, rank, world, local_rank):
         graph.replay()
     e1.record()
     torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
     clk = clocks.stop()
     ms = e0.elapsed_time(e1)
     k2_ms, k2_launches, launches, _, pairs = g.swimmer_profile(h, 2)
@@ -472,6 +479,7 @@ def forward_workload(args, rank, world, local_rank):
         n2 = (ns.astype(np.float64) ** 2).sum() if ns is not None else B * 1024.0 ** 2
         pairs = n2 * steps * args.steps
     status = graph.out[2].cpu().numpy()
+    (pairs, ok_all, samples_all), (ms,) = ranks.totals(dist, [pairs, float(np.sum(status == 0)), B], [ms], device=dev)
     peaks, _ = load_peaks()
     sm = torch.cuda.get_device_properties(dev).multi_processor_count
     fp32_peak = sm * 128 * 2 * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
@@ -485,7 +493,7 @@ def forward_workload(args, rank, world, local_rank):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32" if prec == g.FP32C else "f64",
             "data": "synthetic", "config": {"workload": desc, "precision": args.precision},
-            "clocks": clk, "status_ok_fraction": float(np.mean(status == 0)),
+            "clocks": clk, "status_ok_fraction": ok_all / samples_all,
             "autotuned_threads_per_sample": {str(k): v for k, v in tuned.items()},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
                          "frac": achieved / fp32_peak,
@@ -493,6 +501,8 @@ def forward_workload(args, rank, world, local_rank):
     if rank == 0:
         print(json.dumps(line), flush=True)
     h.close()
+    if dist is not None:
+        dist.destroy_process_group()
     return 0
 
 
@@ -507,6 +517,8 @@ def surrogate_workload(args, rank, world, local_rank):
     import synthetic
     from paper_1910_12007_gb300 import surrogate as sg
 
+    if rank != 0:
+        return 0  # a comparison of two methods on one GPU: rank 0 alone runs it
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
     B = 4096
@@ -551,7 +563,7 @@ def surrogate_workload(args, rank, world, local_rank):
                          "posterior_mean": th.mean(0).tolist(), "posterior_sd": th.std(0).tolist()}
     p, d = results["plain"], results["surrogate"]
     rel_mean = [abs(a - b) / max(abs(b), 1e-12) for a, b in zip(d["posterior_mean"], p["posterior_mean"])]
-    line = {"metric": METRIC, "value": d["samples_per_s"], "unit": "TMCMC samples/s", "n_gpus": world,
+    line = {"metric": METRIC, "value": d["samples_per_s"], "unit": "TMCMC samples/s", "n_gpus": 1,
             "steps": 1, "warmup": 0, "ms_per_step": 1e3 * d["seconds"], "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": "delayed-acceptance TMCMC with the MLP surrogate (trained on 50k forward runs of "
