@@ -133,19 +133,27 @@ int swimmer_kernel_eval_noalloc(double alpha, double delta, double r_max, int m,
 int forward_batch(swimmer_handle *h, int B, const double *theta, const int *n_pts,
                   double *head_traj, double *mean_speed, int *status, void *stream);
 
-/* Autotuner for the forward kernel's launch shape: for batch sizes B = 1, 2, 4, ...,
- * b_max it times the kernel (handle's precision, `steps` Euler steps, representative
- * parameters) with every admissible number of threads per sample (a power of two from
- * the smallest that covers n_max up to 1024 or the shared-memory limit; the extra threads
- * take more pair units in FP32 and split the source loop in FP64) and stores the fastest
- * per batch-size bucket in the handle.  out_threads (host, may be NULL) receives one entry
- * per bucket.  Synchronous; allocates and frees temporary device memory; must not run
- * during stream capture.  Untuned handles use a heuristic. */
-int swimmer_autotune(swimmer_handle *h, int steps, int *out_threads);
+/* Autotuner for the forward kernel's launch shape.  The persistent kernel's time is set by
+ * the number of samples each SM holds, so batch sizes fall into buckets k = 0..16 of
+ * k + 1 samples per SM (ceil(B / SMs) - 1, capped at 16).  For each bucket up to b_max it
+ * times the kernel on B = min((k + 1) SMs, b_max) samples (handle's precision, `steps` Euler
+ * steps) with every admissible number of threads per sample (a
+ * power of two from the smallest that covers n_max up to 1024 or the shared-memory limit;
+ * the extra threads take more pair units in FP32 and split the source loop in FP64) and
+ * stores the fastest in the handle.  The samples are the caller's theta (device, [n_theta][3]
+ * FP64, rows repeated as needed) when given: batches whose runs differ in length (runs that
+ * diverge and stop early) favour shapes with fewer resident samples, whose work queue
+ * rebalances the SMs.  With theta NULL, b_max copies of a mid-prior swimmer are timed.
+ * out_threads (host array of 17, may be NULL) receives the choice per measured bucket, 0
+ * after the last.  Synchronous; allocates and frees
+ * temporary device memory; must not run during stream capture.  Untuned handles use a
+ * heuristic. */
+int swimmer_autotune(swimmer_handle *h, int steps, const double *theta, int n_theta, int *out_threads);
 
 /* Read (set = 0) or replace (set = 1) the handle's launch-shape table for one precision
- * (SWIMMER_FP64 or SWIMMER_FP32C): threads[k] = threads per sample for batches of
- * 2^k <= B < 2^(k+1), k = 0..16 (host array of 17).  0 means "use the heuristic".  Set
+ * (SWIMMER_FP64 or SWIMMER_FP32C): threads[k] = threads per sample for batches holding
+ * k + 1 samples per SM (ceil(B / SMs) = k + 1; k = 16 also takes larger batches), host
+ * array of 17.  0 means "use the heuristic".  Set
  * entries must be 0 or a power of two from 32 to 1024 whose shared memory fits the
  * device, else SWIMMER_E_ARG and nothing changes.  Lets a caller keep autotuned shapes
  * across handles or processes. */

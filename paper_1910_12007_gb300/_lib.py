@@ -41,7 +41,7 @@ SIGNATURES = [
     ("swimmer_kernel_eval", c_int, [c_void_p, c_double, c_double, c_double, c_int, c_void_p, c_void_p, c_void_p, c_int, c_void_p]),
     ("swimmer_kernel_eval_noalloc", c_int, [c_double, c_double, c_double, c_int, c_void_p, c_void_p, c_void_p, c_int, c_void_p]),
     ("forward_batch", c_int, [c_void_p, c_int, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
-    ("swimmer_autotune", c_int, [c_void_p, c_int, c_void_p]),
+    ("swimmer_autotune", c_int, [c_void_p, c_int, c_void_p, c_int, c_void_p]),
     ("swimmer_tuning", c_int, [c_void_p, c_int, c_void_p, c_int]),
     ("loglik_batch", c_int, [c_void_p, c_int, c_void_p, c_void_p, c_void_p, c_double, c_void_p, c_void_p, c_void_p]),
     ("tmcmc_stage", c_int, [c_void_p, P(TmcmcStateC), c_void_p, c_void_p, c_int, c_void_p]),

@@ -318,22 +318,22 @@ def swimmer_profile_launches(h: Handle):
     return [(ms[i], samples[i]) for i in range(n)]
 
 
-def swimmer_autotune(h: Handle, steps=200):
-    """Time the forward kernel's launch shapes per batch-size bucket; returns
-    {batch size: threads per sample} for B = 1, 2, 4, ..., b_max."""
+def swimmer_autotune(h: Handle, steps=200, theta=None):
+    """Time the forward kernel's launch shapes per bucket of samples per SM, on `theta`
+    ([n, 3] FP64 on the device, representative samples) or a built-in swimmer; returns
+    {samples per SM: threads per sample} for the measured buckets."""
     out = (ctypes.c_int * 17)()
-    check(lib().swimmer_autotune(h.ptr, int(steps), out))
-    res, B, k = {}, 1, 0
-    while B <= h.cfg.b_max:
-        res[B] = out[k]
-        B <<= 1
-        k += 1
-    return res
+    if theta is not None:
+        _dev(theta, torch.float64)
+        check(lib().swimmer_autotune(h.ptr, int(steps), _ptr(theta), int(theta.shape[0]), out))
+    else:
+        check(lib().swimmer_autotune(h.ptr, int(steps), None, 0, out))
+    return {k + 1: out[k] for k in range(17) if out[k] > 0}
 
 
 def swimmer_tuning(h: Handle, precision=None, threads=None):
     """Get (threads=None) or set the launch-shape table of one precision: a list of 17
-    threads-per-sample entries, entry k for batches 2^k <= B < 2^(k+1), 0 = heuristic."""
+    threads-per-sample entries, entry k for batches of k + 1 samples per SM, 0 = heuristic."""
     prec = h.cfg.precision if precision is None else precision
     buf = (ctypes.c_int * 17)()
     if threads is None:

@@ -6,6 +6,8 @@
 
 #include <vector>
 
+#include <algorithm>
+
 #include "common.cuh"
 
 static thread_local char g_err[512] = "";
@@ -274,15 +276,23 @@ extern "C" int swimmer_tuning(swimmer_handle *h, int precision, int *threads, in
     return 0;
 }
 
-extern "C" int swimmer_autotune(swimmer_handle *h, int steps, int *out_threads) {
+extern "C" int swimmer_autotune(swimmer_handle *h, int steps, const double *theta_in, int n_theta,
+                                int *out_threads) {
     ARG_CHECK(h != nullptr, "handle is NULL");
     ARG_CHECK(steps >= 1, "steps must be >= 1");
+    ARG_CHECK(theta_in == nullptr || n_theta >= 1, "n_theta must be >= 1 with theta");
     const int bmax = h->cfg.b_max;
     double *theta = nullptr;
     int *status = nullptr;
     CUDA_TRY(cudaMalloc((void **)&theta, sizeof(double) * 3 * bmax));
     CUDA_TRY(cudaMalloc((void **)&status, sizeof(int) * bmax));
-    {
+    if (theta_in) {
+        // the caller's representative samples, repeated to b_max rows
+        for (int off = 0; off < bmax; off += n_theta) {
+            const int rows = std::min(n_theta, bmax - off);
+            CUDA_TRY(cudaMemcpy(theta + 3 * off, theta_in, sizeof(double) * 3 * rows, cudaMemcpyDeviceToDevice));
+        }
+    } else {
         double *ht = (double *)malloc(sizeof(double) * 3 * bmax);
         for (int b = 0; b < bmax; ++b) {
             ht[3 * b] = 1.0 + 0.001 * (b % 17);
@@ -303,7 +313,9 @@ extern "C" int swimmer_autotune(swimmer_handle *h, int steps, int *out_threads) 
     int T0 = 32;
     while (T0 < h->cfg.n_max && T0 < 1024) T0 <<= 1;
     if (T0 < 128) T0 = 128;
-    for (int B = 1; B <= bmax && !rc; B <<= 1, ++k) {
+    // one batch per bucket: k + 1 samples per SM (the last one b_max)
+    for (int per = 1; per <= 17 && !rc; ++per, ++k) {
+        const int B = (int)std::min<long long>((long long)per * h->num_sms, bmax);
         rc = launch_prepare(h, B, theta, nullptr, 0);
         if (!rc) rc = launch_table_build(h, B, 1, 0);
         float best = 1e30f;
@@ -323,11 +335,18 @@ extern "C" int swimmer_autotune(swimmer_handle *h, int steps, int *out_threads) 
                 bestT = T;
             }
         }
-        h->tune_threads[prec == SWIMMER_FP64 ? 0 : 1][k] = bestT;
+        h->tune_threads[prec == SWIMMER_FP64 ? 0 : 1][tune_bucket(h, B)] = bestT;
         if (out_threads) out_threads[k] = bestT;
+        if (B == bmax) {
+            ++k;
+            break;
+        }
     }
     // buckets beyond b_max keep the largest measured choice
-    for (int j = k; j < 17; ++j) h->tune_threads[prec == SWIMMER_FP64 ? 0 : 1][j] = h->tune_threads[prec == SWIMMER_FP64 ? 0 : 1][k > 0 ? k - 1 : 0];
+    for (int j = tune_bucket(h, bmax) + 1; j < 17; ++j)
+        h->tune_threads[prec == SWIMMER_FP64 ? 0 : 1][j] = h->tune_threads[prec == SWIMMER_FP64 ? 0 : 1][j - 1];
+    for (int j = k; j < 17; ++j)
+        if (out_threads) out_threads[j] = 0;
     h->cfg.steps = saved_steps;
     h->cfg.obs_every = saved_obs;
     cudaEventDestroy(e0);

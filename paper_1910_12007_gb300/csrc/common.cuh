@@ -52,7 +52,7 @@ struct swimmer_handle {
                                // kernel, [1] those a one-step-at-a-time TMCMC would also run
     unsigned long long *run_work;  // [b_max] pair evaluations of each run of the last launch
     // autotuned threads per sample for batch sizes in [2^k, 2^(k+1)), per precision; 0 = heuristic
-    int tune_threads[2][17];
+    int tune_threads[2][17];  // [FP64, FP32C][samples per SM - 1, capped at 16]
     int device;
     int num_sms;
     int max_smem;  // opt-in shared memory per block (bytes)
@@ -121,6 +121,7 @@ int launch_forward(swimmer_handle *h, int B, const double *obs, double sigma, do
                    double *head_traj, double *mean_speed, int *status, int precision,
                    cudaStream_t s, int threads_override = 0, int speculative = 0);
 int forward_threads(const swimmer_handle *h, int B, int precision);
+int tune_bucket(const swimmer_handle *h, int B);
 bool forward_fits(const swimmer_handle *h, int threads, int precision);
 int forward_slots(const swimmer_handle *h, int precision);
 int launch_kernel_eval(swimmer_handle *h, int m, const double *r, double *g1, double *g2,

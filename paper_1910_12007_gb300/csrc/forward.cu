@@ -128,20 +128,24 @@ __host__ __device__ size_t state_bytes(int n_max, int threads) {
     return align32(16 * (size_t)n_max) + 1024 * nbm + align32(forces > part ? forces : part);
 }
 
+// FP32: the sample's pair units (I | J << 8 | d0 << 16), ceil(n_max/32)^2 ints after the table
 template <bool F64>
 __host__ __device__ size_t smem_bytes(int n_max, int P, int threads) {
-    return state_bytes<F64>(n_max, threads) + table_bytes<F64>(P);
+    const size_t nbm = (n_max + 31) / 32;
+    return state_bytes<F64>(n_max, threads) + table_bytes<F64>(P) + (F64 ? 0 : 4 * nbm * nbm);
 }
 
 // g1, g2 from the FP32 table: quadratic in F = 1 + f in [1, 2), the mantissa of u
 __device__ __forceinline__ void kern_f32(const float4 *__restrict__ tA, const float2 *__restrict__ tB, int pmax,
                                          float u, float &g1, float &g2) {
-    unsigned bits = __float_as_uint(u);
-    unsigned p = (bits >> (23 - F32_SUB_LOG2)) - (127u << F32_SUB_LOG2);
-    p = min(p, (unsigned)pmax);
-    float F = __uint_as_float(0x3f800000u | ((bits << F32_SUB_LOG2) & 0x7fffffu));
-    float4 a = tA[p];
-    float2 c = tB[p];
+    // u >= 1: the panel is (exponent - 127) * panels per octave + top mantissa bits; the
+    // exponent bias is subtracted after the clamp, where it folds into the load offsets
+    constexpr int BIAS = 127 << F32_SUB_LOG2;
+    const unsigned bits = __float_as_uint(u);
+    const int p = (int)min(bits >> (23 - F32_SUB_LOG2), (unsigned)(pmax + BIAS));
+    const float F = __uint_as_float(0x3f800000u | ((bits << F32_SUB_LOG2) & 0x7fffffu));
+    const float4 a = tA[p - BIAS];
+    const float2 c = tB[p - BIAS];
     g1 = fmaf(F, fmaf(F, a.z, a.y), a.x);
     g2 = fmaf(F, fmaf(F, c.y, c.x), a.w);
 }
@@ -231,6 +235,31 @@ __global__ void __launch_bounds__(1024) forward_kernel(FwdArgs a) {
             for (int i = tid; i < npan; i += T) {
                 t[i] = g[i];
                 tb[i] = gb[i];
+            }
+            // pair units: diagonal blocks first (d = 1..16), then each off-diagonal block
+            // pair as two units (d = 0..15, 16..31) in circulant order: {r, r + k} for
+            // k = 1 .. (nb - 1) / 2, then {r, r + nb / 2} for r < nb / 2 (even nb)
+            const int nbs = (n + 31) >> 5;
+            int *units = (int *)(tabraw + table_bytes<F64>(P));
+            for (int un = tid; un < nbs * nbs; un += T) {
+                int I, Jb, d0;
+                if (un < nbs) {
+                    I = Jb = un;
+                    d0 = 1;
+                } else {
+                    const int v = (un - nbs) >> 1, half = (nbs - 1) >> 1, full = nbs * half;
+                    d0 = ((un - nbs) & 1) << 4;
+                    if (v < full) {
+                        const int kk = v / nbs;
+                        I = v - kk * nbs;
+                        Jb = I + kk + 1;
+                        if (Jb >= nbs) Jb -= nbs;
+                    } else {
+                        I = v - full;
+                        Jb = I + (nbs >> 1);
+                    }
+                }
+                units[un] = I | (Jb << 8) | (d0 << 16);
             }
         }
         // ---- initial straight filament X_k = (k ds, 0), stored relative to (L/2, 0)
@@ -483,26 +512,10 @@ __global__ void __launch_bounds__(1024) forward_kernel(FwdArgs a) {
                 for (int k = lane; k < (nb << 5); k += 32) mypart[k] = make_float2(0.f, 0.f);
                 const int nxt = (lane + 1) & 31;
                 const float half_mask = lane < 16 ? 1.f : 0.f;
+                const int *units = (const int *)(tabraw + table_bytes<F64>(P));
                 for (int un = warp; un < n_units; un += n_pw) {
-                    int I, Jb, d0;
-                    if (un < nb) {
-                        I = Jb = un;
-                        d0 = 1;
-                    } else {
-                        // off-diagonal block pairs in circulant order: {r, r + k} for
-                        // k = 1 .. (nb - 1) / 2, then {r, r + nb / 2} for r < nb / 2 (even nb)
-                        const int v = (un - nb) >> 1, half = (nb - 1) >> 1, full = nb * half;
-                        d0 = ((un - nb) & 1) << 4;
-                        if (v < full) {
-                            const int kk = v / nb;
-                            I = v - kk * nb;
-                            Jb = I + kk + 1;
-                            if (Jb >= nb) Jb -= nb;
-                        } else {
-                            I = v - full;
-                            Jb = I + (nb >> 1);
-                        }
-                    }
+                    const int pk = units[un];
+                    const int I = pk & 255, Jb = (pk >> 8) & 255, d0 = pk >> 16;
                     const bool diag = I == Jb;
                     const float4 me = s4[(I << 6) + lane];
                     const float4 *sp = s4 + (Jb << 6) + lane + d0;
@@ -674,9 +687,15 @@ int forward_slots(const swimmer_handle *h, int precision) {
     return per_sm * h->num_sms;
 }
 
+// Launch-shape bucket of a batch: samples per SM, ceil(B / SMs) - 1, capped at 16.  The
+// persistent kernel's time is set by how many samples each SM holds.
+int tune_bucket(const swimmer_handle *h, int B) {
+    const long long per_sm = ((long long)B + h->num_sms - 1) / h->num_sms;
+    return (int)(per_sm < 1 ? 0 : (per_sm > 17 ? 16 : per_sm - 1));
+}
+
 int forward_threads(const swimmer_handle *h, int B, int precision) {
-    int bucket = 0;
-    while ((2 << bucket) <= B && bucket < 16) ++bucket;
+    const int bucket = tune_bucket(h, B);
     int tuned = h->tune_threads[precision == SWIMMER_FP64 ? 0 : 1][bucket];
     int T = 32;
     while (T < h->cfg.n_max && T < 1024) T <<= 1;

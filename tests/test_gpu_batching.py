@@ -80,3 +80,31 @@ def test_graph_replay_equals_eager():
     torch.cuda.synchronize()
     assert torch.equal(traj_g, traj_e) and torch.equal(speed_g, speed_e) and torch.equal(st_g, st_e)
     h.close()
+
+
+def test_launch_shapes_agree_and_tuning_table_round_trips():
+    # N up to 96 points: 3 blocks of 32, so 128..512 threads give 4, 8 and 9 pair warps
+    cfg = replace(_cfg(64, g.FP32C, steps=300, obs_every=30, n_max=96))
+    h = g.swimmer_init(cfg)
+    th = torch.tensor(synthetic.prior_samples(9, (0.2, -0.5, 0.05), (8.0, 0.5, 0.15), 40), device=DEV)
+    ns = torch.tensor(synthetic.choice_n(9, [40, 70, 96], 40).astype(np.int32), device=DEV)
+    outs = {}
+    for T in (128, 256, 512):
+        g.swimmer_tuning(h, g.FP32C, [T] * 17)
+        assert g.swimmer_tuning(h, g.FP32C) == [T] * 17
+        traj, speed, st = g.forward_batch(h, th, ns)
+        outs[T] = (traj.cpu().numpy(), st.cpu().numpy())
+    ref_traj, ref_st = outs[128]
+    assert np.all(ref_st == 0)
+    scale = np.max(np.abs(ref_traj))
+    for T in (256, 512):
+        # only the grouping of the FP32 partial sums changes with the number of pair warps
+        assert np.array_equal(outs[T][1], ref_st)
+        assert np.max(np.abs(outs[T][0] - ref_traj)) <= 1e-5 * scale
+    with pytest.raises(RuntimeError):
+        g.swimmer_tuning(h, g.FP32C, [96] * 17)  # not a power of two
+    tuned = g.swimmer_autotune(h, steps=20)
+    assert set(tuned) and all(v in (128, 256, 512, 1024) for v in tuned.values())
+    table = g.swimmer_tuning(h, g.FP32C)
+    assert table[0] == tuned[1]
+    h.close()
