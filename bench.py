@@ -205,6 +205,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="fp32c", choices=["fp32c", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--shard-stage", action="store_true",
+                    help="N > 1: one TMCMC population sharded over the ranks (strong scaling, one SUM "
+                         "all-reduce per stage) instead of an independent TMCMC per rank (weak scaling)")
     ap.add_argument("--profile-case", action="store_true",
                     help="run one forward batch of the workload (1024 samples, 200 steps) for ncu and exit")
     ap.add_argument("--workload", default="tmcmc", choices=["tmcmc", "uneven", "large", "surrogate"],
@@ -265,7 +268,8 @@ def main():
     # runs that diverge early make batches uneven, which the shape choice must see
     th_tune = torch.tensor(synthetic.prior_samples(4242, PRIOR_LO, PRIOR_HI, B_STAGE), device=dev)
     tuned = g.swimmer_autotune(h, steps=2000, theta=th_tune)
-    seed0 = ranks.rank_seed(1000, rank)  # independent TMCMC per rank
+    shard = args.shard_stage and world > 1
+    seed0 = 1000 if shard else ranks.rank_seed(1000, rank)  # one shared population, or one per rank
 
     # synthetic observations: forward model at theta*, plus 5 % noise (untimed set-up)
     th_true = torch.tensor([THETA_TRUE], dtype=torch.float64, device=dev)
@@ -287,7 +291,14 @@ def main():
 
         def generate(self):
             th0 = torch.tensor(synthetic.prior_samples(self.seed, PRIOR_LO, PRIOR_HI, B_STAGE), device=dev)
-            ll, _ = g.loglik_batch(h, th0, obs, sigma)
+            if shard:  # each rank evaluates its block of the prior draws, one SUM assembles them
+                a, z = ranks.shard(B_STAGE, world, rank)
+                ll = torch.zeros(B_STAGE, dtype=torch.float64, device=dev)
+                if z > a:
+                    ll[a:z] = g.loglik_batch(h, th0[a:z].contiguous(), obs, sigma)[0]
+                dist.all_reduce(ll, op=dist.ReduceOp.SUM)
+            else:
+                ll, _ = g.loglik_batch(h, th0, obs, sigma)
             self.state = g.TmcmcState(th0, ll, obs, sigma, PRIOR_LO, PRIOR_HI)
             self.stage = 0
 
@@ -305,7 +316,11 @@ def main():
                 Zd = torch.tensor(Z, device=dev)
             else:
                 Ud, Zd = host_io(U, Z)
-            g.tmcmc_stage(h, self.state, Ud, Zd)
+            if shard:
+                g.tmcmc_stage(h, self.state, Ud, Zd, rank=rank, world=world)
+                ranks.assemble_stage(dist, self.state)
+            else:
+                g.tmcmc_stage(h, self.state, Ud, Zd)
             self.stage += 1
             self.stages_done += 1
 
@@ -368,8 +383,10 @@ def main():
     g.swimmer_profile(h, 0)
 
     # ---- aggregate over ranks (max time, summed work)
+    # a shared population counts its samples once (each rank adds its share)
+    samples_mine = stages * B_STAGE / (world if shard else 1)
     (pairs_all, samples_all, pairs_e2e_all, pairs_exec_all), (ms_all, e2e_s) = ranks.totals(
-        dist, [pairs, stages * B_STAGE, pairs_e2e, pairs_exec], [ms_total, t3 - t2], device=dev)
+        dist, [pairs, samples_mine, pairs_e2e, pairs_exec], [ms_total, t3 - t2], device=dev)
 
     if rank == 0:
         peaks, peak_src = load_peaks()
@@ -385,8 +402,12 @@ def main():
         line = {
             "metric": METRIC, "value": value, "unit": "pair-evals/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_all / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32" if prec == g.FP32C else "f64",
-            "data": "synthetic", "config": dict(workload_config(args.precision), parallelism=f"dp{world} (independent TMCMC per GPU)"),
+            "scaling": "strong" if shard else "weak", "vs_baseline": None,
+            "dtype": "f32" if prec == g.FP32C else "f64", "data": "synthetic",
+            "config": dict(workload_config(args.precision),
+                           parallelism=(f"dp{world} (one TMCMC population, chains sharded over ranks, one SUM "
+                                        f"all-reduce of theta/loglik per stage)") if shard
+                           else f"dp{world} (independent TMCMC per GPU)"),
             "tmcmc_samples_per_s": samples_all / (ms_all * 1e-3),
             "value_counts": "pair evaluations a one-step-at-a-time TMCMC performs (pre-fetched runs off the "
                             "realized chain paths excluded)",

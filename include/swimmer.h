@@ -210,6 +210,18 @@ typedef struct tmcmc_state {
 int tmcmc_stage(swimmer_handle *h, tmcmc_state *st, const double *uniforms, const double *normals,
                 int use_surrogate, void *stream);
 
+/* tmcmc_stage for one of `world` processes that share one population (one GPU each).
+ * Every rank passes the same state and random numbers and runs the same analysis and
+ * resampling; rank `rank` then runs only the Metropolis chains whose output rows lie in its
+ * block: chain c (chains in ascending sample order, output rows off_c .. off_c + len_c - 1)
+ * belongs to rank floor((2 off_c + len_c) world / (2 B)).  On return st->theta, st->loglik
+ * (and st->surr_loglik) hold this rank's rows and zeros elsewhere, so a SUM all-reduce over
+ * the ranks assembles the population (the caller's one exchange per stage); the counters
+ * n_accept, n_exact, n_screened and n_exact_path count this rank's work.  world = 1 is
+ * tmcmc_stage.  Errors as tmcmc_stage, plus SWIMMER_E_ARG for rank outside [0, world). */
+int tmcmc_stage_shard(swimmer_handle *h, tmcmc_state *st, const double *uniforms, const double *normals,
+                      int use_surrogate, int rank, int world, void *stream);
+
 /* The decision tree tmcmc_stage pre-fetches for each live chain (host only, no device
  * work): the root plus M - 1 nodes chosen best-first by the probability that a chain
  * accepting each proposal with probability p_accept follows the path to them, depth below

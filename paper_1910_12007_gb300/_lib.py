@@ -45,6 +45,7 @@ SIGNATURES = [
     ("swimmer_tuning", c_int, [c_void_p, c_int, c_void_p, c_int]),
     ("loglik_batch", c_int, [c_void_p, c_int, c_void_p, c_void_p, c_void_p, c_double, c_void_p, c_void_p, c_void_p]),
     ("tmcmc_stage", c_int, [c_void_p, P(TmcmcStateC), c_void_p, c_void_p, c_int, c_void_p]),
+    ("tmcmc_stage_shard", c_int, [c_void_p, P(TmcmcStateC), c_void_p, c_void_p, c_int, c_int, c_int, c_void_p]),
     ("tmcmc_tree_template", c_int, [c_int, c_double, c_int, c_void_p, c_void_p]),
     ("tmcmc_analyze", c_int, [c_void_p, c_int, c_void_p, c_void_p, c_double, c_void_p, c_void_p, c_void_p]),
     ("tmcmc_resample", c_int, [c_void_p, c_int, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),

@@ -205,12 +205,18 @@ def tmcmc_tree_template(M, p_accept, depth_cap):
             for v in range(count.value)]
 
 
-def tmcmc_stage(h: Handle, st: TmcmcState, uniforms, normals, use_surrogate=False, stream=None):
-    """One TMCMC stage on the device; uniforms [3, B], normals [B, 3] (FP64, device)."""
+def tmcmc_stage(h: Handle, st: TmcmcState, uniforms, normals, use_surrogate=False, stream=None, rank=0, world=1):
+    """One TMCMC stage on the device; uniforms [3, B], normals [B, 3] (FP64, device).
+    With world > 1 this process runs only rank `rank`'s chains and leaves zeros in the other
+    ranks' rows of st.theta / st.loglik (``ranks.assemble_stage`` sums them over ranks)."""
     _dev(uniforms, torch.float64)
     _dev(normals, torch.float64)
-    check(lib().tmcmc_stage(h.ptr, ctypes.byref(st.c), _ptr(uniforms), _ptr(normals), int(bool(use_surrogate)),
-                            _stream(stream)))
+    if world == 1:
+        check(lib().tmcmc_stage(h.ptr, ctypes.byref(st.c), _ptr(uniforms), _ptr(normals), int(bool(use_surrogate)),
+                                _stream(stream)))
+    else:
+        check(lib().tmcmc_stage_shard(h.ptr, ctypes.byref(st.c), _ptr(uniforms), _ptr(normals),
+                                      int(bool(use_surrogate)), int(rank), int(world), _stream(stream)))
     return st.summary()
 
 

@@ -269,7 +269,8 @@ extern "C" int swimmer_tuning(swimmer_handle *h, int precision, int *threads, in
     }
     for (int k = 0; k < 17; ++k) {
         const int t = threads[k];
-        ARG_CHECK(t == 0 || (t >= 32 && t <= 1024 && (t & (t - 1)) == 0), "threads[%d] = %d is not 0 or a power of two in [32, 1024]", k, t);
+        ARG_CHECK(t == 0 || (t >= forward_min_threads(h, precision) && t <= 1024 && (t & (t - 1)) == 0),
+                  "threads[%d] = %d is not 0 or a power of two in [%d, 1024]", k, t, forward_min_threads(h, precision));
         ARG_CHECK(t == 0 || forward_fits(h, t, precision), "threads[%d] = %d needs more shared memory than the device has", k, t);
     }
     for (int k = 0; k < 17; ++k) tab[k] = threads[k];
@@ -310,9 +311,7 @@ extern "C" int swimmer_autotune(swimmer_handle *h, int steps, const double *thet
     cudaEventCreate(&e1);
     int rc = 0, k = 0;
     const int prec = h->cfg.precision;
-    int T0 = 32;
-    while (T0 < h->cfg.n_max && T0 < 1024) T0 <<= 1;
-    if (T0 < 128) T0 = 128;
+    const int T0 = forward_min_threads(h, prec);
     // one batch per bucket: k + 1 samples per SM (the last one b_max)
     for (int per = 1; per <= 17 && !rc; ++per, ++k) {
         const int B = (int)std::min<long long>((long long)per * h->num_sms, bmax);

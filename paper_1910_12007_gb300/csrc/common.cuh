@@ -122,6 +122,7 @@ int launch_forward(swimmer_handle *h, int B, const double *obs, double sigma, do
                    cudaStream_t s, int threads_override = 0, int speculative = 0);
 int forward_threads(const swimmer_handle *h, int B, int precision);
 int tune_bucket(const swimmer_handle *h, int B);
+int forward_min_threads(const swimmer_handle *h, int precision);
 bool forward_fits(const swimmer_handle *h, int threads, int precision);
 int forward_slots(const swimmer_handle *h, int precision);
 int launch_kernel_eval(swimmer_handle *h, int m, const double *r, double *g1, double *g2,

@@ -694,13 +694,19 @@ int tune_bucket(const swimmer_handle *h, int B) {
     return (int)(per_sm < 1 ? 0 : (per_sm > 17 ? 16 : per_sm - 1));
 }
 
+// Smallest launch shape: FP64 needs a thread per target, FP32 a few warps for the O(N) phases.
+int forward_min_threads(const swimmer_handle *h, int precision) {
+    int T = 128;
+    if (precision == SWIMMER_FP64)
+        while (T < h->cfg.n_max && T < 1024) T <<= 1;
+    return T;
+}
+
 int forward_threads(const swimmer_handle *h, int B, int precision) {
     const int bucket = tune_bucket(h, B);
-    int tuned = h->tune_threads[precision == SWIMMER_FP64 ? 0 : 1][bucket];
-    int T = 32;
-    while (T < h->cfg.n_max && T < 1024) T <<= 1;
-    if (T < 128) T = 128;
-    if (tuned >= T && tuned <= 1024) return tuned;
+    const int tuned = h->tune_threads[precision == SWIMMER_FP64 ? 0 : 1][bucket];
+    int T = forward_min_threads(h, precision);
+    if (tuned >= T && tuned <= 1024 && forward_fits(h, tuned, precision)) return tuned;
     int cap = 1024;
     if (precision != SWIMMER_FP64) {  // warps beyond the pair units only help the O(N) phases
         const int nbm = (h->cfg.n_max + 31) / 32;

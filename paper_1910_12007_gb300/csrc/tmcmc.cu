@@ -348,9 +348,16 @@ __device__ __forceinline__ int tree_path(const int4 *__restrict__ tmpl, int v, i
     return depth;
 }
 
-// live chains (chain_pos < chain_len) in the longest-first order, their number, the
-// largest remaining length, and the stage's accepted / decided steps so far
-__global__ void __launch_bounds__(T1) live_kernel(int U, const int *__restrict__ order, const int *__restrict__ chain_len,
+// Chain c belongs to rank floor((2 off_c + len_c) world / (2 B)): the ranks own contiguous
+// blocks of output positions (chains in ascending sample order), balanced by chain length.
+__device__ __forceinline__ bool chain_owned(int off, int len, int B, int rank, int world) {
+    return world == 1 || (int)(((2ll * off + len) * world) / (2ll * B)) == rank;
+}
+
+// live chains of this rank (chain_pos < chain_len) in the longest-first order, their
+// number, the largest remaining length, and the rank's accepted / decided steps so far
+__global__ void __launch_bounds__(T1) live_kernel(int U, int B, int rank, int world, const int *__restrict__ order,
+                                                  const int *__restrict__ chain_off, const int *__restrict__ chain_len,
                                                   const int *__restrict__ chain_pos, int *__restrict__ live,
                                                   const int *__restrict__ counter, int *__restrict__ host_info) {
     __shared__ unsigned long long sm[64];
@@ -366,6 +373,7 @@ __global__ void __launch_bounds__(T1) live_kernel(int U, const int *__restrict__
     int rem = 0, dec = 0;
     for (int i = lo; i < hi; ++i) {
         const int c = order[i];
+        if (!chain_owned(chain_off[c], chain_len[c], B, rank, world)) continue;
         const int r = chain_len[c] - chain_pos[c];
         cnt += r > 0;
         rem = max(rem, r);
@@ -377,7 +385,7 @@ __global__ void __launch_bounds__(T1) live_kernel(int U, const int *__restrict__
     atomicAdd(&s_dec, dec);
     for (int i = lo; i < hi; ++i) {
         const int c = order[i];
-        if (chain_len[c] > chain_pos[c]) live[at++] = c;
+        if (chain_len[c] > chain_pos[c] && chain_owned(chain_off[c], chain_len[c], B, rank, world)) live[at++] = c;
     }
     __syncthreads();
     if (tid == 0) {
@@ -589,7 +597,13 @@ extern "C" int tmcmc_resample(swimmer_handle *h, int B, const double *w, const d
 
 extern "C" int tmcmc_stage(swimmer_handle *h, tmcmc_state *st, const double *uniforms, const double *normals,
                            int use_surrogate, void *stream) {
+    return tmcmc_stage_shard(h, st, uniforms, normals, use_surrogate, 0, 1, stream);
+}
+
+extern "C" int tmcmc_stage_shard(swimmer_handle *h, tmcmc_state *st, const double *uniforms, const double *normals,
+                                 int use_surrogate, int rank, int world, void *stream) {
     ARG_CHECK(h != nullptr && st != nullptr, "NULL handle or state");
+    ARG_CHECK(world >= 1 && rank >= 0 && rank < world, "rank %d outside [0, world %d)", rank, world);
     const int B = st->B;
     ARG_CHECK(B >= 1 && B <= h->cfg.b_max, "B outside [1, b_max]");
     ARG_CHECK(st->theta && st->loglik && st->status && st->obs, "NULL device pointer in the state");
@@ -632,9 +646,14 @@ extern "C" int tmcmc_stage(swimmer_handle *h, tmcmc_state *st, const double *uni
     // at once), a best-first template tree of M = slots / live nodes per live chain
     const int slots = min(h->cfg.b_max, forward_slots(h, h->cfg.precision));
     CUDA_TRY(cudaMemsetAsync(h->chain_pos, 0, sizeof(int) * U, s));
+    if (world > 1) {  // rows of other ranks' chains stay zero, so a SUM over ranks assembles them
+        CUDA_TRY(cudaMemsetAsync(h->out_theta, 0, 3 * sizeof(double) * B, s));
+        CUDA_TRY(cudaMemsetAsync(h->out_ll, 0, sizeof(double) * B, s));
+        CUDA_TRY(cudaMemsetAsync(h->out_sl, 0, sizeof(double) * B, s));
+    }
     for (int launch = 0;; ++launch) {
-        live_kernel<<<1, T1, 0, s>>>(U, h->chain_id, h->chain_len, h->chain_pos, h->live, h->info + cap,
-                                     h->info + cap + 8);
+        live_kernel<<<1, T1, 0, s>>>(U, B, rank, world, h->chain_id, h->chain_off, h->chain_len, h->chain_pos,
+                                     h->live, h->info + cap, h->info + cap + 8);
         CUDA_TRY(cudaGetLastError());
         prof_count(h, 1);
         CUDA_TRY(cudaMemcpyAsync(h->host_pinned, h->info + cap + 8, 4 * sizeof(int), cudaMemcpyDeviceToHost, s));

@@ -129,3 +129,57 @@ def test_tmcmc_fp32_posterior_matches_fp64():
     # inputs is far below this
     assert np.all(np.abs(m32 - m64) <= 0.02 * np.abs(m64) + 0.02 * s64), (m32, m64, s32, s64)
     assert np.all(np.abs(s32 - s64) <= 0.2 * s64), (s32, s64)
+
+
+@pytest.mark.parametrize("world", [2, 3])
+def test_sharded_stage_sums_to_the_whole_stage(world):
+    from paper_1910_12007_gb300 import ranks
+
+    B, seed = 256, 3
+    D, sigma = _problem()
+    cfg = g.SwimmerConfig(n_max=BASE.n, b_max=B, length=BASE.length, dt=BASE.dt, steps=BASE.steps,
+                          obs_every=BASE.obs_every, precision=g.FP32C)
+    h = g.swimmer_init(cfg)
+    obs = torch.tensor(D, device=DEV)
+    th0 = torch.tensor(synthetic.prior_samples(seed, LO, HI, B), device=DEV)
+    ll0, _ = g.loglik_batch(h, th0, obs, sigma)
+    u_res, u_acc, z = synthetic.stage_randoms(seed, 0, B, 3)
+    U = torch.tensor(np.concatenate([u_res[None], u_acc]), device=DEV)
+    Z = torch.tensor(z, device=DEV)
+
+    def fresh():
+        return g.TmcmcState(th0.clone(), ll0.clone(), obs, sigma, LO, HI)
+
+    full = fresh()
+    g.tmcmc_stage(h, full, U, Z)
+    parts = []
+    for r in range(world):
+        s = fresh()
+        g.tmcmc_stage(h, s, U, Z, rank=r, world=world)
+        parts.append(s)
+    torch.cuda.synchronize()
+    # which rows each rank owns: the documented rule on the stage's resample counts
+    w, _ = g.tmcmc_analyze(h, th0, ll0, 0.0)
+    _, counts = g.tmcmc_resample(h, w, U[0].contiguous())
+    counts = counts.cpu().numpy()
+    owner = ranks.chain_owner(counts, world)
+    row_owner = np.concatenate([[owner[k]] * int(counts[k]) for k in range(B) if counts[k] > 0])
+    th_full, ll_full = full.theta.cpu().numpy(), full.loglik.cpu().numpy()
+    tot_th = np.zeros_like(th_full)
+    tot_ll = np.zeros_like(ll_full)
+    for r, s in enumerate(parts):
+        th, ll = s.theta.cpu().numpy(), s.loglik.cpu().numpy()
+        mine = row_owner == r
+        assert mine.any()
+        assert np.array_equal(th[mine], th_full[mine]) and np.array_equal(ll[mine], ll_full[mine])
+        assert not th[~mine].any() and not ll[~mine].any()
+        assert s.q == full.q and s.c.max_chain == full.c.max_chain
+        tot_th += th
+        tot_ll += ll
+    assert np.array_equal(tot_th, th_full) and np.array_equal(tot_ll, ll_full)
+    assert sum(s.c.n_accept for s in parts) == full.c.n_accept
+    assert sum(s.c.n_exact_path for s in parts) == full.c.n_exact_path
+    # the blocks are balanced by chain length: each within one chain of B / world rows
+    loads = np.bincount(row_owner, minlength=world)
+    assert np.all(np.abs(loads - B / world) <= counts.max())
+    h.close()
