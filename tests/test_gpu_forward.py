@@ -227,3 +227,57 @@ def test_config1_full_size_fp64():
         sp_ref = (xc[0, 1] - xc[0, 0]) / (p.steps * p.dt)
         assert abs(speed.item() - sp_ref) / abs(sp_ref) < (1e-9 if prec == g.FP64 else 1e-3)
         h.close()
+
+
+WORKLOAD = sw.SwimmerParams(n=128, dt=1e-4 / 64, steps=2000, obs_every=100, k_t=1e3)
+PICK = [0, 1, 333, 700, 1023]
+
+
+@pytest.fixture(scope="module")
+def workload_batch():
+    rng = np.random.default_rng(11)
+    B = 1024
+    th = np.column_stack([rng.uniform(0.0, 10.0, B), rng.uniform(-1.0, 0.2, B), rng.uniform(0.05, 0.2, B)])
+    return th, _oracle_batch(WORKLOAD, [tuple(th[i]) for i in PICK])
+
+
+@pytest.mark.parametrize("threads", [128, 256, 512])
+def test_tmcmc_workload_full_batch_sampled(threads, workload_batch):
+    # the TMCMC workload's sizes in the launch configurations its autotuner picks: 1024 samples
+    # of N = 128 (four blocks of 32: diagonal, circulant and opposite block pairs) in one
+    # persistent launch; sampled runs (including the batch's first and last) against the oracle,
+    # 2000 of the workload's time steps (every step has the same arithmetic)
+    p, pick, B = WORKLOAD, PICK, 1024
+    th, (ps, obs, xc, st) = workload_batch
+    assert np.all(st == 0)
+    h = g.swimmer_init(_cfg(p, B, g.FP32C))
+    g.swimmer_tuning(h, g.FP32C, [threads] * 17)
+    traj, speed, status = g.forward_batch(h, torch.tensor(th, device=DEV))
+    torch.cuda.synchronize()
+    traj = traj.cpu().numpy()
+    for k, i in enumerate(pick):
+        assert status[i].item() == 0
+        x0 = np.array([p.length, 0.0])
+        dr = obs[k] - x0
+        dg = traj[i] - x0
+        err = np.max(np.linalg.norm(dg - dr, axis=1)) / np.max(np.linalg.norm(dr, axis=1))
+        assert err < 1e-3, (i, err)
+    h.close()
+
+
+def test_tmcmc_workload_velocities_n128():
+    # per-step head velocities at N = 128 (1e-4 relative), FP32 and FP64 kernels
+    p = sw.SwimmerParams(n=128, dt=1e-4 / 64, steps=200, obs_every=1, k_t=1e3)
+    thetas = [(1.0, 0.0, 0.1), (6.5, -0.6, 0.17), (0.0, 0.1, 0.06)]
+    ps, obs, xc, st = _oracle_batch(p, thetas)
+    x0 = np.array([[p.length, 0.0]])
+    for prec, tol in [(g.FP32C, 1e-4), (g.FP64, 1e-9)]:
+        h = g.swimmer_init(_cfg(p, 4, prec))
+        traj, _, status = g.forward_batch(h, _theta(ps))
+        torch.cuda.synchronize()
+        for b in range(len(ps)):
+            vr = np.diff(np.concatenate([x0, obs[b]]), axis=0) / p.dt
+            vg = np.diff(np.concatenate([x0, traj[b].cpu().numpy()]), axis=0) / p.dt
+            err = np.max(np.linalg.norm(vg - vr, axis=1)) / np.max(np.linalg.norm(vr, axis=1))
+            assert err < tol, (prec, b, err)
+        h.close()
