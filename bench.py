@@ -210,10 +210,11 @@ def main():
                          "all-reduce per stage) instead of an independent TMCMC per rank (weak scaling)")
     ap.add_argument("--profile-case", action="store_true",
                     help="run one forward batch of the workload (1024 samples, 200 steps) for ncu and exit")
-    ap.add_argument("--workload", default="tmcmc", choices=["tmcmc", "uneven", "large", "surrogate"],
+    ap.add_argument("--workload", default="tmcmc", choices=["tmcmc", "uneven", "large", "surrogate", "shapes"],
                     help="tmcmc (default): TMCMC stages, 1024 samples, N=128; uneven: 4096 samples with "
                          "N in {64,128,256,512} in one graph-captured persistent launch; large: 256 samples "
-                         "x N=1024 x 4e4 steps; surrogate: delayed-acceptance vs plain TMCMC, 4096 samples/stage")
+                         "x N=1024 x 4e4 steps; surrogate: delayed-acceptance vs plain TMCMC, 4096 samples/stage; "
+                         "shapes: forward-kernel time per step vs samples per SM and threads per sample")
     args = ap.parse_args()
 
     from paper_1910_12007_gb300 import ranks
@@ -232,6 +233,8 @@ def main():
         return forward_workload(args, rank, world, local_rank)
     if args.workload == "surrogate":
         return surrogate_workload(args, rank, world, local_rank)
+    if args.workload == "shapes":
+        return shapes_workload(args, rank, local_rank)
 
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
@@ -527,6 +530,52 @@ def forward_workload(args, rank, world, local_rank):
     h.close()
     if dist is not None:
         dist.destroy_process_group()
+    return 0
+
+
+# -------------------------------------------------------------------------------------
+# launch-shape study: forward-kernel time per step vs samples per SM and threads per sample
+# -------------------------------------------------------------------------------------
+def shapes_workload(args, rank, local_rank):
+    import numpy as np
+    import torch
+
+    import paper_1910_12007_gb300 as g
+    import synthetic
+
+    if rank != 0:
+        return 0
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    steps = 2000
+    cfg = g.SwimmerConfig(n_max=N_PTS, b_max=B_STAGE, length=1.0, dt=DT, steps=steps, obs_every=OBS_EVERY,
+                          precision=g.FP32C)
+    h = g.swimmer_init(cfg)
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    # posterior-like samples (every run finishes), so the time is the kernel's, not divergence's
+    lo, hi = (0.5, -0.3, 0.08), (5.0, 0.3, 0.12)
+    rows = []
+    for per in [0] + list(range(1, 8)):
+        B = 1 if per == 0 else min(per * sms, B_STAGE)
+        th = torch.tensor(synthetic.prior_samples(77, lo, hi, B), device=dev)
+        row = {}
+        for T in (128, 256, 512, 1024):
+            try:
+                g.swimmer_tuning(h, g.FP32C, [T] * 17)
+            except RuntimeError:
+                continue
+            g.forward_batch(h, th, want_traj=False)
+            torch.cuda.synchronize()
+            g.swimmer_profile(h, 1)
+            _, _, st = g.forward_batch(h, th, want_traj=False)
+            ms, *_ = g.swimmer_profile(h, 2)
+            g.swimmer_profile(h, 0)
+            if bool((st == 0).all()):
+                row[str(T)] = round(ms * 1e3 / steps, 3)
+        rows.append({"samples": B, "samples_per_sm": B / sms, "us_per_step_by_threads": row})
+    print(json.dumps({"workload": f"forward kernel, N={N_PTS}, {steps} steps, FP32C: microseconds per time step",
+                      "sms": sms, "rows": rows}), flush=True)
+    h.close()
     return 0
 
 

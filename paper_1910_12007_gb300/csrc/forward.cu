@@ -106,7 +106,9 @@ __host__ __device__ size_t table_bytes(int P) {
 __host__ __device__ inline size_t align32(size_t b) { return (b + 31) & ~size_t(31); }
 
 // Warps of a CTA that take part in the FP32 pair sum: one per pair unit at most (a sample of
-// n points has ceil(n/32)^2 units of 16 diagonal steps).
+// n points has ceil(n/32)^2 units of 16 diagonal steps).  Splitting units further for more
+// warps was measured slower: lone samples at 1024 threads with 8-step units took 3.9 us per
+// step against 3.4 us at 512 threads (more partial sums to combine, more per-unit work).
 __host__ __device__ inline int pair_warps(int n_max, int threads) {
     const int nbm = (n_max + 31) / 32;
     const int W = threads / 32;
@@ -134,6 +136,7 @@ __host__ __device__ size_t smem_bytes(int n_max, int P, int threads) {
     const size_t nbm = (n_max + 31) / 32;
     return state_bytes<F64>(n_max, threads) + table_bytes<F64>(P) + (F64 ? 0 : 4 * nbm * nbm);
 }
+
 
 // g1, g2 from the FP32 table: quadratic in F = 1 + f in [1, 2), the mantissa of u
 __device__ __forceinline__ void kern_f32(const float4 *__restrict__ tA, const float2 *__restrict__ tB, int pmax,
@@ -171,6 +174,60 @@ __device__ __forceinline__ void kern_f64(const double *__restrict__ tab, int P, 
     }
     g1 = fma(t, a1, c1[0] - a2);
     g2 = fma(t, b1, c2[0] - b2);
+}
+
+// One FP32 pair unit of 16 diagonal steps: lane l holds target I*32 + l and at step
+// d = d0 .. d0+15 meets source J*32 + (l + d) mod 32; the source-side sums rotate one lane
+// per step.  A diagonal block (I = J) runs d = 1 .. 16, and at d = 16 only lanes < 16 count
+// (lanes l and l + 16 meet the same pair there).  Adds the unit's sums into the warp's
+// partial array.
+__device__ __forceinline__ void pair_unit(const float4 *__restrict__ s4, const float4 *__restrict__ t1,
+                                          const float2 *__restrict__ t2, int pmax, float fid2, int lane, int I,
+                                          int Jb, int d0, float2 *__restrict__ mypart) {
+    const bool diag = I == Jb;
+    const int nxt = (lane + 1) & 31;
+    const float half_mask = lane < 16 ? 1.f : 0.f;
+    const float4 me = s4[(I << 6) + lane];
+    const float4 *sp = s4 + (Jb << 6) + lane + d0;
+    float vx = 0.f, vy = 0.f, ax = 0.f, ay = 0.f;
+#pragma unroll
+    for (int s = 0; s < 16; ++s) {
+        const float4 q = sp[s];
+        const float dx = me.x - q.x, dy = me.y - q.y;
+        const float u = fmaf(fmaf(dx, dx, dy * dy), fid2, 1.0f);
+        float g1, g2;
+        kern_f32(t1, t2, pmax, u, g1, g2);
+        if (s == 15 && diag) {
+            g1 *= half_mask;
+            g2 *= half_mask;
+        }
+        const float wj = fmaf(q.z, dx, q.w * dy) * g2;
+        const float wi = fmaf(me.z, dx, me.w * dy) * g2;
+        vx = fmaf(wj, dx, fmaf(-q.z, g1, vx));
+        vy = fmaf(wj, dy, fmaf(-q.w, g1, vy));
+        ax = fmaf(wi, dx, fmaf(-me.z, g1, ax));
+        ay = fmaf(wi, dy, fmaf(-me.w, g1, ay));
+        ax = __shfl_sync(0xffffffffu, ax, nxt);
+        ay = __shfl_sync(0xffffffffu, ay, nxt);
+    }
+    // lane l now holds the sum of source J*32 + (l + d0 + 16) mod 32
+    const int from = (lane - d0 - 16) & 31;
+    ax = __shfl_sync(0xffffffffu, ax, from);
+    ay = __shfl_sync(0xffffffffu, ay, from);
+    if (diag) {
+        vx += ax;
+        vy += ay;
+    }
+    float2 pv = mypart[(I << 5) + lane];
+    pv.x += vx;
+    pv.y += vy;
+    mypart[(I << 5) + lane] = pv;
+    if (!diag) {
+        float2 pa = mypart[(Jb << 5) + lane];
+        pa.x += ax;
+        pa.y += ay;
+        mypart[(Jb << 5) + lane] = pa;
+    }
 }
 
 template <bool F64>
@@ -510,54 +567,10 @@ __global__ void __launch_bounds__(1024) forward_kernel(FwdArgs a) {
                 const int warp = tid >> 5;
                 float2 *mypart = part + warp * (nb << 5);
                 for (int k = lane; k < (nb << 5); k += 32) mypart[k] = make_float2(0.f, 0.f);
-                const int nxt = (lane + 1) & 31;
-                const float half_mask = lane < 16 ? 1.f : 0.f;
                 const int *units = (const int *)(tabraw + table_bytes<F64>(P));
                 for (int un = warp; un < n_units; un += n_pw) {
                     const int pk = units[un];
-                    const int I = pk & 255, Jb = (pk >> 8) & 255, d0 = pk >> 16;
-                    const bool diag = I == Jb;
-                    const float4 me = s4[(I << 6) + lane];
-                    const float4 *sp = s4 + (Jb << 6) + lane + d0;
-                    float vx = 0.f, vy = 0.f, ax = 0.f, ay = 0.f;
-#pragma unroll
-                    for (int s = 0; s < 16; ++s) {
-                        const float4 q = sp[s];
-                        const float dx = me.x - q.x, dy = me.y - q.y;
-                        const float u = fmaf(fmaf(dx, dx, dy * dy), fid2, 1.0f);
-                        float g1, g2;
-                        kern_f32(t1, t2, npan - 1, u, g1, g2);
-                        if (s == 15 && diag) {
-                            g1 *= half_mask;
-                            g2 *= half_mask;
-                        }
-                        const float wj = fmaf(q.z, dx, q.w * dy) * g2;
-                        const float wi = fmaf(me.z, dx, me.w * dy) * g2;
-                        vx = fmaf(wj, dx, fmaf(-q.z, g1, vx));
-                        vy = fmaf(wj, dy, fmaf(-q.w, g1, vy));
-                        ax = fmaf(wi, dx, fmaf(-me.z, g1, ax));
-                        ay = fmaf(wi, dy, fmaf(-me.w, g1, ay));
-                        ax = __shfl_sync(0xffffffffu, ax, nxt);
-                        ay = __shfl_sync(0xffffffffu, ay, nxt);
-                    }
-                    // lane l now holds the sum of source J*32 + (l + d0 + 16) mod 32
-                    const int from = (lane - d0 - 16) & 31;
-                    ax = __shfl_sync(0xffffffffu, ax, from);
-                    ay = __shfl_sync(0xffffffffu, ay, from);
-                    if (diag) {
-                        vx += ax;
-                        vy += ay;
-                    }
-                    float2 pv = mypart[(I << 5) + lane];
-                    pv.x += vx;
-                    pv.y += vy;
-                    mypart[(I << 5) + lane] = pv;
-                    if (!diag) {
-                        float2 pa = mypart[(Jb << 5) + lane];
-                        pa.x += ax;
-                        pa.y += ay;
-                        mypart[(Jb << 5) + lane] = pa;
-                    }
+                    pair_unit(s4, t1, t2, npan - 1, fid2, lane, pk & 255, (pk >> 8) & 255, pk >> 16, mypart);
                 }
             }
             if (!F64) __syncthreads();
