@@ -681,11 +681,11 @@ bool forward_fits(const swimmer_handle *h, int threads, int precision) {
     return smem + 1024 <= (size_t)h->max_smem;  // static shared memory of the kernel
 }
 
-// Samples the forward kernel runs at once on the device (resident CTAs at the launch shape
-// of a large batch); at least one per SM.
+// Samples the forward kernel holds at once on the device at its smallest launch shape (the
+// most resident samples); at least one per SM.
 int forward_slots(const swimmer_handle *h, int precision) {
     const bool f64 = precision == SWIMMER_FP64;
-    const int T = forward_threads(h, 1 << 30, precision);
+    const int T = forward_min_threads(h, precision);
     const int P = handle_octaves(h) * (f64 ? F64_SUB : F32_SUB);
     size_t smem = f64 ? smem_bytes<true>(h->cfg.n_max, P, T) : smem_bytes<false>(h->cfg.n_max, P, T);
     auto kern = f64 ? forward_kernel<true> : forward_kernel<false>;

@@ -643,7 +643,9 @@ extern "C" int tmcmc_stage_shard(swimmer_handle *h, tmcmc_state *st, const doubl
         box.hi[a] = st->prior_hi[a];
     }
     // pre-fetching: each launch runs up to `slots` forward models (as many as the GPU holds
-    // at once), a best-first template tree of M = slots / live nodes per live chain
+    // at once at the smallest launch shape), a best-first template tree of M = slots / live
+    // nodes per live chain.  Filling the resident capacity beat smaller budgets and a
+    // cost-per-resolved-step choice in simulations of the stage with measured launch costs.
     const int slots = min(h->cfg.b_max, forward_slots(h, h->cfg.precision));
     CUDA_TRY(cudaMemsetAsync(h->chain_pos, 0, sizeof(int) * U, s));
     if (world > 1) {  // rows of other ranks' chains stay zero, so a SUM over ranks assembles them
