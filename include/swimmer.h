@@ -63,7 +63,24 @@ typedef struct swimmer_config {
     long long steps;        /* time steps per forward run */
     long long obs_every;    /* observation of the head point every obs_every steps */
     int precision;          /* SWIMMER_FP64 or SWIMMER_FP32C */
+    /* Full sperm model (Appendix, Table Tab:param): a circular head of n_head points joined
+     * to the flagellum's proximal point by five neck springs and a neck-angle energy.
+     * n_head = 0 is the flagellum alone.  Points per sample = n (flagellum) + n_head <=
+     * n_max; head and gap sizes in units of ds (0 selects n_head / (2 pi) and 1). */
+    int n_head;             /* head points N_H: 0, or even in [4, 256] */
+    double head_radius_over_ds;  /* H_r / ds */
+    double neck_gap_over_ds;     /* dN / ds: initial gap between flagellum end and head */
+    double k_head_tens;     /* K_{H,tens}: head membrane and diametral springs */
+    double k_head_c;        /* K_{H,C}: head bending toward curvature 1/H_r */
+    double k_neck_tens;     /* K_{N,tens}: the five neck springs */
+    double k_neck_ang;      /* K_{N,ang}: neck angle energy K (z1 . z2)^2 */
+    int obs_kind;           /* SWIMMER_OBS_HEAD_POINT: proximal flagellum point (x, y);
+                               SWIMMER_OBS_HEAD_VELOCITY: head-centre velocity (x, y), the
+                               centre's displacement over each observation interval / its
+                               duration (n_head > 0) */
 } swimmer_config;
+
+enum { SWIMMER_OBS_HEAD_POINT = 0, SWIMMER_OBS_HEAD_VELOCITY = 1 };
 
 typedef struct swimmer_handle swimmer_handle;
 

@@ -190,9 +190,10 @@ def kernel_table(p: SpermParams):
     return KernelTable(p.flag.alpha, p.flag.delta, 1.25 * (p.flag.length + p.gap + 2 * p.hr))
 
 
-def run_numpy(p: SpermParams, table=None, steps=None):
-    """Forward Euler time loop.  Returns (obs[n_obs, 2] head-centre velocities, X_final,
-    status) with status 0 = ok, 1 = diverged (non-finite, or a point moving more than ds)."""
+def run_numpy(p: SpermParams, table=None, steps=None, observe="velocity"):
+    """Forward Euler time loop.  Returns (obs[n_obs, 2], X_final, status) with status 0 = ok,
+    1 = diverged (non-finite, or a point moving more than ds).  ``observe``: "velocity" for
+    head-centre velocities, "point" for the proximal flagellum point X_{N_F-1}."""
     fp = p.flag
     table = table or kernel_table(p)
     steps = fp.steps if steps is None else steps
@@ -206,7 +207,15 @@ def run_numpy(p: SpermParams, table=None, steps=None):
             return np.array(obs).reshape(-1, 2), X, 1
         X = X + fp.dt * v
         if (n + 1) % fp.obs_every == 0:
-            c = head_centre(X, p)
-            obs.append((c - c_prev) / (fp.obs_every * fp.dt))
-            c_prev = c
+            if observe == "velocity":
+                c = head_centre(X, p)
+                obs.append((c - c_prev) / (fp.obs_every * fp.dt))
+                c_prev = c
+            else:
+                obs.append(X[p.nf - 1].copy())
     return np.array(obs).reshape(-1, 2), X, 0
+
+
+def mean_speed(X0, X1, p: SpermParams, T):
+    """Head-centre x-displacement over the run divided by its duration."""
+    return float(head_centre(X1, p)[0] - head_centre(X0, p)[0]) / T

@@ -16,7 +16,9 @@ class SwimmerConfigC(ctypes.Structure):
         ("n_max", c_int), ("b_max", c_int), ("length", c_double), ("ds_fixed", c_double),
         ("mu", c_double), ("delta_over_ds", c_double), ("dt", c_double), ("k_t", c_double),
         ("eta", c_double), ("omega", c_double), ("steps", c_ll), ("obs_every", c_ll),
-        ("precision", c_int),
+        ("precision", c_int), ("n_head", c_int), ("head_radius_over_ds", c_double),
+        ("neck_gap_over_ds", c_double), ("k_head_tens", c_double), ("k_head_c", c_double),
+        ("k_neck_tens", c_double), ("k_neck_ang", c_double), ("obs_kind", c_int),
     ]
 
 

@@ -17,6 +17,9 @@ FP64 = 0
 FP32C = 1
 
 
+OBS_HEAD_POINT, OBS_HEAD_VELOCITY = 0, 1
+
+
 @dataclass
 class SwimmerConfig:
     """Mirror of ``swimmer_config`` (physical and numerical parameters, Table Tab:param)."""
@@ -34,6 +37,15 @@ class SwimmerConfig:
     steps: int = 80000
     obs_every: int = 800
     precision: int = FP32C
+    # full sperm model (head and neck); n_head = 0 is the flagellum alone
+    n_head: int = 0
+    head_radius_over_ds: float = 0.0
+    neck_gap_over_ds: float = 0.0
+    k_head_tens: float = 1e4
+    k_head_c: float = 0.8
+    k_neck_tens: float = 500.0
+    k_neck_ang: float = 1e4
+    obs_kind: int = 0  # OBS_HEAD_POINT or OBS_HEAD_VELOCITY
 
     def to_c(self):
         return SwimmerConfigC(**{f.name: getattr(self, f.name) for f in fields(self)})

@@ -114,6 +114,14 @@ static int check_config(const swimmer_config *c) {
     ARG_CHECK(c->steps >= 1, "steps must be >= 1");
     ARG_CHECK(c->obs_every >= 1, "obs_every must be >= 1");
     ARG_CHECK(c->precision == SWIMMER_FP64 || c->precision == SWIMMER_FP32C, "precision must be 0 or 1");
+    ARG_CHECK(c->n_head == 0 || (c->n_head >= 4 && c->n_head <= 256 && c->n_head % 2 == 0),
+              "n_head must be 0 or even in [4, 256]");
+    ARG_CHECK(c->n_head == 0 || c->n_max - c->n_head >= 3, "n_max must leave at least 3 flagellum points");
+    ARG_CHECK(c->head_radius_over_ds >= 0.0 && c->neck_gap_over_ds >= 0.0, "head sizes must be >= 0");
+    ARG_CHECK(c->k_head_tens >= 0.0 && c->k_head_c >= 0.0 && c->k_neck_tens >= 0.0 && c->k_neck_ang >= 0.0,
+              "head and neck stiffnesses must be >= 0");
+    ARG_CHECK(c->obs_kind == SWIMMER_OBS_HEAD_POINT || (c->obs_kind == SWIMMER_OBS_HEAD_VELOCITY && c->n_head > 0),
+              "obs_kind must be HEAD_POINT, or HEAD_VELOCITY with a head");
     return 0;
 }
 

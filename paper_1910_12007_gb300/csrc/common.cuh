@@ -37,8 +37,21 @@ constexpr double X_MAX = 600.0;        // largest alpha * r the Bessel evaluatio
 // per-sample derived parameters written by the table builder and read by the forward kernel
 struct SampleParams {
     double alpha, kc, amp, length, ds, delta;
-    int n, n_oct, status, pad;
+    int n, n_oct, status, nh;  // flagellum points, table octaves, status, head points
 };
+
+// head model geometry in units of ds (defaults: head points spaced like the flagellum's, a
+// gap of one ds), and the largest distance between two points of a straight swimmer of n
+// flagellum points (flagellum, neck gap, head diameter), in units of ds
+__host__ __device__ inline double head_radius_over_ds(const swimmer_config &c) {
+    return c.head_radius_over_ds > 0.0 ? c.head_radius_over_ds : c.n_head / (2.0 * 3.14159265358979323846);
+}
+__host__ __device__ inline double neck_gap_over_ds(const swimmer_config &c) {
+    return c.neck_gap_over_ds > 0.0 ? c.neck_gap_over_ds : 1.0;
+}
+__host__ __device__ inline double reach_over_ds(const swimmer_config &c, int n_flag) {
+    return (n_flag - 1) + (c.n_head > 0 ? neck_gap_over_ds(c) + 2.0 * head_radius_over_ds(c) : 0.0);
+}
 
 struct ProfileEvents;
 

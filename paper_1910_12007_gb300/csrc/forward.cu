@@ -46,6 +46,8 @@ struct FwdArgs {
     const double *tab64;
     const float4 *tab32;
     double mu, dt, kt, eta, omega;
+    double hr_over_ds, gap_over_ds, k_head_tens, k_head_c, k_neck_tens, k_neck_ang;  // head model
+    int obs_kind;
     long long steps, obs_every;
     const double *obs;
     double sigma;
@@ -94,6 +96,72 @@ __device__ __forceinline__ void acc_two_sum(float &s, float &e, float b) {
     two_sum(s, b, t, err);
     e += err;
     s = t;
+}
+
+// X_j - X_i of double-float coordinates (hi, lo) as a double-float (dh, dl)
+__device__ __forceinline__ void df_sub(const float *h, const float *l, int i, int j, float &dh, float &dl) {
+    float s, e;
+    two_sum(h[j], -h[i], s, e);
+    fast_two_sum(s, e + (l[j] - l[i]), dh, dl);
+}
+
+// A Hookean spring E = K (l/l0 - 1)^2 l0 (Eq. EFT's form): rest length l0 (and l0^2 as a
+// double-float), 2 K.  spring_*(i, j) returns t with force on i = t (X_j - X_i),
+// t = 2 K (l/l0 - 1)/l, and the strain l/l0 - 1 (from l^2/l0^2 - 1, without cancellation).
+struct RestF32 {
+    float l0, l02_hi, l02_lo, inv_l02, k2;
+};
+struct RestF64 {
+    double l0, inv_l02, k2;
+};
+
+__host__ __device__ inline RestF32 rest_f32(double l0, double k) {
+    RestF32 r;
+    r.l0 = (float)l0;
+    r.l02_hi = (float)(l0 * l0);
+    r.l02_lo = (float)(l0 * l0 - (double)r.l02_hi);
+    r.inv_l02 = (float)(1.0 / (l0 * l0));
+    r.k2 = (float)(2.0 * k);
+    return r;
+}
+
+__host__ __device__ inline RestF64 rest_f64(double l0, double k) {
+    RestF64 r;
+    r.l0 = l0;
+    r.inv_l02 = 1.0 / (l0 * l0);
+    r.k2 = 2.0 * k;
+    return r;
+}
+
+__device__ __forceinline__ float spring_f32(const float *xh, const float *xl, const float *yh, const float *yl, int i,
+                                            int j, const RestF32 &r, float &ex, float &ey, float &strain) {
+    float exh, exl, eyh, eyl;
+    df_sub(xh, xl, i, j, exh, exl);
+    df_sub(yh, yl, i, j, eyh, eyl);
+    // |e|^2 - l0^2 without cancellation: exact squares of the hi parts
+    float pxx = exh * exh, qxx = fmaf(exh, exh, -pxx);
+    float pyy = eyh * eyh, qyy = fmaf(eyh, eyh, -pyy);
+    float sp, spe;
+    two_sum(pxx, pyy, sp, spe);
+    float rest = ((spe + qxx + qyy) + 2.0f * (exh * exl + eyh * eyl)) - r.l02_lo;
+    float s2 = ((sp - r.l02_hi) + rest) * r.inv_l02;  // l^2/l0^2 - 1
+    float one = 1.0f + s2;
+    float root = one * rsqrtf(one);                   // l/l0
+    strain = __fdividef(s2, 1.0f + root);            // l/l0 - 1
+    float ell = r.l0 * (1.0f + strain);
+    ex = exh;
+    ey = eyh;
+    return __fdividef(r.k2 * strain, ell);
+}
+
+__device__ __forceinline__ double spring_f64(const double *sx, const double *sy, int i, int j, const RestF64 &r,
+                                             double &ex, double &ey, double &strain) {
+    ex = sx[j] - sx[i];
+    ey = sy[j] - sy[i];
+    double s2 = fma(fma(ex, ex, ey * ey), r.inv_l02, -1.0);  // l^2/l0^2 - 1
+    strain = s2 / (1.0 + sqrt(1.0 + s2));
+    double ell = r.l0 * (1.0 + strain);
+    return r.k2 * strain / ell;
 }
 
 // table region in shared memory: FP32: float4 part A [P] then float2 part B [P];
@@ -230,7 +298,34 @@ __device__ __forceinline__ void pair_unit(const float4 *__restrict__ s4, const f
     }
 }
 
+// observations are head-centre velocities (head model), else the proximal point's position
+__device__ __forceinline__ bool vel_obs(const FwdArgs &a, int nh) {
+    return a.obs_kind == SWIMMER_OBS_HEAD_VELOCITY && nh > 0;
+}
+
+// Mean of the head points (FP64 sums over one warp, fixed order); all lanes of warp 0 call
+// it, lane 0 gets the result.
 template <bool F64>
+__device__ __forceinline__ void head_centre(const double *sx, const double *sy, const float *xh, const float *xl,
+                                            const float *yh, const float *yl, int nf, int nh, int lane, double &cx,
+                                            double &cy) {
+    cx = 0.0;
+    cy = 0.0;
+    for (int m = lane; m < nh; m += 32) {
+        const int k = nf + m;
+        cx += F64 ? sx[k] : (double)xh[k] + (double)xl[k];
+        cy += F64 ? sy[k] : (double)yh[k] + (double)yl[k];
+    }
+    for (int o = 16; o >= 1; o >>= 1) {
+        cx += __shfl_xor_sync(0xffffffffu, cx, o);
+        cy += __shfl_xor_sync(0xffffffffu, cy, o);
+    }
+    cx /= nh;
+    cy /= nh;
+}
+
+// HEAD: the full sperm model (head points and neck); without it the head code compiles out
+template <bool F64, bool HEAD>
 __global__ void __launch_bounds__(1024) forward_kernel(FwdArgs a) {
     typedef typename Types<F64>::R R;
     typedef typename Types<F64>::R4 R4;
@@ -248,7 +343,14 @@ __global__ void __launch_bounds__(1024) forward_kernel(FwdArgs a) {
     float2 *part = (float2 *)tvx;  // FP32 pair sum: per-warp partial velocities
     unsigned char *tabraw = smraw + state_bytes<F64>(n_max, blockDim.x);
     __shared__ int s_work;
-    __shared__ double s_red[32];
+    // the sample's model constants: [0, 18) the springs (flagellum segment, head membrane,
+    // diametral, neck A (end to H(pi +- dth)), neck B (next-to-end to H(pi +- dth)), neck
+    // gap (end to H(pi))) as RestF64 or RestF32 records; then 1/(2 ds_H), 1/ds_H^2, 1/H_r,
+    // 2 K_HC ds_H, 2 K_NA; [23, 25) the head centre at the previous observation
+    __shared__ double s_model[26];
+    const RestF32 *rest32 = (const RestF32 *)s_model;
+    const RestF64 *rest64 = (const RestF64 *)s_model;
+    enum { M_I2H = 18, M_IH2, M_IHR, M_KHC, M_KANG, M_CX, M_CY };
 
     const int tid = threadIdx.x, T = blockDim.x;
     const int lane = tid & 31;
@@ -260,7 +362,8 @@ __global__ void __launch_bounds__(1024) forward_kernel(FwdArgs a) {
         if (w >= a.B) break;
         const int b = a.order[w];
         const SampleParams p = a.sp[b];
-        const int n = p.n;
+        const int nf = p.n, nh = HEAD ? p.nh : 0, h2 = nh >> 1;
+        const int n = nf + nh;  // flagellum points, then head points
         const long long n_obs = a.steps / a.obs_every;
         if (p.status != SWIMMER_OK) {
             if (tid == 0) {
@@ -319,21 +422,55 @@ __global__ void __launch_bounds__(1024) forward_kernel(FwdArgs a) {
                 units[un] = I | (Jb << 8) | (d0 << 16);
             }
         }
-        // ---- initial straight filament X_k = (k ds, 0), stored relative to (L/2, 0)
+        // ---- initial straight filament X_k = (k ds, 0), stored relative to (L/2, 0); the
+        //      head circle's centre H_r + dN to the right of the proximal point, head point m
+        //      at angle 2 pi m / N_H (Appendix)
         const double ds = p.ds, L = p.length;
         const double xref = 0.5 * L;
+        {
+        const double hr = a.hr_over_ds * ds, gap = a.gap_over_ds * ds;
+        const double dth = nh ? 2.0 * PI / nh : 0.0, dsh = hr * dth;
         for (int k = tid; k < n; k += T) {
-            double x0 = k * ds - xref;
+            double x0, y0;
+            if (k < nf) {
+                x0 = k * ds - xref;
+                y0 = 0.0;
+            } else {
+                double sn, cs;
+                sincos((k - nf) * dth, &sn, &cs);
+                x0 = L + gap + hr + hr * cs - xref;
+                y0 = hr * sn;
+            }
             if (F64) {
                 sx[k] = x0;
-                sy[k] = 0.0;
+                sy[k] = y0;
             } else {
                 float h = (float)x0;
                 xh[k] = h;
                 xl[k] = (float)(x0 - (double)h);
-                yh[k] = 0.f;
-                yl[k] = 0.f;
+                h = (float)y0;
+                yh[k] = h;
+                yl[k] = (float)(y0 - (double)h);
             }
+        }
+        if (tid == 0) {
+            const double c1 = hr * (1.0 - cos(dth)), s1 = hr * sin(dth);
+            const double l0[6] = {ds, 2.0 * hr * sin(0.5 * dth), 2.0 * hr, hypot(gap + c1, s1), hypot(ds + gap + c1, s1),
+                                  gap};
+            const double kk[6] = {a.kt, a.k_head_tens, a.k_head_tens, a.k_neck_tens, a.k_neck_tens, a.k_neck_tens};
+            for (int q = 0; q < 6; ++q) {
+                const double lq = l0[q] > 0.0 ? l0[q] : 1.0;  // unused without a head
+                if (F64)
+                    ((RestF64 *)s_model)[q] = rest_f64(lq, kk[q]);
+                else
+                    ((RestF32 *)s_model)[q] = rest_f32(lq, kk[q]);
+            }
+            s_model[M_I2H] = nh ? 0.5 / dsh : 0.0;
+            s_model[M_IH2] = nh ? 1.0 / (dsh * dsh) : 0.0;
+            s_model[M_IHR] = nh ? 1.0 / hr : 0.0;
+            s_model[M_KHC] = 2.0 * a.k_head_c * dsh;
+            s_model[M_KANG] = 2.0 * a.k_neck_ang;
+        }
         }
         if (!F64) {  // pad the last block with force-free sources at the origin
             const int npad = ((n + 31) >> 5) << 5;
@@ -344,9 +481,8 @@ __global__ void __launch_bounds__(1024) forward_kernel(FwdArgs a) {
             }
         }
         const double inv_ds2 = 1.0 / (ds * ds);
-        const float ds2_hi = (float)(ds * ds), ds2_lo = (float)(ds * ds - (double)ds2_hi);
         const R r_ds = (R)ds, r_inv2ds = (R)(0.5 / ds), r_invds2 = (R)inv_ds2;
-        const R kt2 = (R)(2.0 * a.kt), kc2ds = (R)(2.0 * p.kc * ds);
+        const R kc2ds = (R)(2.0 * p.kc * ds);
         const R r_amp = (R)p.amp, r_eta = (R)a.eta, r_omega = (R)a.omega, r_L = (R)L;
         const R inv_d2 = (R)(1.0 / (p.delta * p.delta));
         const double dt_mu = a.dt / a.mu;
@@ -360,12 +496,22 @@ __global__ void __launch_bounds__(1024) forward_kernel(FwdArgs a) {
         // FP32 pair sum: ceil(n/32)^2 units of 16 steps over the pair warps
         const int nb = (n + 31) >> 5, n_units = nb * nb;
         const int n_pw = pair_warps(n_max, T);
-        // the thread that updates the head point n - 1 (observations, log-likelihood)
-        const bool head_thread = F64 ? (owner && tgt == n - 1) : (tid == (n - 1) % T);
+        // the thread that keeps the log-likelihood: thread 0 for head-centre velocities (one
+        // warp reduces the head after each observation step), else the one that updates the
+        // proximal flagellum point nf - 1 (the observed point)
+        const bool head_thread = vel_obs(a, nh) ? tid == 0 : F64 ? (owner && tgt == nf - 1) : (tid == (nf - 1) % T);
         double J = 0.0;
         int status = SWIMMER_OK;
         long long steps_done = a.steps;
         __syncthreads();
+        if (vel_obs(a, nh) && tid < 32) {  // head centre at the previous observation
+            double cx, cy;
+            head_centre<F64>(sx, sy, xh, xl, yh, yl, nf, nh, lane, cx, cy);
+            if (tid == 0) {
+                s_model[M_CX] = cx;
+                s_model[M_CY] = cy;
+            }
+        }
         float g10 = 0.f;  // FP32: g1 at r = 0 (self term)
         if (!F64) {
             float g2unused;
@@ -377,65 +523,51 @@ __global__ void __launch_bounds__(1024) forward_kernel(FwdArgs a) {
             const R tR = (R)(step * a.dt);
             int bad = 0;
             // ---- A+B: segments, tension, curvature stencils, relative positions.  Thread k
-            //      forms e_k (tension of segment k) and again e_{k-1} (for the curvature at
-            //      k), which saves a barrier.
+            //      forms e_k (tension of the segment to its next point) and again e_{k-1}
+            //      (for the curvature at k), which saves a barrier.  Flagellum points
+            //      k < nf form an open chain; head points a closed one (periodic stencils).
             for (int k = tid; k < n; k += T) {
+                const bool hd = HEAD && k >= nf;
+                const int m = k - nf;
+                const int next = hd ? nf + (m + 1 == nh ? 0 : m + 1) : (k + 1 < nf ? k + 1 : -1);
+                const int prev = hd ? nf + (m == 0 ? nh - 1 : m - 1) : k - 1;
+                const bool center = hd || (k >= 1 && k + 1 < nf);
                 R qx, qy, epx = 0, epy = 0, emx = 0, emy = 0, tk = 0;
                 if (F64) {
-                    if (k + 1 < n) {
-                        double ex = sx[k + 1] - sx[k], ey = sy[k + 1] - sy[k];
-                        double s2 = fma(fma(ex, ex, ey * ey), inv_ds2, -1.0);  // l^2/ds^2 - 1
-                        R strain = (R)(s2 / (1.0 + sqrt(1.0 + s2)));
-                        R ell = r_ds * ((R)1 + strain);
+                    if (next >= 0) {
+                        double ex, ey, strain;
+                        tk = (R)spring_f64(sx, sy, k, next, rest64[hd ? 1 : 0], ex, ey, strain);
                         epx = (R)ex;
                         epy = (R)ey;
-                        tk = kt2 * strain / ell;
-                        if (!(fabs((double)strain) <= STRETCH_MAX)) bad = 1;
+                        if (!(fabs(strain) <= STRETCH_MAX)) bad = 1;
                     }
-                    if (k >= 1) {
-                        emx = (R)(sx[k] - sx[k - 1]);
-                        emy = (R)(sy[k] - sy[k - 1]);
+                    if (center) {
+                        emx = (R)(sx[k] - sx[prev]);
+                        emy = (R)(sy[k] - sy[prev]);
                     }
                     qx = (R)sx[k];
                     qy = (R)sy[k];
                 } else {
-                    float s, e, lo;
-                    if (k + 1 < n) {
-                        // e = X_{k+1} - X_k as a double-float (hi, lo)
-                        two_sum(xh[k + 1], -xh[k], s, e);
-                        float exh, exl;
-                        fast_two_sum(s, e + (xl[k + 1] - xl[k]), exh, exl);
-                        two_sum(yh[k + 1], -yh[k], s, e);
-                        float eyh, eyl;
-                        fast_two_sum(s, e + (yl[k + 1] - yl[k]), eyh, eyl);
-                        // |e|^2 - ds^2 without cancellation: exact squares of the hi parts
-                        float pxx = exh * exh, qxx = fmaf(exh, exh, -pxx);
-                        float pyy = eyh * eyh, qyy = fmaf(eyh, eyh, -pyy);
-                        float sp, spe;
-                        two_sum(pxx, pyy, sp, spe);
-                        float rest = ((spe + qxx + qyy) + 2.0f * (exh * exl + eyh * eyl)) - ds2_lo;
-                        float s2 = ((sp - ds2_hi) + rest) * (float)inv_ds2;  // l^2/ds^2 - 1
-                        float one = 1.0f + s2;
-                        float root = one * rsqrtf(one);                     // l/ds
-                        float strain = __fdividef(s2, 1.0f + root);        // l/ds - 1
-                        float ell = ds_f * (1.0f + strain);
-                        epx = (R)exh;
-                        epy = (R)eyh;
-                        tk = (R)__fdividef((float)kt2 * strain, ell);
+                    if (next >= 0) {
+                        float strain, ex, ey;
+                        tk = (R)spring_f32(xh, xl, yh, yl, k, next, rest32[hd ? 1 : 0], ex, ey, strain);
+                        epx = (R)ex;
+                        epy = (R)ey;
                         if (!(fabsf(strain) <= (float)STRETCH_MAX)) bad = 1;
                     }
-                    if (k >= 1) {
-                        two_sum(xh[k], -xh[k - 1], s, e);
-                        lo = e + (xl[k] - xl[k - 1]);
+                    if (center) {
+                        float s, e, lo;
+                        two_sum(xh[k], -xh[prev], s, e);
+                        lo = e + (xl[k] - xl[prev]);
                         emx = (R)(s + lo);
-                        two_sum(yh[k], -yh[k - 1], s, e);
-                        lo = e + (yl[k] - yl[k - 1]);
+                        two_sum(yh[k], -yh[prev], s, e);
+                        lo = e + (yl[k] - yl[prev]);
                         emy = (R)(s + lo);
                     }
                     qx = (R)(xh[k] + xl[k]);
                     qy = (R)(yh[k] + yl[k]);
                 }
-                if (k + 1 < n) {  // tension force vector of segment k
+                if (next >= 0) {  // tension force vector of segment (k, next)
                     tvx[k] = tk * epx;
                     tvy[k] = tk * epy;
                 }
@@ -445,9 +577,10 @@ __global__ void __launch_bounds__(1024) forward_kernel(FwdArgs a) {
                 src[ks].y = qy;
                 src[kd].x = qx;
                 src[kd].y = qy;
-                if (k >= 1 && k + 1 < n) {
-                    R A = (emx + epx) * r_inv2ds, Bv = (emy + epy) * r_inv2ds;
-                    R C = (epx - emx) * r_invds2, D = (epy - emy) * r_invds2;
+                if (center) {
+                    const R i2h = hd ? (R)s_model[M_I2H] : r_inv2ds, ih2 = hd ? (R)s_model[M_IH2] : r_invds2;
+                    R A = (emx + epx) * i2h, Bv = (emy + epy) * i2h;
+                    R C = (epx - emx) * ih2, D = (epy - emy) * ih2;
                     R S2 = A * A + Bv * Bv;
                     R rs;
                     if (F64)
@@ -458,59 +591,144 @@ __global__ void __launch_bounds__(1024) forward_kernel(FwdArgs a) {
                     R S25 = S15 * rs * rs;
                     R cross = A * D - Bv * C;
                     R zeta = cross * S15;
-                    R s = (R)k * r_ds;
-                    R ph = r_eta * s - r_omega * tR;
-                    R sn, cs;
-                    if (F64) {
-                        double sd, cd;
-                        sincos((double)ph, &sd, &cd);
-                        sn = (R)sd;
-                        cs = (R)cd;
+                    R zhat;
+                    if (hd) {
+                        zhat = (R)s_model[M_IHR];  // preferred head curvature 1/H_r
                     } else {
-                        // reduce to [-pi, pi], then the fast hardware approximation
-                        float pf = (float)ph;
-                        pf = fmaf(-6.28318530717958648f, rintf(pf * 0.159154943091895336f), pf);
-                        float sf, cf;
-                        __sincosf(pf, &sf, &cf);
-                        sn = (R)sf;
-                        cs = (R)cf;
+                        R s = (R)k * r_ds;
+                        R ph = r_eta * s - r_omega * tR;
+                        R sn, cs;
+                        if (F64) {
+                            double sd, cd;
+                            sincos((double)ph, &sd, &cd);
+                            sn = (R)sd;
+                            cs = (R)cd;
+                        } else {
+                            // reduce to [-pi, pi], then the fast hardware approximation
+                            float pf = (float)ph;
+                            pf = fmaf(-6.28318530717958648f, rintf(pf * 0.159154943091895336f), pf);
+                            float sf, cf;
+                            __sincosf(pf, &sf, &cf);
+                            sn = (R)sf;
+                            cs = (R)cf;
+                        }
+                        zhat = -r_amp * ((R)2 * r_eta / r_L * cs + ((R)1 - s / r_L) * r_eta * r_eta * sn);
                     }
-                    R zhat = -r_amp * ((R)2 * r_eta / r_L * cs + ((R)1 - s / r_L) * r_eta * r_eta * sn);
-                    R ck = kc2ds * (zeta - zhat);
+                    R ck = (hd ? (R)s_model[M_KHC] : kc2ds) * (zeta - zhat);
                     R za = D * S15 - (R)3 * A * cross * S25;
                     R zb = -C * S15 - (R)3 * Bv * cross * S25;
                     R zc = -Bv * S15, zd = A * S15;
-                    bend[0 * n_max + k] = ck * (-za * r_inv2ds + zc * r_invds2);
-                    bend[1 * n_max + k] = ck * (-zb * r_inv2ds + zd * r_invds2);
-                    bend[2 * n_max + k] = ck * ((R)-2 * zc * r_invds2);
-                    bend[3 * n_max + k] = ck * ((R)-2 * zd * r_invds2);
-                    bend[4 * n_max + k] = ck * (za * r_inv2ds + zc * r_invds2);
-                    bend[5 * n_max + k] = ck * (zb * r_inv2ds + zd * r_invds2);
+                    bend[0 * n_max + k] = ck * (-za * i2h + zc * ih2);
+                    bend[1 * n_max + k] = ck * (-zb * i2h + zd * ih2);
+                    bend[2 * n_max + k] = ck * ((R)-2 * zc * ih2);
+                    bend[3 * n_max + k] = ck * ((R)-2 * zd * ih2);
+                    bend[4 * n_max + k] = ck * (za * i2h + zc * ih2);
+                    bend[5 * n_max + k] = ck * (zb * i2h + zd * ih2);
                 }
             }
             __syncthreads();
-            // ---- C: point forces
+            // ---- C: point forces, gathered per point (no atomics): segment tensions, the
+            //      bending stencils of the centres k-1, k, k+1, and for the head model the
+            //      diametral and neck springs and the neck angle (Appendix)
             for (int k = tid; k < n; k += T) {
+                const bool hd = HEAD && k >= nf;
+                const int m = k - nf;
+                const int next = hd ? nf + (m + 1 == nh ? 0 : m + 1) : (k + 1 < nf ? k + 1 : -1);
+                const int prev = hd ? nf + (m == 0 ? nh - 1 : m - 1) : k - 1;
                 R fx = 0, fy = 0;
-                if (k + 1 < n) {
+                if (next >= 0) {
                     fx += tvx[k];
                     fy += tvy[k];
                 }
-                if (k >= 1) {
-                    fx -= tvx[k - 1];
-                    fy -= tvy[k - 1];
+                if (prev >= 0) {
+                    fx -= tvx[prev];
+                    fy -= tvy[prev];
                 }
-                if (k >= 2) {
-                    fx -= bend[4 * n_max + k - 1];
-                    fy -= bend[5 * n_max + k - 1];
+                if (hd || k >= 2) {  // centre prev acts on k as its next neighbour
+                    fx -= bend[4 * n_max + prev];
+                    fy -= bend[5 * n_max + prev];
                 }
-                if (k >= 1 && k + 1 < n) {
+                if (hd || (k >= 1 && k + 1 < nf)) {
                     fx -= bend[2 * n_max + k];
                     fy -= bend[3 * n_max + k];
                 }
-                if (k + 2 < n) {
-                    fx -= bend[0 * n_max + k + 1];
-                    fy -= bend[1 * n_max + k + 1];
+                if (hd || k + 2 < nf) {  // centre next acts on k as its previous neighbour
+                    fx -= bend[0 * n_max + next];
+                    fy -= bend[1 * n_max + next];
+                }
+                if (HEAD && nh > 0) {
+                    // springs (k, j): force on k = t e, e = X_j - X_k; up to three per point
+                    for (int q = 0; q < 3; ++q) {
+                        int j = -1, kind = 0;  // kind: 0 diametral, 1 neck A, 2 neck B, 3 neck gap
+                        if (hd) {
+                            if (q == 0) {
+                                j = nf + (m + h2 >= nh ? m + h2 - nh : m + h2);
+                            } else if (m == h2 - 1 || m == h2 + 1) {
+                                j = q == 1 ? nf - 1 : nf - 2;
+                                kind = q;
+                            } else if (m == h2 && q == 1) {
+                                j = nf - 1;
+                                kind = 3;
+                            }
+                        } else if (k == nf - 1) {
+                            j = nf + h2 - 1 + q;
+                            kind = q == 1 ? 3 : 1;
+                        } else if (k == nf - 2 && q < 2) {
+                            j = nf + h2 - 1 + 2 * q;
+                            kind = 2;
+                        }
+                        if (j < 0) continue;
+                        if (F64) {
+                            const RestF64 &r = rest64[2 + kind];
+                            double ex, ey, strain;
+                            double t = spring_f64(sx, sy, k, j, r, ex, ey, strain);
+                            fx += (R)(t * ex);
+                            fy += (R)(t * ey);
+                            if (!(fabs(strain) <= STRETCH_MAX)) bad = 1;
+                        } else {
+                            const RestF32 &r = rest32[2 + kind];
+                            float ex, ey, strain;
+                            float t = spring_f32(xh, xl, yh, yl, k, j, r, ex, ey, strain);
+                            fx += (R)(t * ex);
+                            fy += (R)(t * ey);
+                            if (!(fabsf(strain) <= (float)STRETCH_MAX)) bad = 1;
+                        }
+                    }
+                    // neck angle E = K (z1 . z2)^2, z1 = H(pi) - X_{nf-1}, z2 = H(pi+dth) - H(pi-dth)
+                    const int ihp = nf + h2, iplus = nf + h2 + 1, iminus = nf + h2 - 1, iend = nf - 1;
+                    if (k == ihp || k == iplus || k == iminus || k == iend) {
+                        R z1x, z1y, z2x, z2y;
+                        if (F64) {
+                            z1x = (R)(sx[ihp] - sx[iend]);
+                            z1y = (R)(sy[ihp] - sy[iend]);
+                            z2x = (R)(sx[iplus] - sx[iminus]);
+                            z2y = (R)(sy[iplus] - sy[iminus]);
+                        } else {
+                            float h, l;
+                            df_sub(xh, xl, iend, ihp, h, l);
+                            z1x = (R)(h + l);
+                            df_sub(yh, yl, iend, ihp, h, l);
+                            z1y = (R)(h + l);
+                            df_sub(xh, xl, iminus, iplus, h, l);
+                            z2x = (R)(h + l);
+                            df_sub(yh, yl, iminus, iplus, h, l);
+                            z2y = (R)(h + l);
+                        }
+                        const R w = (R)s_model[M_KANG] * (z1x * z2x + z1y * z2y);
+                        if (k == ihp) {
+                            fx -= w * z2x;
+                            fy -= w * z2y;
+                        } else if (k == iend) {
+                            fx += w * z2x;
+                            fy += w * z2y;
+                        } else if (k == iplus) {
+                            fx -= w * z1x;
+                            fy -= w * z1y;
+                        } else {
+                            fx += w * z1x;
+                            fy += w * z1y;
+                        }
+                    }
                 }
                 const int ks = F64 ? k : ((k >> 5) << 6) + (k & 31);
                 const int kd = F64 ? k + n : ks + 32;
@@ -576,7 +794,7 @@ __global__ void __launch_bounds__(1024) forward_kernel(FwdArgs a) {
             if (!F64) __syncthreads();
             // ---- E: Euler step, divergence, observations
             for (int k = F64 ? (owner ? tgt : n) : tid; k < n; k += F64 ? n : T) {
-                const bool head_obs = (k == n - 1) && ((step + 1) % a.obs_every == 0);
+                const bool head_obs = !vel_obs(a, nh) && (k == nf - 1) && ((step + 1) % a.obs_every == 0);
                 double hxo = 0.0, hyo = 0.0;
                 if (F64) {
                     double dx = vxd * dt_mu, dy = vyd * dt_mu;  // displacement this step
@@ -628,19 +846,39 @@ __global__ void __launch_bounds__(1024) forward_kernel(FwdArgs a) {
                 steps_done = step + 1;
                 break;
             }
+            if (vel_obs(a, nh) && (step + 1) % a.obs_every == 0 && tid < 32) {
+                // head-centre velocity over the observation interval (Sec. 4.1)
+                double cx, cy;
+                head_centre<F64>(sx, sy, xh, xl, yh, yl, nf, nh, lane, cx, cy);
+                if (tid == 0) {
+                    const double inv = 1.0 / ((double)a.obs_every * a.dt);
+                    const double vx = (cx - s_model[M_CX]) * inv, vy = (cy - s_model[M_CY]) * inv;
+                    s_model[M_CX] = cx;
+                    s_model[M_CY] = cy;
+                    const long long o = (step + 1) / a.obs_every - 1;
+                    if (a.obs) {
+                        double rx = a.obs[2 * o] - vx, ry = a.obs[2 * o + 1] - vy;
+                        J = fma(rx, rx, fma(ry, ry, J));
+                    }
+                    if (a.head_traj) {
+                        a.head_traj[((size_t)b * n_obs + o) * 2] = vx;
+                        a.head_traj[((size_t)b * n_obs + o) * 2 + 1] = vy;
+                    }
+                }
+            }
         }
         // ---- outputs
-        if (a.speed) {
+        if (a.speed && tid < 32) {
+            // mean speed: x-displacement of the flagellum's centroid (which starts at 0 in the
+            // stored coordinates) or, with a head, of the head centre, over the run's duration;
+            // one warp sums in a fixed order
+            const int k0 = nh > 0 ? nf : 0;
             double cx = 0.0;
-            for (int k = tid; k < n; k += T) cx += F64 ? sx[k] : (double)xh[k] + (double)xl[k];
+            for (int k = k0 + lane; k < n; k += 32) cx += F64 ? sx[k] : (double)xh[k] + (double)xl[k];
             for (int o = 16; o >= 1; o >>= 1) cx += __shfl_xor_sync(0xffffffffu, cx, o);
-            if (lane == 0) s_red[tid >> 5] = cx;
-            __syncthreads();
             if (tid == 0) {
-                double tot = 0.0;
-                for (int i = 0; i < (T + 31) / 32; ++i) tot += s_red[i];
-                // the centroid starts at x = L/2, which is 0 in the stored coordinates
-                a.speed[b] = status == SWIMMER_OK ? (tot / n) / (a.steps * a.dt) : nan("");
+                const double c0 = nh > 0 ? L + (a.gap_over_ds + a.hr_over_ds) * ds - xref : 0.0;
+                a.speed[b] = status == SWIMMER_OK ? (cx / (n - k0) - c0) / (a.steps * a.dt) : nan("");
             }
         }
         if (tid == 0) {
@@ -669,6 +907,13 @@ __global__ void __launch_bounds__(1024) forward_kernel(FwdArgs a) {
     }
 }
 
+typedef void (*ForwardKernel)(FwdArgs);
+
+ForwardKernel forward_kernel_for(bool f64, bool head) {
+    return f64 ? (head ? forward_kernel<true, true> : forward_kernel<true, false>)
+               : (head ? forward_kernel<false, true> : forward_kernel<false, false>);
+}
+
 }  // namespace
 
 // Threads per sample: at least one per target (FP64) or one warp per pair unit (FP32);
@@ -688,7 +933,7 @@ int forward_slots(const swimmer_handle *h, int precision) {
     const int T = forward_min_threads(h, precision);
     const int P = handle_octaves(h) * (f64 ? F64_SUB : F32_SUB);
     size_t smem = f64 ? smem_bytes<true>(h->cfg.n_max, P, T) : smem_bytes<false>(h->cfg.n_max, P, T);
-    auto kern = f64 ? forward_kernel<true> : forward_kernel<false>;
+    auto kern = forward_kernel_for(f64, h->cfg.n_head > 0);
     int per_sm = 0;
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
         cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared) !=
@@ -743,6 +988,13 @@ int launch_forward(swimmer_handle *h, int B, const double *obs, double sigma, do
     a.mu = h->cfg.mu;
     a.dt = h->cfg.dt;
     a.kt = h->cfg.k_t;
+    a.hr_over_ds = head_radius_over_ds(h->cfg);
+    a.gap_over_ds = neck_gap_over_ds(h->cfg);
+    a.k_head_tens = h->cfg.k_head_tens;
+    a.k_head_c = h->cfg.k_head_c;
+    a.k_neck_tens = h->cfg.k_neck_tens;
+    a.k_neck_ang = h->cfg.k_neck_ang;
+    a.obs_kind = h->cfg.obs_kind;
     a.eta = h->cfg.eta;
     a.omega = h->cfg.omega;
     a.steps = h->cfg.steps;
@@ -762,7 +1014,7 @@ int launch_forward(swimmer_handle *h, int B, const double *obs, double sigma, do
     const bool f64 = precision == SWIMMER_FP64;
     a.tab_panels = handle_octaves(h) * (f64 ? F64_SUB : F32_SUB);
     size_t smem = f64 ? smem_bytes<true>(a.n_max, a.tab_panels, T) : smem_bytes<false>(a.n_max, a.tab_panels, T);
-    auto kern = f64 ? forward_kernel<true> : forward_kernel<false>;
+    auto kern = forward_kernel_for(f64, h->cfg.n_head > 0);
     CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
                                   cudaSharedmemCarveoutMaxShared));
