@@ -211,12 +211,13 @@ def main():
     ap.add_argument("--profile-case", action="store_true",
                     help="run one forward batch of the workload (1024 samples, 200 steps) for ncu and exit")
     ap.add_argument("--workload", default="tmcmc",
-                    choices=["tmcmc", "uneven", "large", "surrogate", "shapes", "sperm"],
+                    choices=["tmcmc", "uneven", "large", "surrogate", "shapes", "sperm", "sperm-tmcmc"],
                     help="tmcmc (default): TMCMC stages, 1024 samples, N=128; uneven: 4096 samples with "
                          "N in {64,128,256,512} in one graph-captured persistent launch; large: 256 samples "
                          "x N=1024 x 4e4 steps; surrogate: delayed-acceptance vs plain TMCMC, 4096 samples/stage; "
                          "shapes: forward-kernel time per step vs samples per SM and threads per sample; sperm: "
-                         "1024 full sperm models (flagellum 50 + head 24 points, Table Tab:param) x one beat")
+                         "1024 full sperm models (flagellum 50 + head 24 points, Table Tab:param) x one beat; "
+                         "sperm-tmcmc: a whole TMCMC run on the full sperm model, head-centre velocities")
     args = ap.parse_args()
 
     from paper_1910_12007_gb300 import ranks
@@ -237,6 +238,8 @@ def main():
         return surrogate_workload(args, rank, world, local_rank)
     if args.workload == "shapes":
         return shapes_workload(args, rank, local_rank)
+    if args.workload == "sperm-tmcmc":
+        return sperm_tmcmc_workload(args, rank, local_rank)
 
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
@@ -592,6 +595,64 @@ def shapes_workload(args, rank, local_rank):
         rows.append({"samples": B, "samples_per_sm": B / sms, "us_per_step_by_threads": row})
     print(json.dumps({"workload": f"forward kernel, N={N_PTS}, {steps} steps, FP32C: microseconds per time step",
                       "sms": sms, "rows": rows}), flush=True)
+    h.close()
+    return 0
+
+
+# -------------------------------------------------------------------------------------
+# a whole TMCMC run on the full sperm model (the paper's single-swimmer experiments)
+# -------------------------------------------------------------------------------------
+def sperm_tmcmc_workload(args, rank, local_rank):
+    import numpy as np
+    import torch
+
+    import paper_1910_12007_gb300 as g
+    import synthetic
+
+    if rank != 0:
+        return 0
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    # Table Tab:param swimmer, 2000 samples per stage (Sec. 4), head-centre velocities at 50
+    # observation times; the horizon is T = 2 (4 beats) instead of T = 20, at the stable
+    # dt = 1e-4 / 8 (1.6e5 steps per run)
+    B, steps, obs_every = 2000, 160000, 3200
+    cfg = g.SwimmerConfig(n_max=74, b_max=B, length=1.0, delta_over_ds=0.045 * 49, dt=1e-4 / 8, k_t=1e4,
+                          omega=4 * math.pi, steps=steps, obs_every=obs_every, precision=g.FP32C, n_head=24,
+                          k_head_tens=1e4, k_head_c=0.8, k_neck_tens=500.0, k_neck_ang=1e4,
+                          obs_kind=g.OBS_HEAD_VELOCITY)
+    h = g.swimmer_init(cfg)
+    lo, hi = (0.0, 0.6, 0.08), (5.0, 0.95, 0.12)
+    th_tune = torch.tensor(synthetic.prior_samples(4243, lo, hi, B), device=dev)
+    g.swimmer_autotune(h, steps=2000, theta=th_tune)
+    truth = (1.0, math.log10(8.0), 0.1)
+    xi = g.forward_batch(h, torch.tensor([truth], dtype=torch.float64, device=dev))[0][0].cpu().numpy()
+    sigma = 0.1 * float(np.mean(np.abs(xi)))  # 10 % noise
+    obs = torch.tensor(xi + sigma * synthetic.normals(1235, synthetic.NOISE, 0, xi.size).reshape(xi.shape),
+                       device=dev)
+    th0 = torch.tensor(synthetic.prior_samples(601, lo, hi, B), device=dev)
+    log = []
+    g.swimmer_profile(h, 1)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    st = g.tmcmc_run(h, th0, obs, sigma, lo, hi, lambda j: synthetic.stage_randoms(601, j, B, 3), log=log)
+    torch.cuda.synchronize()
+    secs = time.perf_counter() - t0
+    _, _, _, pairs_exec, pairs = g.swimmer_profile(h, 2)
+    g.swimmer_profile(h, 0)
+    th = st.theta.cpu().numpy()
+    samples = B * (len(log) + 1)  # the prior draw and every stage's population
+    line = {"metric": METRIC, "value": samples / secs, "unit": "TMCMC samples/s", "n_gpus": 1, "steps": len(log),
+            "warmup": 0, "ms_per_step": 1e3 * secs / max(len(log), 1), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "TMCMC on the full sperm model (flagellum 50 + head 24 points, Table Tab:param), "
+                                   "2000 samples per stage, theta = (alpha, log10 K_C, a), head-centre velocities "
+                                   "at 50 times over T = 2 (1.6e5 steps per run, dt = 1e-4/8), 10 % noise"},
+            "stages": len(log), "seconds": secs, "pair_evals_per_s": pairs / secs,
+            "executed_pair_evals_per_s": pairs_exec / secs,
+            "posterior_mean": th.mean(0).tolist(), "posterior_sd": th.std(0).tolist(), "truth": list(truth),
+            "q": [s["q"] for s in log]}
+    print(json.dumps(line), flush=True)
     h.close()
     return 0
 
