@@ -219,3 +219,77 @@ def run_numpy(p: SpermParams, table=None, steps=None, observe="velocity"):
 def mean_speed(X0, X1, p: SpermParams, T):
     """Head-centre x-displacement over the run divided by its duration."""
     return float(head_centre(X1, p)[0] - head_centre(X0, p)[0]) / T
+
+
+# ---------------------------------------------------------------------------------------
+# Two swimmers (Sec. 4.2): the same swimmer twice, the second displaced by d along y; each
+# has its own elastic energy, the fluid couples them through the pair sum over all points.
+# Observations: the distance between the last points of the tails (flagellum point 0) and
+# between the head centres, every obs_every steps.
+# ---------------------------------------------------------------------------------------
+@dataclass(frozen=True)
+class PairParams:
+    one: SpermParams
+    d: float = 2.0  # initial vertical separation of the two swimmers
+
+    @property
+    def nt(self):
+        return 2 * self.one.nt
+
+
+def pair_initial_shape(q: PairParams):
+    X = initial_shape(q.one)
+    return np.concatenate([X, X + np.array([0.0, q.d])])
+
+
+def pair_forces(X, q: PairParams, t):
+    n = q.one.nt
+    return np.concatenate([forces(X[:n], q.one, t), forces(X[n:], q.one, t)])
+
+
+def pair_energy(X, q: PairParams, t):
+    n = q.one.nt
+    return energy(X[:n], q.one, t) + energy(X[n:], q.one, t)
+
+
+def pair_distances(X, q: PairParams):
+    """(tail-tip distance, head-centre distance)."""
+    n = q.one.nt
+    tail = float(np.hypot(*(X[n] - X[0])))
+    head = float(np.hypot(*(head_centre(X[n:], q.one) - head_centre(X[:n], q.one))))
+    return np.array([tail, head])
+
+
+def pair_kernel_table(q: PairParams):
+    from .brinkmanlet import KernelTable
+
+    p = q.one
+    return KernelTable(p.flag.alpha, p.flag.delta, 1.25 * (p.flag.length + p.gap + 2 * p.hr + q.d))
+
+
+def pair_run_numpy(q: PairParams, table=None, steps=None):
+    """Forward Euler for both swimmers.  Returns (obs[n_obs, 2] = (tail, head) distances,
+    X_final, status)."""
+    fp = q.one.flag
+    table = table or pair_kernel_table(q)
+    steps = fp.steps if steps is None else steps
+    X = pair_initial_shape(q)
+    obs = []
+    for n in range(steps):
+        F = pair_forces(X, q, n * fp.dt)
+        v = sw.velocity(X, F, table, fp.mu)
+        if not np.all(np.isfinite(v)) or np.max(np.abs(v)) * fp.dt > fp.ds:
+            return np.array(obs).reshape(-1, 2), X, 1
+        X = X + fp.dt * v
+        if (n + 1) % fp.obs_every == 0:
+            obs.append(pair_distances(X, q))
+    return np.array(obs).reshape(-1, 2), X, 0
+
+
+def log_likelihood_two_sigma(obs_model, data, sigma_t, sigma_h):
+    """Sec. 4.2, two noise levels: Sigma diagonal with sigma_t^2 on the tail distances (odd
+    positions, 1-based) and sigma_h^2 on the head distances (even positions)."""
+    r = np.asarray(data, dtype=np.float64).reshape(-1, 2) - np.asarray(obs_model, dtype=np.float64).reshape(-1, 2)
+    m = r.shape[0]
+    return (-0.5 * m * (math.log(2 * math.pi * sigma_t ** 2) + math.log(2 * math.pi * sigma_h ** 2))
+            - 0.5 * float(np.sum(r[:, 0] ** 2)) / sigma_t ** 2 - 0.5 * float(np.sum(r[:, 1] ** 2)) / sigma_h ** 2)

@@ -86,3 +86,59 @@ def test_first_order_in_dt():
     # (1 - 1/8)/(1/2 - 1/8) = 7/3 and (1/2 - 1/8)/(1/4 - 1/8) = 3
     assert abs(e[0] / e[1] - 7.0 / 3.0) < 0.15
     assert abs(e[1] / e[2] - 3.0) < 0.2
+
+
+# two swimmers (Sec. 4.2)
+PAIR = sp.PairParams(replace(P, flag=replace(FLAG, n=12, delta_over_ds=1.5)), d=0.5)
+
+
+def test_pair_forces_are_the_exact_energy_gradient_and_separate():
+    X = sp.pair_initial_shape(PAIR) + 2e-3 * np.random.default_rng(4).standard_normal((PAIR.nt, 2))
+    F = sp.pair_forces(X, PAIR, 0.21)
+    G = np.zeros_like(X)
+    h = 1e-6
+    for i in range(X.shape[0]):
+        for c in range(2):
+            a = X.copy()
+            a[i, c] += h
+            b = X.copy()
+            b[i, c] -= h
+            G[i, c] = -(sp.pair_energy(a, PAIR, 0.21) - sp.pair_energy(b, PAIR, 0.21)) / (2 * h)
+    assert np.max(np.abs(F - G)) <= 1e-7 * np.max(np.abs(G))
+    # each swimmer's forces are its own: zero net force and torque per swimmer
+    n = PAIR.one.nt
+    for Fs, Xs in ((F[:n], X[:n]), (F[n:], X[n:])):
+        assert np.all(np.abs(Fs.sum(0)) < 1e-9 * np.max(np.abs(Fs)) * n)
+
+
+def test_pair_initial_distances_and_far_field_decay():
+    X = sp.pair_initial_shape(PAIR)
+    assert np.allclose(sp.pair_distances(X, PAIR), [PAIR.d, PAIR.d], atol=1e-15)
+    # each swimmer is force-free, so in a Brinkman fluid the other's influence is the
+    # potential-flow dipole far field, ~ d^-3: doubling the separation divides the deviation
+    # from a lone swimmer by about 8
+    one = replace(PAIR.one, flag=replace(PAIR.one.flag, alpha=2.0, steps=60, obs_every=60))
+    dev = []
+    for d in (12.0, 24.0):
+        far = sp.PairParams(one, d=d)
+        _, Xp, st = sp.pair_run_numpy(far)
+        _, X1, st1 = sp.run_numpy(one, table=sp.pair_kernel_table(far))
+        assert st == 0 and st1 == 0
+        n = one.nt
+        disp1 = X1 - sp.initial_shape(one)
+        dev.append(np.max(np.abs((Xp[:n] - sp.initial_shape(one)) - disp1)) / np.max(np.abs(disp1)))
+        # the second swimmer mirrors the first's motion (same start, displaced by d)
+        assert np.max(np.abs((Xp[n:] - [0.0, d]) - Xp[:n])) < 10 * dev[-1] * np.max(np.abs(disp1))
+    assert dev[1] < 1e-5
+    assert 6.5 < dev[0] / dev[1] < 9.5
+
+
+def test_two_sigma_likelihood_by_hand():
+    g = np.array([[1.0, 2.0], [1.5, 2.5]])
+    D = np.array([[1.1, 1.8], [1.4, 2.9]])
+    st, sh = 0.2, 0.5
+    want = (-2 * 0.5 * (math.log(2 * math.pi * 0.04) + math.log(2 * math.pi * 0.25))
+            - 0.5 * (0.1 ** 2 + 0.1 ** 2) / 0.04 - 0.5 * (0.2 ** 2 + 0.4 ** 2) / 0.25)
+    assert sp.log_likelihood_two_sigma(g, D, st, sh) == pytest.approx(want, rel=1e-14)
+    # equal noise levels reduce to the one-sigma likelihood
+    assert sp.log_likelihood_two_sigma(g, D, 0.3, 0.3) == pytest.approx(sw.log_likelihood(g, D, 0.3), rel=1e-14)
