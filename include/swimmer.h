@@ -77,10 +77,19 @@ typedef struct swimmer_config {
     int obs_kind;           /* SWIMMER_OBS_HEAD_POINT: proximal flagellum point (x, y);
                                SWIMMER_OBS_HEAD_VELOCITY: head-centre velocity (x, y), the
                                centre's displacement over each observation interval / its
-                               duration (n_head > 0) */
+                               duration (n_head > 0);
+                               SWIMMER_OBS_PAIR_DISTANCES: (distance between the tail tips,
+                               distance between the head centres) of two swimmers */
+    /* Two swimmers per sample (Sec. 4.2): the same swimmer twice, the second displaced by
+     * swimmer_distance along y; the fluid couples them (one pair sum over all points).
+     * Points per sample = n_swimmers (n + n_head) <= n_max. */
+    int n_swimmers;         /* 1 or 2 (2 needs n_head > 0) */
+    double swimmer_distance;  /* initial vertical separation d (length units) */
+    double sigma_ratio;     /* noise of the second observed component / the first (sigma_h /
+                               sigma_t for two swimmers); 0 means 1 */
 } swimmer_config;
 
-enum { SWIMMER_OBS_HEAD_POINT = 0, SWIMMER_OBS_HEAD_VELOCITY = 1 };
+enum { SWIMMER_OBS_HEAD_POINT = 0, SWIMMER_OBS_HEAD_VELOCITY = 1, SWIMMER_OBS_PAIR_DISTANCES = 2 };
 
 typedef struct swimmer_handle swimmer_handle;
 

@@ -18,7 +18,8 @@ class SwimmerConfigC(ctypes.Structure):
         ("eta", c_double), ("omega", c_double), ("steps", c_ll), ("obs_every", c_ll),
         ("precision", c_int), ("n_head", c_int), ("head_radius_over_ds", c_double),
         ("neck_gap_over_ds", c_double), ("k_head_tens", c_double), ("k_head_c", c_double),
-        ("k_neck_tens", c_double), ("k_neck_ang", c_double), ("obs_kind", c_int),
+        ("k_neck_tens", c_double), ("k_neck_ang", c_double), ("obs_kind", c_int), ("n_swimmers", c_int),
+        ("swimmer_distance", c_double), ("sigma_ratio", c_double),
     ]
 
 

@@ -17,7 +17,7 @@ FP64 = 0
 FP32C = 1
 
 
-OBS_HEAD_POINT, OBS_HEAD_VELOCITY = 0, 1
+OBS_HEAD_POINT, OBS_HEAD_VELOCITY, OBS_PAIR_DISTANCES = 0, 1, 2
 
 
 @dataclass
@@ -45,7 +45,11 @@ class SwimmerConfig:
     k_head_c: float = 0.8
     k_neck_tens: float = 500.0
     k_neck_ang: float = 1e4
-    obs_kind: int = 0  # OBS_HEAD_POINT or OBS_HEAD_VELOCITY
+    obs_kind: int = 0  # OBS_HEAD_POINT, OBS_HEAD_VELOCITY or OBS_PAIR_DISTANCES
+    # two swimmers per sample; noise ratio of the second observed component
+    n_swimmers: int = 1
+    swimmer_distance: float = 2.0
+    sigma_ratio: float = 0.0
 
     def to_c(self):
         return SwimmerConfigC(**{f.name: getattr(self, f.name) for f in fields(self)})

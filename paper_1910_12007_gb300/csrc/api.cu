@@ -120,8 +120,13 @@ static int check_config(const swimmer_config *c) {
     ARG_CHECK(c->head_radius_over_ds >= 0.0 && c->neck_gap_over_ds >= 0.0, "head sizes must be >= 0");
     ARG_CHECK(c->k_head_tens >= 0.0 && c->k_head_c >= 0.0 && c->k_neck_tens >= 0.0 && c->k_neck_ang >= 0.0,
               "head and neck stiffnesses must be >= 0");
-    ARG_CHECK(c->obs_kind == SWIMMER_OBS_HEAD_POINT || (c->obs_kind == SWIMMER_OBS_HEAD_VELOCITY && c->n_head > 0),
-              "obs_kind must be HEAD_POINT, or HEAD_VELOCITY with a head");
+    ARG_CHECK(c->n_swimmers == 1 || (c->n_swimmers == 2 && c->n_head > 0), "n_swimmers must be 1, or 2 with a head");
+    ARG_CHECK(c->n_swimmers == 1 || c->swimmer_distance > 0.0, "swimmer_distance must be > 0");
+    ARG_CHECK(c->n_max - c->n_swimmers * c->n_head >= 3 * c->n_swimmers, "n_max too small for the swimmers");
+    ARG_CHECK(c->sigma_ratio >= 0.0, "sigma_ratio must be >= 0");
+    ARG_CHECK(c->obs_kind == SWIMMER_OBS_HEAD_POINT || (c->obs_kind == SWIMMER_OBS_HEAD_VELOCITY && c->n_head > 0) ||
+                  (c->obs_kind == SWIMMER_OBS_PAIR_DISTANCES && c->n_swimmers == 2),
+              "obs_kind must be HEAD_POINT, HEAD_VELOCITY with a head, or PAIR_DISTANCES with two swimmers");
     return 0;
 }
 

@@ -52,6 +52,15 @@ __host__ __device__ inline double neck_gap_over_ds(const swimmer_config &c) {
 __host__ __device__ inline double reach_over_ds(const swimmer_config &c, int n_flag) {
     return (n_flag - 1) + (c.n_head > 0 ? neck_gap_over_ds(c) + 2.0 * head_radius_over_ds(c) : 0.0);
 }
+// flagellum points per swimmer when a sample does not give its own
+__host__ __device__ inline int default_flagellum_points(const swimmer_config &c) {
+    const int ns = c.n_swimmers == 2 ? 2 : 1;
+    return c.n_max / ns - c.n_head;
+}
+// the largest distance between two points of a sample (two swimmers add their separation)
+__host__ __device__ inline double sample_reach(const swimmer_config &c, int n_flag, double ds) {
+    return reach_over_ds(c, n_flag) * ds + (c.n_swimmers == 2 ? c.swimmer_distance : 0.0);
+}
 
 struct ProfileEvents;
 

@@ -48,6 +48,8 @@ struct FwdArgs {
     double mu, dt, kt, eta, omega;
     double hr_over_ds, gap_over_ds, k_head_tens, k_head_c, k_neck_tens, k_neck_ang;  // head model
     int obs_kind;
+    double swim_d;        // two swimmers: initial separation along y
+    double sigma_ratio;   // noise of the second observed component / the first
     long long steps, obs_every;
     const double *obs;
     double sigma;
@@ -298,9 +300,10 @@ __device__ __forceinline__ void pair_unit(const float4 *__restrict__ s4, const f
     }
 }
 
-// observations are head-centre velocities (head model), else the proximal point's position
+// observations computed by warp 0 after a step (head-centre velocities, two-swimmer
+// distances) rather than by the thread that updates the proximal point
 __device__ __forceinline__ bool vel_obs(const FwdArgs &a, int nh) {
-    return a.obs_kind == SWIMMER_OBS_HEAD_VELOCITY && nh > 0;
+    return (a.obs_kind == SWIMMER_OBS_HEAD_VELOCITY || a.obs_kind == SWIMMER_OBS_PAIR_DISTANCES) && nh > 0;
 }
 
 // Mean of the head points (FP64 sums over one warp, fixed order); all lanes of warp 0 call
@@ -324,9 +327,11 @@ __device__ __forceinline__ void head_centre(const double *sx, const double *sy, 
     cy /= nh;
 }
 
-// HEAD: the full sperm model (head points and neck); without it the head code compiles out
-template <bool F64, bool HEAD>
+// MODEL 0: the flagellum; 1: the full sperm model (head points and neck); 2: two sperm models
+// coupled by the fluid.  Code for models a launch does not run compiles out.
+template <bool F64, int MODEL>
 __global__ void __launch_bounds__(1024) forward_kernel(FwdArgs a) {
+    constexpr bool HEAD = MODEL >= 1, TWO = MODEL == 2;
     typedef typename Types<F64>::R R;
     typedef typename Types<F64>::R4 R4;
     extern __shared__ __align__(32) unsigned char smraw[];
@@ -363,7 +368,8 @@ __global__ void __launch_bounds__(1024) forward_kernel(FwdArgs a) {
         const int b = a.order[w];
         const SampleParams p = a.sp[b];
         const int nf = p.n, nh = HEAD ? p.nh : 0, h2 = nh >> 1;
-        const int n = nf + nh;  // flagellum points, then head points
+        const int nsw = nf + nh;            // points per swimmer: flagellum, then head
+        const int n = TWO ? 2 * nsw : nsw;  // all points of the sample
         const long long n_obs = a.steps / a.obs_every;
         if (p.status != SWIMMER_OK) {
             if (tid == 0) {
@@ -431,16 +437,19 @@ __global__ void __launch_bounds__(1024) forward_kernel(FwdArgs a) {
         const double hr = a.hr_over_ds * ds, gap = a.gap_over_ds * ds;
         const double dth = nh ? 2.0 * PI / nh : 0.0, dsh = hr * dth;
         for (int k = tid; k < n; k += T) {
+            const int sw = TWO && k >= nsw;  // second swimmer: displaced by d along y
+            const int kl = k - sw * nsw;
             double x0, y0;
-            if (k < nf) {
-                x0 = k * ds - xref;
+            if (kl < nf) {
+                x0 = kl * ds - xref;
                 y0 = 0.0;
             } else {
                 double sn, cs;
-                sincos((k - nf) * dth, &sn, &cs);
+                sincos((kl - nf) * dth, &sn, &cs);
                 x0 = L + gap + hr + hr * cs - xref;
                 y0 = hr * sn;
             }
+            if (sw) y0 += a.swim_d;
             if (F64) {
                 sx[k] = x0;
                 sy[k] = y0;
@@ -527,11 +536,13 @@ __global__ void __launch_bounds__(1024) forward_kernel(FwdArgs a) {
             //      (for the curvature at k), which saves a barrier.  Flagellum points
             //      k < nf form an open chain; head points a closed one (periodic stencils).
             for (int k = tid; k < n; k += T) {
-                const bool hd = HEAD && k >= nf;
-                const int m = k - nf;
-                const int next = hd ? nf + (m + 1 == nh ? 0 : m + 1) : (k + 1 < nf ? k + 1 : -1);
-                const int prev = hd ? nf + (m == 0 ? nh - 1 : m - 1) : k - 1;
-                const bool center = hd || (k >= 1 && k + 1 < nf);
+                const int base = (TWO && k >= nsw) ? nsw : 0;  // the point's swimmer
+                const int kl = k - base;
+                const bool hd = HEAD && kl >= nf;
+                const int m = kl - nf;
+                const int next = hd ? base + nf + (m + 1 == nh ? 0 : m + 1) : (kl + 1 < nf ? k + 1 : -1);
+                const int prev = hd ? base + nf + (m == 0 ? nh - 1 : m - 1) : k - 1;
+                const bool center = hd || (kl >= 1 && kl + 1 < nf);
                 R qx, qy, epx = 0, epy = 0, emx = 0, emy = 0, tk = 0;
                 if (F64) {
                     if (next >= 0) {
@@ -595,7 +606,7 @@ __global__ void __launch_bounds__(1024) forward_kernel(FwdArgs a) {
                     if (hd) {
                         zhat = (R)s_model[M_IHR];  // preferred head curvature 1/H_r
                     } else {
-                        R s = (R)k * r_ds;
+                        R s = (R)kl * r_ds;
                         R ph = r_eta * s - r_omega * tR;
                         R sn, cs;
                         if (F64) {
@@ -631,10 +642,12 @@ __global__ void __launch_bounds__(1024) forward_kernel(FwdArgs a) {
             //      bending stencils of the centres k-1, k, k+1, and for the head model the
             //      diametral and neck springs and the neck angle (Appendix)
             for (int k = tid; k < n; k += T) {
-                const bool hd = HEAD && k >= nf;
-                const int m = k - nf;
-                const int next = hd ? nf + (m + 1 == nh ? 0 : m + 1) : (k + 1 < nf ? k + 1 : -1);
-                const int prev = hd ? nf + (m == 0 ? nh - 1 : m - 1) : k - 1;
+                const int base = (TWO && k >= nsw) ? nsw : 0;  // the point's swimmer
+                const int kl = k - base;
+                const bool hd = HEAD && kl >= nf;
+                const int m = kl - nf;
+                const int next = hd ? base + nf + (m + 1 == nh ? 0 : m + 1) : (kl + 1 < nf ? k + 1 : -1);
+                const int prev = hd ? base + nf + (m == 0 ? nh - 1 : m - 1) : (kl >= 1 ? k - 1 : -1);
                 R fx = 0, fy = 0;
                 if (next >= 0) {
                     fx += tvx[k];
@@ -644,15 +657,15 @@ __global__ void __launch_bounds__(1024) forward_kernel(FwdArgs a) {
                     fx -= tvx[prev];
                     fy -= tvy[prev];
                 }
-                if (hd || k >= 2) {  // centre prev acts on k as its next neighbour
+                if (hd || kl >= 2) {  // centre prev acts on k as its next neighbour
                     fx -= bend[4 * n_max + prev];
                     fy -= bend[5 * n_max + prev];
                 }
-                if (hd || (k >= 1 && k + 1 < nf)) {
+                if (hd || (kl >= 1 && kl + 1 < nf)) {
                     fx -= bend[2 * n_max + k];
                     fy -= bend[3 * n_max + k];
                 }
-                if (hd || k + 2 < nf) {  // centre next acts on k as its previous neighbour
+                if (hd || kl + 2 < nf) {  // centre next acts on k as its previous neighbour
                     fx -= bend[0 * n_max + next];
                     fy -= bend[1 * n_max + next];
                 }
@@ -670,14 +683,15 @@ __global__ void __launch_bounds__(1024) forward_kernel(FwdArgs a) {
                                 j = nf - 1;
                                 kind = 3;
                             }
-                        } else if (k == nf - 1) {
+                        } else if (kl == nf - 1) {
                             j = nf + h2 - 1 + q;
                             kind = q == 1 ? 3 : 1;
-                        } else if (k == nf - 2 && q < 2) {
+                        } else if (kl == nf - 2 && q < 2) {
                             j = nf + h2 - 1 + 2 * q;
                             kind = 2;
                         }
                         if (j < 0) continue;
+                        j += base;
                         if (F64) {
                             const RestF64 &r = rest64[2 + kind];
                             double ex, ey, strain;
@@ -695,7 +709,7 @@ __global__ void __launch_bounds__(1024) forward_kernel(FwdArgs a) {
                         }
                     }
                     // neck angle E = K (z1 . z2)^2, z1 = H(pi) - X_{nf-1}, z2 = H(pi+dth) - H(pi-dth)
-                    const int ihp = nf + h2, iplus = nf + h2 + 1, iminus = nf + h2 - 1, iend = nf - 1;
+                    const int ihp = base + nf + h2, iplus = ihp + 1, iminus = ihp - 1, iend = base + nf - 1;
                     if (k == ihp || k == iplus || k == iminus || k == iend) {
                         R z1x, z1y, z2x, z2y;
                         if (F64) {
@@ -832,7 +846,7 @@ __global__ void __launch_bounds__(1024) forward_kernel(FwdArgs a) {
                     long long o = (step + 1) / a.obs_every - 1;
                     hxo += xref;
                     if (a.obs) {
-                        double rx = a.obs[2 * o] - hxo, ry = a.obs[2 * o + 1] - hyo;
+                        double rx = a.obs[2 * o] - hxo, ry = (a.obs[2 * o + 1] - hyo) / a.sigma_ratio;
                         J = fma(rx, rx, fma(ry, ry, J));
                     }
                     if (a.head_traj) {
@@ -847,22 +861,47 @@ __global__ void __launch_bounds__(1024) forward_kernel(FwdArgs a) {
                 break;
             }
             if (vel_obs(a, nh) && (step + 1) % a.obs_every == 0 && tid < 32) {
-                // head-centre velocity over the observation interval (Sec. 4.1)
-                double cx, cy;
-                head_centre<F64>(sx, sy, xh, xl, yh, yl, nf, nh, lane, cx, cy);
-                if (tid == 0) {
+                double ox, oy;
+                if (TWO && a.obs_kind == SWIMMER_OBS_PAIR_DISTANCES) {
+                    // distances between the tail tips and between the head centres (Sec. 4.2)
+                    double c0x, c0y, c1x, c1y;
+                    head_centre<F64>(sx, sy, xh, xl, yh, yl, nf, nh, lane, c0x, c0y);
+                    head_centre<F64>(sx, sy, xh, xl, yh, yl, nsw + nf, nh, lane, c1x, c1y);
+                    double tx, ty;
+                    if (F64) {
+                        tx = sx[nsw] - sx[0];
+                        ty = sy[nsw] - sy[0];
+                    } else {
+                        float hh, ll;
+                        df_sub(xh, xl, 0, nsw, hh, ll);
+                        tx = (double)hh + (double)ll;
+                        df_sub(yh, yl, 0, nsw, hh, ll);
+                        ty = (double)hh + (double)ll;
+                    }
+                    ox = sqrt(tx * tx + ty * ty);
+                    oy = sqrt((c1x - c0x) * (c1x - c0x) + (c1y - c0y) * (c1y - c0y));
+                } else {
+                    // head-centre velocity over the observation interval (Sec. 4.1)
+                    double cx, cy;
+                    head_centre<F64>(sx, sy, xh, xl, yh, yl, nf, nh, lane, cx, cy);
                     const double inv = 1.0 / ((double)a.obs_every * a.dt);
-                    const double vx = (cx - s_model[M_CX]) * inv, vy = (cy - s_model[M_CY]) * inv;
-                    s_model[M_CX] = cx;
-                    s_model[M_CY] = cy;
+                    ox = (cx - s_model[M_CX]) * inv;
+                    oy = (cy - s_model[M_CY]) * inv;
+                    __syncwarp();
+                    if (tid == 0) {
+                        s_model[M_CX] = cx;
+                        s_model[M_CY] = cy;
+                    }
+                }
+                if (tid == 0) {
                     const long long o = (step + 1) / a.obs_every - 1;
                     if (a.obs) {
-                        double rx = a.obs[2 * o] - vx, ry = a.obs[2 * o + 1] - vy;
+                        const double rx = a.obs[2 * o] - ox, ry = (a.obs[2 * o + 1] - oy) / a.sigma_ratio;
                         J = fma(rx, rx, fma(ry, ry, J));
                     }
                     if (a.head_traj) {
-                        a.head_traj[((size_t)b * n_obs + o) * 2] = vx;
-                        a.head_traj[((size_t)b * n_obs + o) * 2 + 1] = vy;
+                        a.head_traj[((size_t)b * n_obs + o) * 2] = ox;
+                        a.head_traj[((size_t)b * n_obs + o) * 2 + 1] = oy;
                     }
                 }
             }
@@ -872,13 +911,14 @@ __global__ void __launch_bounds__(1024) forward_kernel(FwdArgs a) {
             // mean speed: x-displacement of the flagellum's centroid (which starts at 0 in the
             // stored coordinates) or, with a head, of the head centre, over the run's duration;
             // one warp sums in a fixed order
+            // (the first swimmer's, with two)
             const int k0 = nh > 0 ? nf : 0;
             double cx = 0.0;
-            for (int k = k0 + lane; k < n; k += 32) cx += F64 ? sx[k] : (double)xh[k] + (double)xl[k];
+            for (int k = k0 + lane; k < nsw; k += 32) cx += F64 ? sx[k] : (double)xh[k] + (double)xl[k];
             for (int o = 16; o >= 1; o >>= 1) cx += __shfl_xor_sync(0xffffffffu, cx, o);
             if (tid == 0) {
                 const double c0 = nh > 0 ? L + (a.gap_over_ds + a.hr_over_ds) * ds - xref : 0.0;
-                a.speed[b] = status == SWIMMER_OK ? (cx / (n - k0) - c0) / (a.steps * a.dt) : nan("");
+                a.speed[b] = status == SWIMMER_OK ? (cx / (nsw - k0) - c0) / (a.steps * a.dt) : nan("");
             }
         }
         if (tid == 0) {
@@ -892,8 +932,13 @@ __global__ void __launch_bounds__(1024) forward_kernel(FwdArgs a) {
         if (head_thread) {
             a.status[b] = status;
             if (a.loglik) {
+                // Sigma = diag(sigma^2, (sigma_ratio sigma)^2) per observation (Sec. 3.1; two
+                // noise levels, Sec. 4.2): residuals of the second component are divided by
+                // sigma_ratio in J
                 double s2 = a.sigma * a.sigma;
-                a.loglik[b] = status == SWIMMER_OK ? -(double)n_obs * log(2.0 * PI * s2) - 0.5 * J / s2 : -INFINITY;
+                a.loglik[b] = status == SWIMMER_OK
+                                  ? -(double)n_obs * (log(2.0 * PI * s2) + log(a.sigma_ratio)) - 0.5 * J / s2
+                                  : -INFINITY;
             }
             if (status != SWIMMER_OK && a.head_traj) {
                 // observations after the divergence were never taken
@@ -909,9 +954,10 @@ __global__ void __launch_bounds__(1024) forward_kernel(FwdArgs a) {
 
 typedef void (*ForwardKernel)(FwdArgs);
 
-ForwardKernel forward_kernel_for(bool f64, bool head) {
-    return f64 ? (head ? forward_kernel<true, true> : forward_kernel<true, false>)
-               : (head ? forward_kernel<false, true> : forward_kernel<false, false>);
+ForwardKernel forward_kernel_for(bool f64, const swimmer_config &c) {
+    const int model = c.n_swimmers == 2 ? 2 : c.n_head > 0 ? 1 : 0;
+    if (f64) return model == 2 ? forward_kernel<true, 2> : model == 1 ? forward_kernel<true, 1> : forward_kernel<true, 0>;
+    return model == 2 ? forward_kernel<false, 2> : model == 1 ? forward_kernel<false, 1> : forward_kernel<false, 0>;
 }
 
 }  // namespace
@@ -933,7 +979,7 @@ int forward_slots(const swimmer_handle *h, int precision) {
     const int T = forward_min_threads(h, precision);
     const int P = handle_octaves(h) * (f64 ? F64_SUB : F32_SUB);
     size_t smem = f64 ? smem_bytes<true>(h->cfg.n_max, P, T) : smem_bytes<false>(h->cfg.n_max, P, T);
-    auto kern = forward_kernel_for(f64, h->cfg.n_head > 0);
+    auto kern = forward_kernel_for(f64, h->cfg);
     int per_sm = 0;
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
         cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared) !=
@@ -995,6 +1041,8 @@ int launch_forward(swimmer_handle *h, int B, const double *obs, double sigma, do
     a.k_neck_tens = h->cfg.k_neck_tens;
     a.k_neck_ang = h->cfg.k_neck_ang;
     a.obs_kind = h->cfg.obs_kind;
+    a.swim_d = h->cfg.swimmer_distance;
+    a.sigma_ratio = h->cfg.sigma_ratio > 0.0 ? h->cfg.sigma_ratio : 1.0;
     a.eta = h->cfg.eta;
     a.omega = h->cfg.omega;
     a.steps = h->cfg.steps;
@@ -1014,7 +1062,7 @@ int launch_forward(swimmer_handle *h, int B, const double *obs, double sigma, do
     const bool f64 = precision == SWIMMER_FP64;
     a.tab_panels = handle_octaves(h) * (f64 ? F64_SUB : F32_SUB);
     size_t smem = f64 ? smem_bytes<true>(a.n_max, a.tab_panels, T) : smem_bytes<false>(a.n_max, a.tab_panels, T);
-    auto kern = forward_kernel_for(f64, h->cfg.n_head > 0);
+    auto kern = forward_kernel_for(f64, h->cfg);
     CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
                                   cudaSharedmemCarveoutMaxShared));

@@ -237,27 +237,27 @@ __global__ void prepare_kernel(int B, const double *__restrict__ theta, const in
     int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= B) return;
     SampleParams p;
-    p.n = n_pts ? n_pts[b] : cfg.n_max - cfg.n_head;
+    p.n = n_pts ? n_pts[b] : default_flagellum_points(cfg);
     p.nh = cfg.n_head;
     p.alpha = theta[3 * b + 0];
     p.kc = pow(10.0, theta[3 * b + 1]);
     p.amp = theta[3 * b + 2];
     p.length = cfg.ds_fixed > 0.0 ? (p.n - 1) * cfg.ds_fixed : cfg.length;
     p.status = SWIMMER_OK;
-    if (p.n < 3 || p.n + p.nh > cfg.n_max) {
+    if (p.n < 3 || (cfg.n_swimmers == 2 ? 2 : 1) * (p.n + p.nh) > cfg.n_max) {
         p.n = 3;
         p.status = SWIMMER_BAD_SAMPLE;
     }
     p.ds = p.length / (p.n - 1);
     p.delta = cfg.delta_over_ds * p.ds;
-    double rho = R_MAX_OVER_L * reach_over_ds(cfg, p.n) / cfg.delta_over_ds;  // r_max/delta, as handle_octaves()
+    double rho = R_MAX_OVER_L * sample_reach(cfg, p.n, p.ds) / p.delta;  // r_max/delta, as handle_octaves()
     int n_oct = (int)floor(log2(1.0 + rho * rho)) + 1;
     if (n_oct > N_OCT_MAX) {
         n_oct = N_OCT_MAX;
         p.status = SWIMMER_BAD_SAMPLE;
     }
     p.n_oct = n_oct;
-    if (!(p.alpha >= 0.0) || p.alpha * R_MAX_OVER_L * reach_over_ds(cfg, p.n) * p.ds > X_MAX || !isfinite(p.kc) ||
+    if (!(p.alpha >= 0.0) || p.alpha * R_MAX_OVER_L * sample_reach(cfg, p.n, p.ds) > X_MAX || !isfinite(p.kc) ||
         !isfinite(p.amp) || !(p.kc > 0.0))
         p.status = SWIMMER_BAD_SAMPLE;
     sp[b] = p;
@@ -683,7 +683,10 @@ int gl_init() {
 }
 
 int handle_octaves(const swimmer_handle *h) {
-    double rho = R_MAX_OVER_L * reach_over_ds(h->cfg, h->cfg.n_max - h->cfg.n_head) / h->cfg.delta_over_ds;
+    // the sample with the most flagellum points and, for two swimmers, the smallest ds
+    const int nfm = default_flagellum_points(h->cfg);
+    const double ds = h->cfg.ds_fixed > 0.0 ? h->cfg.ds_fixed : h->cfg.length / (nfm - 1);
+    double rho = R_MAX_OVER_L * sample_reach(h->cfg, nfm, ds) / (h->cfg.delta_over_ds * ds);
     int n_oct = (int)floor(log2(1.0 + rho * rho)) + 1;
     return n_oct > N_OCT_MAX ? N_OCT_MAX : n_oct;
 }

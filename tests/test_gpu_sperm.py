@@ -126,3 +126,60 @@ def test_head_model_rejects_bad_configs():
             setattr(c, k, v)
         with pytest.raises(RuntimeError):
             g.swimmer_init(c)
+
+
+# two swimmers (Sec. 4.2): distances between the tail tips and between the head centres
+PAIR = sp.PairParams(replace(BASE, flag=replace(FLAG, n=12, delta_over_ds=0.045 * 11, steps=400, obs_every=40)),
+                     d=0.5)
+
+
+def _pair_cfg(q: sp.PairParams, b_max, precision, sigma_ratio=0.0):
+    c = _cfg(q.one, b_max, precision, observe=g.OBS_PAIR_DISTANCES)
+    c.n_max = q.nt
+    c.n_swimmers = 2
+    c.swimmer_distance = q.d
+    c.sigma_ratio = sigma_ratio
+    return c
+
+
+@pytest.fixture(scope="module")
+def pair_oracle():
+    out = []
+    for t in THETAS[:2]:
+        q = sp.PairParams(PAIR.one.with_theta(t), PAIR.d)
+        obs, X, st = sp.pair_run_numpy(q)
+        assert st == 0
+        out.append(obs)
+    return out
+
+
+@pytest.mark.parametrize("precision,tol", [(g.FP64, 1e-10), (g.FP32C, 1e-4)])
+def test_two_swimmer_distances_match_oracle(pair_oracle, precision, tol):
+    h = g.swimmer_init(_pair_cfg(PAIR, 2, precision))
+    traj, _, status = g.forward_batch(h, _theta(THETAS[:2]))
+    torch.cuda.synchronize()
+    assert np.all(status.cpu().numpy() == 0)
+    for b, obs in enumerate(pair_oracle):
+        # distances change by O(1e-2) from d: compare the changes
+        dg = traj[b].cpu().numpy() - PAIR.d
+        dr = obs - PAIR.d
+        err = np.max(np.abs(dg - dr)) / np.max(np.abs(dr))
+        assert err < tol, (b, err)
+    h.close()
+
+
+def test_two_sigma_log_likelihood(pair_oracle):
+    D = pair_oracle[0] + np.array([0.002, -0.004]) * synthetic_normals(pair_oracle[0].shape)
+    st, ratio = 0.003, 2.5
+    ref = [sp.log_likelihood_two_sigma(obs, D, st, ratio * st) for obs in pair_oracle]
+    h = g.swimmer_init(_pair_cfg(PAIR, 2, g.FP64, sigma_ratio=ratio))
+    ll, status = g.loglik_batch(h, _theta(THETAS[:2]), torch.tensor(D, device=DEV), st)
+    torch.cuda.synchronize()
+    assert np.allclose(ll.cpu().numpy(), ref, rtol=1e-9, atol=1e-6)
+    h.close()
+
+
+def synthetic_normals(shape):
+    import synthetic
+
+    return synthetic.normals(77, synthetic.NOISE, 0, int(np.prod(shape))).reshape(shape)
