@@ -211,13 +211,14 @@ def main():
     ap.add_argument("--profile-case", action="store_true",
                     help="run one forward batch of the workload (1024 samples, 200 steps) for ncu and exit")
     ap.add_argument("--workload", default="tmcmc",
-                    choices=["tmcmc", "uneven", "large", "surrogate", "shapes", "sperm", "sperm-tmcmc"],
+                    choices=["tmcmc", "uneven", "large", "surrogate", "shapes", "sperm", "sperm-tmcmc", "two-sperm"],
                     help="tmcmc (default): TMCMC stages, 1024 samples, N=128; uneven: 4096 samples with "
                          "N in {64,128,256,512} in one graph-captured persistent launch; large: 256 samples "
                          "x N=1024 x 4e4 steps; surrogate: delayed-acceptance vs plain TMCMC, 4096 samples/stage; "
                          "shapes: forward-kernel time per step vs samples per SM and threads per sample; sperm: "
                          "1024 full sperm models (flagellum 50 + head 24 points, Table Tab:param) x one beat; "
-                         "sperm-tmcmc: a whole TMCMC run on the full sperm model, head-centre velocities")
+                         "sperm-tmcmc: a whole TMCMC run on the full sperm model, head-centre velocities; "
+                         "two-sperm: 1024 pairs of sperm models 0.5 apart (148 points) x one beat, distances")
     args = ap.parse_args()
 
     from paper_1910_12007_gb300 import ranks
@@ -232,7 +233,7 @@ def main():
     import paper_1910_12007_gb300 as g
     import synthetic
 
-    if args.workload in ("uneven", "large", "sperm"):
+    if args.workload in ("uneven", "large", "sperm", "two-sperm"):
         return forward_workload(args, rank, world, local_rank)
     if args.workload == "surrogate":
         return surrogate_workload(args, rank, world, local_rank)
@@ -474,6 +475,20 @@ def forward_workload(args, rank, world, local_rank):
         lo, hi = PRIOR_LO, (10.0, 0.0, 0.2)
         desc = ("4096 samples, N uniform in {64,128,256,512} at fixed ds=1/255 (L=(N-1)ds), 1e4 steps, "
                 "dt=1e-4/512, one graph-captured persistent launch, longest first")
+    elif args.workload == "two-sperm":
+        # Sec. 4.2: two Table Tab:param swimmers 0.5 apart, coupled by the fluid; tail and
+        # head distances observed, two noise levels
+        B, steps = 1024, 40000
+        dt = 1e-4 / 8
+        cfg = g.SwimmerConfig(n_max=148, b_max=B, length=1.0, delta_over_ds=0.045 * 49, dt=dt, k_t=1e4,
+                              omega=4 * math.pi, steps=steps, obs_every=4000, precision=prec, n_head=24,
+                              k_head_tens=1e4, k_head_c=0.8, k_neck_tens=500.0, k_neck_ang=1e4,
+                              obs_kind=g.OBS_PAIR_DISTANCES, n_swimmers=2, swimmer_distance=0.5, sigma_ratio=2.0)
+        ns = None
+        lo, hi = (0.0, 0.6, 0.08), (5.0, 0.95, 0.12)
+        desc = ("1024 pairs of full sperm models (2 x (50 + 24) points) 0.5 apart, Table Tab:param stiffnesses, "
+                "alpha in [0,5], K_C in [4,9], one beat (4e4 steps, dt=1e-4/8), tail and head distances every 4000 "
+                "steps")
     elif args.workload == "sperm":
         # Table Tab:param: flagellum 50 points, head 24, epsilon 0.045, K_tens 1e4, K_C ~ 8,
         # K_H,tens 1e4, K_H,C 0.8, K_N,tens 500, K_N,ang 1e4, omega 4 pi, a ~ 0.1; the printed
