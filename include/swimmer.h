@@ -218,6 +218,9 @@ typedef struct tmcmc_state {
     int n_accept;          /* accepted proposals this stage */
     int n_exact_path;      /* forward-model runs the chains used (what one-step-at-a-time needs) */
     double *surr_loglik;   /* device [B] surrogate log-likelihoods (delayed acceptance) */
+    double log_evidence;   /* host: sum of log S_j over the stages run with this state, the
+                              estimate of log p(D | M) once q = 1 (Sec. 3.2, model evidence;
+                              start it at 0) */
 } tmcmc_state;
 
 /* One TMCMC stage: analyze (q_{j+1} by bisection on COV(w) = 1, w_bar, S_j, mu_j,

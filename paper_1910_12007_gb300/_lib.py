@@ -30,7 +30,7 @@ class TmcmcStateC(ctypes.Structure):
         ("prior_lo", c_double * 3), ("prior_hi", c_double * 3), ("q", c_double), ("stage", c_int),
         ("log_s", c_double), ("mu", c_double * 3), ("sigma_prop", c_double * 9),
         ("unique", c_int), ("max_chain", c_int), ("n_exact", c_int), ("n_screened", c_int),
-        ("n_accept", c_int), ("n_exact_path", c_int), ("surr_loglik", c_void_p),
+        ("n_accept", c_int), ("n_exact_path", c_int), ("surr_loglik", c_void_p), ("log_evidence", c_double),
     ]
 
 

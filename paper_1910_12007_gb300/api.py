@@ -206,7 +206,7 @@ class TmcmcState:
 
     def summary(self):
         c = self.c
-        return dict(stage=c.stage, q=c.q, log_s=c.log_s, mu=list(c.mu), unique=c.unique,
+        return dict(stage=c.stage, q=c.q, log_s=c.log_s, log_evidence=c.log_evidence, mu=list(c.mu), unique=c.unique,
                     max_chain=c.max_chain, n_exact=c.n_exact, n_screened=c.n_screened, n_accept=c.n_accept,
                     n_exact_path=c.n_exact_path)
 

@@ -706,6 +706,7 @@ extern "C" int tmcmc_stage_shard(swimmer_handle *h, tmcmc_state *st, const doubl
     st->q = qn;
     st->stage += 1;
     st->log_s = hs[S_LOGS];
+    st->log_evidence += hs[S_LOGS];
     for (int a = 0; a < 3; ++a) st->mu[a] = hs[S_MU + a];
     for (int e = 0; e < 9; ++e) st->sigma_prop[e] = hs[S_SIG + e];
     st->unique = U;

@@ -112,6 +112,8 @@ def test_tmcmc_fp64_matches_oracle_sample_by_sample():
                                    randoms=lambda j: synthetic.stage_randoms(seed, j, B, 3))
     assert [s["q"] for s in log_g] == pytest.approx(log_o.q, rel=1e-9)
     assert [s["unique"] for s in log_g] == log_o.unique
+    # model evidence log p(D|M) = sum_j log S_j (Sec. 3.2), accumulated in the state
+    assert log_g[-1]["log_evidence"] == pytest.approx(sum(log_o.log_s), rel=1e-9)
     assert np.allclose(th_g, th_o, rtol=1e-8, atol=1e-10)
     assert np.allclose(ll_g, ll_o, rtol=1e-8, atol=1e-8)
 

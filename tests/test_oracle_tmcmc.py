@@ -40,6 +40,51 @@ def test_gaussian_toy_posterior():
     assert np.all(np.abs(s / sd - 1) < 0.1)
 
 
+def _box_gauss_log_evidence(mean, sd, lo, hi):
+    # log of (1/V) * prod_i int_lo^hi exp(-((x - mean_i)/sd_i)^2 / 2) dx, exactly (erf)
+    from scipy.special import erf
+
+    mean, sd, lo, hi = (np.asarray(v, dtype=np.float64) for v in (mean, sd, lo, hi))
+    one_d = sd * np.sqrt(np.pi / 2) * (erf((hi - mean) / (sd * np.sqrt(2))) - erf((lo - mean) / (sd * np.sqrt(2))))
+    return float(np.sum(np.log(one_d)) - np.sum(np.log(hi - lo)))
+
+
+def test_model_evidence_single_stage_is_the_prior_mean_of_the_likelihood():
+    # a likelihood wide enough that q goes from 0 to 1 in one stage: log p(D|M) = log S_0, the
+    # Monte-Carlo mean of the likelihood over prior draws (Sec. 3.2), against the exact integral
+    mean = np.array([0.5, -1.0, 2.0])
+    sd = np.array([6.0, 8.0, 10.0])
+    lo, hi = np.full(3, -8.0), np.full(3, 8.0)
+    B = 4096
+    th0 = synthetic.prior_samples(3, lo, hi, B)
+    _, _, log = tm.run(th0, _toy(mean, sd), lo, hi, 3, randoms=lambda j: synthetic.stage_randoms(3, j, B, 3))
+    assert log.q == [1.0]
+    exact = _box_gauss_log_evidence(mean, sd, lo, hi)
+    ll = _toy(mean, sd)(th0)
+    assert log.log_s[0] == pytest.approx(math.log(np.mean(np.exp(ll))), rel=1e-12)
+    # Monte-Carlo error of the mean of B draws of a likelihood with COV < 1: below 1.6 %
+    assert abs(log.log_s[0] - exact) < 0.03, (log.log_s[0], exact)
+
+
+def test_model_evidence_of_the_gaussian_toy():
+    # sum_j log S_j over a multi-stage run against the closed form.  Short Metropolis chains
+    # leave each stage's samples slightly off f_j, so the estimate sits a little low (about
+    # -0.3 in log here, a 25 % underestimate); a wrong weight or a dropped l_max term would be
+    # off by orders of magnitude
+    mean = np.array([0.7, -1.2, 2.0])
+    sd = np.array([0.3, 0.5, 0.2])
+    lo, hi = np.full(3, -8.0), np.full(3, 8.0)
+    exact = _box_gauss_log_evidence(mean, sd, lo, hi)
+    est = []
+    for seed in range(30, 38):
+        B = 2048
+        th0 = synthetic.prior_samples(seed, lo, hi, B)
+        _, _, log = tm.run(th0, _toy(mean, sd), lo, hi, seed, randoms=lambda j: synthetic.stage_randoms(seed, j, B, 3))
+        assert len(log.q) > 2
+        est.append(sum(log.log_s))
+    assert abs(np.mean(est) - exact) < 0.6, (est, exact)
+
+
 def test_delayed_acceptance_keeps_target():
     mean = np.array([0.3, 0.1])
     sd = np.array([0.2, 0.4])
