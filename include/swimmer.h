@@ -87,6 +87,11 @@ typedef struct swimmer_config {
     double swimmer_distance;  /* initial vertical separation d (length units) */
     double sigma_ratio;     /* noise of the second observed component / the first (sigma_h /
                                sigma_t for two swimmers); 0 means 1 */
+    /* Unknowns per sample: 3 = theta (alpha, log10 K_C, a); 4 adds the noise level as an
+     * unknown (Sec. 3.1, sigma/beta inferred): a sample's sigma is theta[3] times the sigma
+     * passed to the likelihood calls.  theta rows have n_params entries in every call of
+     * the handle.  0 means 3. */
+    int n_params;
 } swimmer_config;
 
 enum { SWIMMER_OBS_HEAD_POINT = 0, SWIMMER_OBS_HEAD_VELOCITY = 1, SWIMMER_OBS_PAIR_DISTANCES = 2 };
@@ -197,20 +202,20 @@ int loglik_batch(swimmer_handle *h, int B, const double *theta, const int *n_pts
  * ------------------------------------------------------------------------------------- */
 typedef struct tmcmc_state {
     int B;                 /* samples per stage (<= b_max) */
-    double *theta;         /* device [B][3] current samples (updated in place) */
+    double *theta;         /* device [B][P] current samples (updated in place), P = n_params */
     double *loglik;        /* device [B] their log-likelihoods (updated in place) */
     int *status;           /* device [B] */
     const int *n_pts;      /* ignored: every TMCMC sample uses n_max points */
     const double *obs;     /* device [n_obs][2] observations D */
-    double sigma;          /* noise standard deviation */
-    double prior_lo[3];    /* host: box-uniform prior bounds */
-    double prior_hi[3];
+    double sigma;          /* noise standard deviation (the scale beta when n_params = 4) */
+    double prior_lo[4];    /* host: box-uniform prior bounds (first P used) */
+    double prior_hi[4];
     double q;              /* host: annealing exponent q_j of the current samples */
     int stage;             /* host: stage index j */
     /* host outputs of the last stage */
     double log_s;          /* log S_j (evidence factor) */
-    double mu[3];          /* weighted sample mean mu_j */
-    double sigma_prop[9];  /* scaled covariance b^2 Sigma_j (row-major) */
+    double mu[4];          /* weighted sample mean mu_j (first P) */
+    double sigma_prop[16]; /* scaled covariance b^2 Sigma_j (P x P, row-major, row stride 4) */
     int unique;            /* number of distinct resampled samples (chains) */
     int max_chain;         /* longest chain */
     int n_exact;           /* forward-model runs executed this stage (pre-fetched runs included) */
@@ -260,10 +265,11 @@ int tmcmc_stage_shard(swimmer_handle *h, tmcmc_state *st, const double *uniforms
 int tmcmc_tree_template(int M, double p_accept, int depth_cap, int *nodes, int *count);
 
 /* Stage pieces, exposed for testing (Algorithm 1 'Analyze' and 'Resample'):
- * tmcmc_analyze: from loglik[B] (device), theta[B][3] (device) and q (host) compute on the
- *   device: out_w[B] = exp(dq (l - l_max)) (0 for -inf), and stats[32] (device FP64) =
- *   {dq, q_next, log_S, l_max, mu[3], Sigma[9], L[9] (lower Cholesky factor of Sigma),
- *   status (0 ok, 1 every log-likelihood is -inf, 2 Sigma not positive definite), ...}.
+ * tmcmc_analyze: from loglik[B] (device), theta[B][P] (device, P = n_params) and q (host)
+ *   compute on the device: out_w[B] = exp(dq (l - l_max)) (0 for -inf), and stats[64]
+ *   (device FP64) = {dq, q_next, log_S, l_max, mu[4], Sigma[4][4], L[4][4] (lower Cholesky
+ *   factor of Sigma; the first P rows and columns used), status (0 ok, 1 every
+ *   log-likelihood is -inf, 2 Sigma not positive definite), ...}.
  * tmcmc_resample: idx[B] (device int) = min{i : C_i > floor(u_k C_B)}, C = inclusive
  *   prefix of floor(w_i 2^40); also counts[B] (device int).  Integer results are exact. */
 int tmcmc_analyze(swimmer_handle *h, int B, const double *theta, const double *loglik, double q,

@@ -304,8 +304,10 @@ def _loglik_chunk(args):
     obs, _, _, st = run_c_batch(ps, threads=1)
     out = np.full(len(ps), -np.inf)
     for b in range(len(ps)):
-        if st[b] == 0:
-            out[b] = log_likelihood(obs[b], D, sigma)
+        # a fourth column is the sample's noise level in units of sigma (sigma/beta inferred)
+        sg = sigma * thetas[b][3] if len(thetas[b]) > 3 else sigma
+        if st[b] == 0 and sg > 0:
+            out[b] = log_likelihood(obs[b], D, sg)
     return out
 
 

@@ -19,7 +19,7 @@ class SwimmerConfigC(ctypes.Structure):
         ("precision", c_int), ("n_head", c_int), ("head_radius_over_ds", c_double),
         ("neck_gap_over_ds", c_double), ("k_head_tens", c_double), ("k_head_c", c_double),
         ("k_neck_tens", c_double), ("k_neck_ang", c_double), ("obs_kind", c_int), ("n_swimmers", c_int),
-        ("swimmer_distance", c_double), ("sigma_ratio", c_double),
+        ("swimmer_distance", c_double), ("sigma_ratio", c_double), ("n_params", c_int),
     ]
 
 
@@ -27,8 +27,8 @@ class TmcmcStateC(ctypes.Structure):
     _fields_ = [
         ("B", c_int), ("theta", c_void_p), ("loglik", c_void_p), ("status", c_void_p),
         ("n_pts", c_void_p), ("obs", c_void_p), ("sigma", c_double),
-        ("prior_lo", c_double * 3), ("prior_hi", c_double * 3), ("q", c_double), ("stage", c_int),
-        ("log_s", c_double), ("mu", c_double * 3), ("sigma_prop", c_double * 9),
+        ("prior_lo", c_double * 4), ("prior_hi", c_double * 4), ("q", c_double), ("stage", c_int),
+        ("log_s", c_double), ("mu", c_double * 4), ("sigma_prop", c_double * 16),
         ("unique", c_int), ("max_chain", c_int), ("n_exact", c_int), ("n_screened", c_int),
         ("n_accept", c_int), ("n_exact_path", c_int), ("surr_loglik", c_void_p), ("log_evidence", c_double),
     ]

@@ -50,6 +50,8 @@ class SwimmerConfig:
     n_swimmers: int = 1
     swimmer_distance: float = 2.0
     sigma_ratio: float = 0.0
+    # unknowns per sample: 3, or 4 with the noise level (sigma = theta[3] * sigma)
+    n_params: int = 3
 
     def to_c(self):
         return SwimmerConfigC(**{f.name: getattr(self, f.name) for f in fields(self)})
@@ -159,7 +161,7 @@ def tmcmc_analyze(h: Handle, theta, loglik, q, stream=None):
     _dev(loglik, torch.float64)
     B = loglik.numel()
     w = torch.empty(B, dtype=torch.float64, device=loglik.device)
-    stats = torch.zeros(32, dtype=torch.float64, device=loglik.device)
+    stats = torch.zeros(64, dtype=torch.float64, device=loglik.device)
     check(lib().tmcmc_analyze(h.ptr, B, _ptr(theta), _ptr(loglik), float(q), _ptr(w), _ptr(stats), _stream(stream)))
     return w, stats
 
@@ -192,7 +194,8 @@ class TmcmcState:
         c.n_pts = None
         c.obs = obs.data_ptr()
         c.sigma = float(sigma)
-        for a in range(3):
+        self.P = theta.shape[1]
+        for a in range(self.P):
             c.prior_lo[a] = float(prior_lo[a])
             c.prior_hi[a] = float(prior_hi[a])
         c.q = 0.0
@@ -206,7 +209,8 @@ class TmcmcState:
 
     def summary(self):
         c = self.c
-        return dict(stage=c.stage, q=c.q, log_s=c.log_s, log_evidence=c.log_evidence, mu=list(c.mu), unique=c.unique,
+        return dict(stage=c.stage, q=c.q, log_s=c.log_s, log_evidence=c.log_evidence, mu=list(c.mu)[:self.P],
+                    unique=c.unique,
                     max_chain=c.max_chain, n_exact=c.n_exact, n_screened=c.n_screened, n_accept=c.n_accept,
                     n_exact_path=c.n_exact_path)
 

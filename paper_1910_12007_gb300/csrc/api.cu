@@ -124,6 +124,7 @@ static int check_config(const swimmer_config *c) {
     ARG_CHECK(c->n_swimmers == 1 || c->swimmer_distance > 0.0, "swimmer_distance must be > 0");
     ARG_CHECK(c->n_max - c->n_swimmers * c->n_head >= 3 * c->n_swimmers, "n_max too small for the swimmers");
     ARG_CHECK(c->sigma_ratio >= 0.0, "sigma_ratio must be >= 0");
+    ARG_CHECK(c->n_params == 0 || c->n_params == 3 || c->n_params == 4, "n_params must be 0, 3 or 4");
     ARG_CHECK(c->obs_kind == SWIMMER_OBS_HEAD_POINT || (c->obs_kind == SWIMMER_OBS_HEAD_VELOCITY && c->n_head > 0) ||
                   (c->obs_kind == SWIMMER_OBS_PAIR_DISTANCES && c->n_swimmers == 2),
               "obs_kind must be HEAD_POINT, HEAD_VELOCITY with a head, or PAIR_DISTANCES with two swimmers");
@@ -169,13 +170,13 @@ extern "C" int swimmer_init(const swimmer_config *cfg, swimmer_handle **out) {
     ALLOC(h->chain_off, B);
     ALLOC(h->chain_len, B);
     ALLOC(h->aux, B + 64);
-    ALLOC(h->cur_theta, 3 * B);
+    ALLOC(h->cur_theta, P_MAX * B);
     ALLOC(h->cur_ll, B);
     ALLOC(h->cur_sl, B);
-    ALLOC(h->prop_theta, 3 * B);
+    ALLOC(h->prop_theta, P_MAX * B);
     ALLOC(h->prop_ll, B);
     ALLOC(h->prop_sl, B);
-    ALLOC(h->out_theta, 3 * B);
+    ALLOC(h->out_theta, P_MAX * B);
     ALLOC(h->out_ll, B);
     ALLOC(h->out_sl, B);
     ALLOC(h->prop_status, B);
@@ -298,22 +299,24 @@ extern "C" int swimmer_autotune(swimmer_handle *h, int steps, const double *thet
     const int bmax = h->cfg.b_max;
     double *theta = nullptr;
     int *status = nullptr;
-    CUDA_TRY(cudaMalloc((void **)&theta, sizeof(double) * 3 * bmax));
+    const int np = n_params(h->cfg);
+    CUDA_TRY(cudaMalloc((void **)&theta, sizeof(double) * np * bmax));
     CUDA_TRY(cudaMalloc((void **)&status, sizeof(int) * bmax));
     if (theta_in) {
         // the caller's representative samples, repeated to b_max rows
         for (int off = 0; off < bmax; off += n_theta) {
             const int rows = std::min(n_theta, bmax - off);
-            CUDA_TRY(cudaMemcpy(theta + 3 * off, theta_in, sizeof(double) * 3 * rows, cudaMemcpyDeviceToDevice));
+            CUDA_TRY(cudaMemcpy(theta + np * off, theta_in, sizeof(double) * np * rows, cudaMemcpyDeviceToDevice));
         }
     } else {
-        double *ht = (double *)malloc(sizeof(double) * 3 * bmax);
+        double *ht = (double *)malloc(sizeof(double) * np * bmax);
         for (int b = 0; b < bmax; ++b) {
-            ht[3 * b] = 1.0 + 0.001 * (b % 17);
-            ht[3 * b + 1] = 0.0;
-            ht[3 * b + 2] = 0.1;
+            ht[np * b] = 1.0 + 0.001 * (b % 17);
+            ht[np * b + 1] = 0.0;
+            ht[np * b + 2] = 0.1;
+            if (np == 4) ht[np * b + 3] = 1.0;
         }
-        cudaMemcpy(theta, ht, sizeof(double) * 3 * bmax, cudaMemcpyHostToDevice);
+        cudaMemcpy(theta, ht, sizeof(double) * np * bmax, cudaMemcpyHostToDevice);
         free(ht);
     }
     const long long saved_steps = h->cfg.steps, saved_obs = h->cfg.obs_every;

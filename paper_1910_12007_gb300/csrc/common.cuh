@@ -38,6 +38,7 @@ constexpr double X_MAX = 600.0;        // largest alpha * r the Bessel evaluatio
 struct SampleParams {
     double alpha, kc, amp, length, ds, delta;
     int n, n_oct, status, nh;  // flagellum points, table octaves, status, head points
+    double sig;                // noise scale of the sample (theta[3] with 4 unknowns, else 1)
 };
 
 // head model geometry in units of ds (defaults: head points spaced like the flagellum's, a
@@ -52,6 +53,10 @@ __host__ __device__ inline double neck_gap_over_ds(const swimmer_config &c) {
 __host__ __device__ inline double reach_over_ds(const swimmer_config &c, int n_flag) {
     return (n_flag - 1) + (c.n_head > 0 ? neck_gap_over_ds(c) + 2.0 * head_radius_over_ds(c) : 0.0);
 }
+// unknowns per sample (rows of theta)
+__host__ __device__ inline int n_params(const swimmer_config &c) { return c.n_params == 4 ? 4 : 3; }
+constexpr int P_MAX = 4;
+
 // flagellum points per swimmer when a sample does not give its own
 __host__ __device__ inline int default_flagellum_points(const swimmer_config &c) {
     const int ns = c.n_swimmers == 2 ? 2 : 1;

@@ -935,7 +935,8 @@ __global__ void __launch_bounds__(1024) forward_kernel(FwdArgs a) {
                 // Sigma = diag(sigma^2, (sigma_ratio sigma)^2) per observation (Sec. 3.1; two
                 // noise levels, Sec. 4.2): residuals of the second component are divided by
                 // sigma_ratio in J
-                double s2 = a.sigma * a.sigma;
+                const double sg = a.sigma * p.sig;  // the sample's noise level
+                double s2 = sg * sg;
                 a.loglik[b] = status == SWIMMER_OK
                                   ? -(double)n_obs * (log(2.0 * PI * s2) + log(a.sigma_ratio)) - 0.5 * J / s2
                                   : -INFINITY;

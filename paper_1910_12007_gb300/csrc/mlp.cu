@@ -254,12 +254,12 @@ extern "C" int mlp_adam(float *params, const float *grad, float *m, float *v, in
 // ---------------------------------------------------------------------------------
 namespace {
 
-__global__ void surr_input_kernel(int B, const double *__restrict__ theta, float *__restrict__ x, double lo0,
+__global__ void surr_input_kernel(int B, int np, const double *__restrict__ theta, float *__restrict__ x, double lo0,
                                   double lo1, double lo2, double lo3, double lo4, double hi0, double hi1, double hi2,
                                   double hi3, double hi4, double log10_kt, double omega) {
     int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= B) return;
-    double v[5] = {theta[3 * b], theta[3 * b + 1], theta[3 * b + 2], log10_kt, omega};
+    double v[5] = {theta[np * b], theta[np * b + 1], theta[np * b + 2], log10_kt, omega};
     double lo[5] = {lo0, lo1, lo2, lo3, lo4}, hi[5] = {hi0, hi1, hi2, hi3, hi4};
     for (int k = 0; k < 5; ++k) {
         double span = hi[k] - lo[k];
@@ -267,12 +267,14 @@ __global__ void surr_input_kernel(int B, const double *__restrict__ theta, float
     }
 }
 
-__global__ void surr_loglik_kernel(int B, const double *__restrict__ theta, const float *__restrict__ y,
+__global__ void surr_loglik_kernel(int B, int np, const double *__restrict__ theta, const float *__restrict__ y,
                                    const double *__restrict__ norm, const double *__restrict__ obs, int stride,
                                    long long n_obs, double sigma, double *__restrict__ ll) {
     int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= B) return;
-    if (isnan(theta[3 * b])) {
+    // the sample's noise level: theta[3] times sigma with 4 unknowns
+    const double sg = np == 4 ? sigma * theta[np * b + 3] : sigma;
+    if (isnan(theta[np * b]) || !(sg > 0.0)) {
         ll[b] = -INFINITY;
         return;
     }
@@ -285,7 +287,7 @@ __global__ void surr_loglik_kernel(int B, const double *__restrict__ theta, cons
         J = fma(rx, rx, fma(ry, ry, J));
     }
     J *= (double)n_obs / (double)(OUT / 2);
-    double s2 = sigma * sigma;
+    double s2 = sg * sg;
     ll[b] = -(double)n_obs * log(2.0 * 3.14159265358979323846 * s2) - 0.5 * J / s2;
 }
 
@@ -294,13 +296,14 @@ __global__ void surr_loglik_kernel(int B, const double *__restrict__ theta, cons
 int run_surrogate_loglik(swimmer_handle *h, int B, const double *theta, const double *obs, double sigma,
                          double *loglik, cudaStream_t s) {
     const double *lo = h->surr_in_lo, *hi = h->surr_in_hi;
-    surr_input_kernel<<<(B + 127) / 128, 128, 0, s>>>(B, theta, h->surr_x, lo[0], lo[1], lo[2], lo[3], lo[4], hi[0],
+    const int np = n_params(h->cfg);
+    surr_input_kernel<<<(B + 127) / 128, 128, 0, s>>>(B, np, theta, h->surr_x, lo[0], lo[1], lo[2], lo[3], lo[4], hi[0],
                                                      hi[1], hi[2], hi[3], hi[4], h->surr_log10_kt, h->surr_omega);
     CUDA_TRY(cudaGetLastError());
     Ws w = carve(h->surr_ws, B);
     int rc = forward_all(s, B, h->surr_params, h->surr_x, h->surr_y, w);
     if (rc) return rc;
-    surr_loglik_kernel<<<(B + 127) / 128, 128, 0, s>>>(B, theta, h->surr_y, h->surr_norm, obs, h->surr_obs_stride,
+    surr_loglik_kernel<<<(B + 127) / 128, 128, 0, s>>>(B, np, theta, h->surr_y, h->surr_norm, obs, h->surr_obs_stride,
                                                        h->cfg.steps / h->cfg.obs_every, sigma, loglik);
     CUDA_TRY(cudaGetLastError());
     return 0;

@@ -239,9 +239,11 @@ __global__ void prepare_kernel(int B, const double *__restrict__ theta, const in
     SampleParams p;
     p.n = n_pts ? n_pts[b] : default_flagellum_points(cfg);
     p.nh = cfg.n_head;
-    p.alpha = theta[3 * b + 0];
-    p.kc = pow(10.0, theta[3 * b + 1]);
-    p.amp = theta[3 * b + 2];
+    const int np = n_params(cfg);
+    p.alpha = theta[np * b + 0];
+    p.kc = pow(10.0, theta[np * b + 1]);
+    p.amp = theta[np * b + 2];
+    p.sig = np == 4 ? theta[np * b + 3] : 1.0;
     p.length = cfg.ds_fixed > 0.0 ? (p.n - 1) * cfg.ds_fixed : cfg.length;
     p.status = SWIMMER_OK;
     if (p.n < 3 || (cfg.n_swimmers == 2 ? 2 : 1) * (p.n + p.nh) > cfg.n_max) {
@@ -257,6 +259,7 @@ __global__ void prepare_kernel(int B, const double *__restrict__ theta, const in
         p.status = SWIMMER_BAD_SAMPLE;
     }
     p.n_oct = n_oct;
+    if (!(p.sig > 0.0) || !isfinite(p.sig)) p.status = SWIMMER_BAD_SAMPLE;
     if (!(p.alpha >= 0.0) || p.alpha * R_MAX_OVER_L * sample_reach(cfg, p.n, p.ds) > X_MAX || !isfinite(p.kc) ||
         !isfinite(p.amp) || !(p.kc > 0.0))
         p.status = SWIMMER_BAD_SAMPLE;
@@ -509,6 +512,7 @@ __global__ void set_sample_kernel(SampleParams *sp, double alpha, double delta, 
     p.length = r_max / R_MAX_OVER_L;
     p.n = 3;
     p.nh = 0;
+    p.sig = 1.0;
     p.ds = p.length / 2;
     p.delta = delta;
     double rho = r_max / delta;

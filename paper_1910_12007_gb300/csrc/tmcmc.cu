@@ -37,8 +37,10 @@ constexpr double COV_TARGET = 1.0;
 constexpr double FIXED_SCALE = 1099511627776.0;  // 2^40
 
 // stats layout
-enum { S_DQ = 0, S_QN, S_LOGS, S_LMAX, S_MU, S_SIG = S_MU + 3, S_L = S_SIG + 9, S_STATUS = S_L + 9,
-       S_U, S_MAXLEN, S_COUNT };
+// (P <= P_MAX unknowns: mean [P_MAX], covariance and its Cholesky factor [P_MAX][P_MAX], row-major
+// with row stride P_MAX)
+enum { S_DQ = 0, S_QN, S_LOGS, S_LMAX, S_MU, S_SIG = S_MU + P_MAX, S_L = S_SIG + P_MAX * P_MAX,
+       S_STATUS = S_L + P_MAX * P_MAX, S_U, S_MAXLEN, S_COUNT };
 
 // fixed-order block sum of one double per thread (T1 threads); result to all threads
 __device__ double block_sum(double v, double *red) {
@@ -92,7 +94,7 @@ __device__ double cov_of(int B, const double *__restrict__ ll, double lmax, doub
     return sqrt(var) / m;
 }
 
-__global__ void __launch_bounds__(T1) analyze_kernel(int B, const double *__restrict__ theta,
+__global__ void __launch_bounds__(T1) analyze_kernel(int B, int P, const double *__restrict__ theta,
                                                     const double *__restrict__ ll, double q,
                                                     double *__restrict__ w_out, double *__restrict__ st) {
     __shared__ double red[40];
@@ -129,36 +131,37 @@ __global__ void __launch_bounds__(T1) analyze_kernel(int B, const double *__rest
         sw += w;
     }
     const double W = block_sum(sw, red);
-    double mu[3];
-    for (int a = 0; a < 3; ++a) {
+    double mu[P_MAX] = {0, 0, 0, 0};
+    for (int a = 0; a < P; ++a) {
         double s = 0.0;
-        for (int k = tid; k < B; k += T1) s += (w_out[k] / W) * theta[3 * k + a];
+        for (int k = tid; k < B; k += T1) s += (w_out[k] / W) * theta[P * k + a];
         mu[a] = block_sum(s, red);
     }
-    double sig[6];
-    const int ia[6] = {0, 1, 2, 1, 2, 2}, ib[6] = {0, 0, 0, 1, 1, 2};
-    for (int e = 0; e < 6; ++e) {
-        double s = 0.0;
-        for (int k = tid; k < B; k += T1) {
-            double wb = w_out[k] / W;
-            s += wb * (theta[3 * k + ia[e]] - mu[ia[e]]) * (theta[3 * k + ib[e]] - mu[ib[e]]);
+    // lower triangle of the weighted covariance, b^2 scaled
+    double S[P_MAX][P_MAX];
+    for (int a = 0; a < P; ++a)
+        for (int c = 0; c <= a; ++c) {
+            double s = 0.0;
+            for (int k = tid; k < B; k += T1) {
+                double wb = w_out[k] / W;
+                s += wb * (theta[P * k + a] - mu[a]) * (theta[P * k + c] - mu[c]);
+            }
+            S[a][c] = S[c][a] = B_SCALE * B_SCALE * block_sum(s, red);
         }
-        sig[e] = B_SCALE * B_SCALE * block_sum(s, red);
-    }
     if (tid == 0) {
         st[S_DQ] = dq;
         st[S_QN] = (q + dq >= 1.0 - 1e-15) ? 1.0 : q + dq;
         st[S_LOGS] = dq * lmax + log(W / B);
         st[S_LMAX] = lmax;
-        for (int a = 0; a < 3; ++a) st[S_MU + a] = mu[a];
-        double S[3][3];
-        for (int e = 0; e < 6; ++e) S[ia[e]][ib[e]] = S[ib[e]][ia[e]] = sig[e];
-        for (int a = 0; a < 3; ++a)
-            for (int c = 0; c < 3; ++c) st[S_SIG + 3 * a + c] = S[a][c];
+        for (int a = 0; a < P_MAX; ++a) st[S_MU + a] = a < P ? mu[a] : 0.0;
+        for (int a = 0; a < P_MAX; ++a)
+            for (int c = 0; c < P_MAX; ++c) st[S_SIG + P_MAX * a + c] = a < P && c < P ? S[a][c] : 0.0;
         // Cholesky S = L L^T
-        double L[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+        double L[P_MAX][P_MAX];
+        for (int a = 0; a < P_MAX; ++a)
+            for (int c = 0; c < P_MAX; ++c) L[a][c] = 0.0;
         int ok = 1;
-        for (int a = 0; a < 3; ++a) {
+        for (int a = 0; a < P; ++a) {
             for (int c = 0; c <= a; ++c) {
                 double s = S[a][c];
                 for (int k = 0; k < c; ++k) s -= L[a][k] * L[c][k];
@@ -170,8 +173,8 @@ __global__ void __launch_bounds__(T1) analyze_kernel(int B, const double *__rest
                 }
             }
         }
-        for (int a = 0; a < 3; ++a)
-            for (int c = 0; c < 3; ++c) st[S_L + 3 * a + c] = L[a][c];
+        for (int a = 0; a < P_MAX; ++a)
+            for (int c = 0; c < P_MAX; ++c) st[S_L + P_MAX * a + c] = L[a][c];
         st[S_STATUS] = ok ? 0.0 : 2.0;
     }
 }
@@ -238,7 +241,7 @@ __global__ void __launch_bounds__(T1) resample_kernel(int B, const double *__res
 
 // chains: ids/offsets/lengths in ascending sample order, a longest-first processing order,
 // per-step alive counts (host-visible) and the chains' starting states
-__global__ void __launch_bounds__(T1) chains_kernel(int B, const int *__restrict__ counts,
+__global__ void __launch_bounds__(T1) chains_kernel(int B, int P, const int *__restrict__ counts,
                                                    const double *__restrict__ theta, const double *__restrict__ ll,
                                                    const double *__restrict__ sl, int *__restrict__ chain_off,
                                                    int *__restrict__ chain_len, int *__restrict__ order,
@@ -269,9 +272,7 @@ __global__ void __launch_bounds__(T1) chains_kernel(int B, const int *__restrict
         if (n > 0) {
             chain_off[cidx] = (int)off;
             chain_len[cidx] = n;
-            cur_theta[3 * cidx + 0] = theta[3 * k + 0];
-            cur_theta[3 * cidx + 1] = theta[3 * k + 1];
-            cur_theta[3 * cidx + 2] = theta[3 * k + 2];
+            for (int a = 0; a < P; ++a) cur_theta[P * cidx + a] = theta[P * k + a];
             cur_ll[cidx] = ll[k];
             cur_sl[cidx] = sl ? sl[k] : 0.0;
             atomicAdd(&hist[n], 1);
@@ -325,16 +326,22 @@ __global__ void __launch_bounds__(T1) chains_kernel(int B, const int *__restrict
 // ---------------------------------------------------------------------------------
 constexpr int TREE_DEPTH_MAX = 31;
 
-__device__ __forceinline__ void add_step(const double *L, const double *z, const double *base, double *out) {
-    out[0] = base[0] + L[0] * z[0] + L[1] * z[1] + L[2] * z[2];
-    out[1] = base[1] + L[3] * z[0] + L[4] * z[1] + L[5] * z[2];
-    out[2] = base[2] + L[6] * z[0] + L[7] * z[1] + L[8] * z[2];
+// proposal base + L z (L lower triangular, row stride P_MAX), summed left to right
+__device__ __forceinline__ void add_step(int P, const double *L, const double *z, const double *base, double *out) {
+    for (int a = 0; a < P; ++a) {
+        double v = base[a];
+        for (int c = 0; c < P; ++c) v += L[P_MAX * a + c] * z[c];
+        out[a] = v;
+    }
 }
 
 struct Box {
-    double lo[3], hi[3];
+    int P;
+    double lo[P_MAX], hi[P_MAX];
     __device__ bool in(const double *t) const {
-        return t[0] >= lo[0] && t[0] <= hi[0] && t[1] >= lo[1] && t[1] <= hi[1] && t[2] >= lo[2] && t[2] <= hi[2];
+        bool ok = true;
+        for (int a = 0; a < P; ++a) ok = ok && t[a] >= lo[a] && t[a] <= hi[a];
+        return ok;
     }
 };
 
@@ -410,26 +417,24 @@ __global__ void tree_propose_kernel(int A, int M, const int *__restrict__ live, 
     const int slot = idx / M, v = idx % M;
     const int c = live[slot];
     const int row = chain_off[c] + chain_pos[c];  // normals row of the chain's next step
+    const int P = box.P;
     int path[TREE_DEPTH_MAX + 1];
     const int depth = tree_path(tmpl, v, path);
     const double *L = st + S_L;
-    double base[3] = {cur_theta[3 * c], cur_theta[3 * c + 1], cur_theta[3 * c + 2]};
+    double base[P_MAX], cand[P_MAX];
+    for (int a = 0; a < P; ++a) base[a] = cur_theta[P * c + a];
     bool ok = chain_pos[c] + depth < chain_len[c];
-    double cand[3];
     for (int i = 0; i < depth && ok; ++i) {
-        add_step(L, normals + 3 * (row + i), base, cand);
+        add_step(P, L, normals + P * (row + i), base, cand);
         if (tmpl[path[i + 1]].y & 1) {  // the path accepts at depth i
             if (!box.in(cand)) ok = false;
-            base[0] = cand[0];
-            base[1] = cand[1];
-            base[2] = cand[2];
+            for (int a = 0; a < P; ++a) base[a] = cand[a];
         }
     }
-    add_step(L, normals + 3 * (row + depth), base, cand);
+    add_step(P, L, normals + P * (row + depth), base, cand);
     ok = ok && box.in(cand);
-    prop[3 * idx] = ok ? cand[0] : nan("");
-    prop[3 * idx + 1] = cand[1];
-    prop[3 * idx + 2] = cand[2];
+    prop[P * idx] = ok ? cand[0] : nan("");
+    for (int a = 1; a < P; ++a) prop[P * idx + a] = cand[a];
     if (ok) atomicAdd(counter, 1);
 }
 
@@ -437,14 +442,14 @@ __global__ void tree_propose_kernel(int A, int M, const int *__restrict__ live, 
 // surrogate against its base (the candidate of the deepest accepted decision above it, else
 // the chain's state).  A node is not run when its own candidate fails the screen or when its
 // path accepts a candidate that fails it (that path cannot happen).
-__global__ void tree_screen_kernel(int A, int M, const int *__restrict__ live, const int *__restrict__ chain_off,
+__global__ void tree_screen_kernel(int A, int M, int P, const int *__restrict__ live, const int *__restrict__ chain_off,
                                    const int *__restrict__ chain_pos, const double *__restrict__ cur_sl,
                                    const double *__restrict__ prop_sl, const double *__restrict__ st,
                                    const double *__restrict__ u1, const int4 *__restrict__ tmpl,
                                    double *__restrict__ prop, int *__restrict__ counter) {
     int idx = blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= A * M) return;
-    if (isnan(prop[3 * idx])) return;
+    if (isnan(prop[P * idx])) return;
     const int slot = idx / M, v = idx % M;
     const int c = live[slot];
     const int row = chain_off[c] + chain_pos[c];
@@ -461,12 +466,12 @@ __global__ void tree_screen_kernel(int A, int M, const int *__restrict__ live, c
         }
     }
     const bool pass = reach && log(u1[row + depth]) < qn * (prop_sl[idx] - bsl);
-    if (!pass) prop[3 * idx] = nan("");
+    if (!pass) prop[P * idx] = nan("");
     else atomicAdd(counter, 1);
 }
 
 // walk each live chain down the template along the decisions it actually takes
-__global__ void tree_resolve_kernel(int A, int M, int delayed, const int *__restrict__ live,
+__global__ void tree_resolve_kernel(int A, int M, int P, int delayed, const int *__restrict__ live,
                                     const int *__restrict__ chain_off, const int *__restrict__ chain_len,
                                     int *__restrict__ chain_pos, double *__restrict__ cur_theta,
                                     double *__restrict__ cur_ll, double *__restrict__ cur_sl,
@@ -488,7 +493,7 @@ __global__ void tree_resolve_kernel(int A, int M, int delayed, const int *__rest
     while (v >= 0 && p < len) {
         const int idx = slot * M + v;
         const int pos = chain_off[c] + p;
-        const bool run = !isnan(prop[3 * idx]);  // the one-step chain would have run this proposal
+        const bool run = !isnan(prop[P * idx]);  // the one-step chain would have run this proposal
         ran += run;
         if (run) work += run_work[idx];
         const bool valid = run && prop_status[idx] == SWIMMER_OK;
@@ -496,16 +501,12 @@ __global__ void tree_resolve_kernel(int A, int M, int delayed, const int *__rest
         if (delayed) thr -= qn * (prop_sl[idx] - cur_sl[c]);
         const bool accept = valid && log(u_acc[pos]) < thr;
         if (accept) {
-            cur_theta[3 * c] = prop[3 * idx];
-            cur_theta[3 * c + 1] = prop[3 * idx + 1];
-            cur_theta[3 * c + 2] = prop[3 * idx + 2];
+            for (int q = 0; q < P; ++q) cur_theta[P * c + q] = prop[P * idx + q];
             cur_ll[c] = prop_ll[idx];
             if (delayed) cur_sl[c] = prop_sl[idx];
             ++acc;
         }
-        out_theta[3 * pos] = cur_theta[3 * c];
-        out_theta[3 * pos + 1] = cur_theta[3 * c + 1];
-        out_theta[3 * pos + 2] = cur_theta[3 * c + 2];
+        for (int q = 0; q < P; ++q) out_theta[P * pos + q] = cur_theta[P * c + q];
         out_ll[pos] = cur_ll[c];
         out_sl[pos] = cur_sl[c];
         ++p;
@@ -580,7 +581,7 @@ extern "C" int tmcmc_analyze(swimmer_handle *h, int B, const double *theta, cons
     ARG_CHECK(B >= 1 && B <= h->cfg.b_max, "B outside [1, b_max]");
     ARG_CHECK(theta && loglik && out_w && stats, "NULL device pointer");
     ARG_CHECK(q >= 0.0 && q < 1.0, "q must be in [0, 1)");
-    analyze_kernel<<<1, T1, 0, (cudaStream_t)stream>>>(B, theta, loglik, q, out_w, stats);
+    analyze_kernel<<<1, T1, 0, (cudaStream_t)stream>>>(B, n_params(h->cfg), theta, loglik, q, out_w, stats);
     CUDA_TRY(cudaGetLastError());
     return 0;
 }
@@ -611,20 +612,21 @@ extern "C" int tmcmc_stage_shard(swimmer_handle *h, tmcmc_state *st, const doubl
     ARG_CHECK(st->sigma > 0.0, "sigma must be > 0");
     ARG_CHECK(st->q >= 0.0 && st->q < 1.0, "stage already at q = 1");
     ARG_CHECK(!use_surrogate || (h->surr_ready && st->surr_loglik), "surrogate not set up");
-    for (int a = 0; a < 3; ++a) ARG_CHECK(st->prior_lo[a] <= st->prior_hi[a], "prior box is empty");
+    const int P = n_params(h->cfg);
+    for (int a = 0; a < P; ++a) ARG_CHECK(st->prior_lo[a] <= st->prior_hi[a], "prior box is empty");
     cudaStream_t s = (cudaStream_t)stream;
     const int cap = 64;
-    analyze_kernel<<<1, T1, 0, s>>>(B, st->theta, st->loglik, st->q, h->w, h->stats);
+    analyze_kernel<<<1, T1, 0, s>>>(B, P, st->theta, st->loglik, st->q, h->w, h->stats);
     CUDA_TRY(cudaGetLastError());
     resample_kernel<<<1, T1, 0, s>>>(B, h->w, uniforms, (unsigned long long *)h->cum, h->idx, h->counts);
     CUDA_TRY(cudaGetLastError());
     const double *sl = use_surrogate ? st->surr_loglik : nullptr;
-    chains_kernel<<<1, T1, 0, s>>>(B, h->counts, st->theta, st->loglik, sl, h->chain_off, h->chain_len,
+    chains_kernel<<<1, T1, 0, s>>>(B, P, h->counts, st->theta, st->loglik, sl, h->chain_off, h->chain_len,
                                    h->chain_id, h->aux, h->cur_theta, h->cur_ll, h->cur_sl, h->info, cap);
     CUDA_TRY(cudaGetLastError());
     prof_count(h, 3);
     CUDA_TRY(cudaMemcpyAsync(h->host_pinned, h->info, cap * sizeof(int), cudaMemcpyDeviceToHost, s));
-    CUDA_TRY(cudaMemcpyAsync(h->host_pinned_d, h->stats, 32 * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaMemcpyAsync(h->host_pinned_d, h->stats, S_COUNT * sizeof(double), cudaMemcpyDeviceToHost, s));
     CUDA_TRY(cudaStreamSynchronize(s));
     const double *hs = h->host_pinned_d;
     if (hs[S_STATUS] != 0.0) {
@@ -638,9 +640,10 @@ extern "C" int tmcmc_stage_shard(swimmer_handle *h, tmcmc_state *st, const doubl
     CUDA_TRY(cudaMemsetAsync(h->info + cap, 0, 4 * sizeof(int), s));
     int n_screened = 0;
     Box box;
-    for (int a = 0; a < 3; ++a) {
-        box.lo[a] = st->prior_lo[a];
-        box.hi[a] = st->prior_hi[a];
+    box.P = P;
+    for (int a = 0; a < P_MAX; ++a) {
+        box.lo[a] = a < P ? st->prior_lo[a] : 0.0;
+        box.hi[a] = a < P ? st->prior_hi[a] : 0.0;
     }
     // pre-fetching: each launch runs up to `slots` forward models (as many as the GPU holds
     // at once at the smallest launch shape), a best-first template tree of M = slots / live
@@ -649,7 +652,7 @@ extern "C" int tmcmc_stage_shard(swimmer_handle *h, tmcmc_state *st, const doubl
     const int slots = min(h->cfg.b_max, forward_slots(h, h->cfg.precision));
     CUDA_TRY(cudaMemsetAsync(h->chain_pos, 0, sizeof(int) * U, s));
     if (world > 1) {  // rows of other ranks' chains stay zero, so a SUM over ranks assembles them
-        CUDA_TRY(cudaMemsetAsync(h->out_theta, 0, 3 * sizeof(double) * B, s));
+        CUDA_TRY(cudaMemsetAsync(h->out_theta, 0, P * sizeof(double) * B, s));
         CUDA_TRY(cudaMemsetAsync(h->out_ll, 0, sizeof(double) * B, s));
         CUDA_TRY(cudaMemsetAsync(h->out_sl, 0, sizeof(double) * B, s));
     }
@@ -679,7 +682,7 @@ extern "C" int tmcmc_stage_shard(swimmer_handle *h, tmcmc_state *st, const doubl
             int rc = run_surrogate_loglik(h, n, h->prop_theta, st->obs, st->sigma, h->prop_sl, s);
             if (rc) return rc;
             n_screened += n;
-            tree_screen_kernel<<<grid, 128, 0, s>>>(A, M, h->live, h->chain_off, h->chain_pos, h->cur_sl,
+            tree_screen_kernel<<<grid, 128, 0, s>>>(A, M, P, h->live, h->chain_off, h->chain_pos, h->cur_sl,
                                                     h->prop_sl, h->stats, uniforms + B, h->tmpl, h->prop_theta,
                                                     h->info + cap + 1);
             CUDA_TRY(cudaGetLastError());
@@ -689,14 +692,14 @@ extern "C" int tmcmc_stage_shard(swimmer_handle *h, tmcmc_state *st, const doubl
                              h->prop_status, s, 1);
         if (rc) return rc;
         tree_resolve_kernel<<<(A + 127) / 128, 128, 0, s>>>(
-            A, M, use_surrogate, h->live, h->chain_off, h->chain_len, h->chain_pos, h->cur_theta, h->cur_ll,
+            A, M, P, use_surrogate, h->live, h->chain_off, h->chain_len, h->chain_pos, h->cur_theta, h->cur_ll,
             h->cur_sl, h->prop_theta, h->prop_ll, h->prop_sl, h->prop_status, h->stats,
             uniforms + (use_surrogate ? 2 * B : B), h->tmpl, h->out_theta, h->out_ll, h->out_sl, h->info + cap,
             h->run_work, h->work + 1);
         CUDA_TRY(cudaGetLastError());
         prof_count(h, 1);
     }
-    CUDA_TRY(cudaMemcpyAsync(st->theta, h->out_theta, 3 * sizeof(double) * B, cudaMemcpyDeviceToDevice, s));
+    CUDA_TRY(cudaMemcpyAsync(st->theta, h->out_theta, P * sizeof(double) * B, cudaMemcpyDeviceToDevice, s));
     CUDA_TRY(cudaMemcpyAsync(st->loglik, h->out_ll, sizeof(double) * B, cudaMemcpyDeviceToDevice, s));
     if (use_surrogate)
         CUDA_TRY(cudaMemcpyAsync(st->surr_loglik, h->out_sl, sizeof(double) * B, cudaMemcpyDeviceToDevice, s));
@@ -707,8 +710,9 @@ extern "C" int tmcmc_stage_shard(swimmer_handle *h, tmcmc_state *st, const doubl
     st->stage += 1;
     st->log_s = hs[S_LOGS];
     st->log_evidence += hs[S_LOGS];
-    for (int a = 0; a < 3; ++a) st->mu[a] = hs[S_MU + a];
-    for (int e = 0; e < 9; ++e) st->sigma_prop[e] = hs[S_SIG + e];
+    for (int a = 0; a < 4; ++a) st->mu[a] = a < P ? hs[S_MU + a] : 0.0;
+    for (int a = 0; a < 4; ++a)
+        for (int c = 0; c < 4; ++c) st->sigma_prop[4 * a + c] = a < P && c < P ? hs[S_SIG + P_MAX * a + c] : 0.0;
     st->unique = U;
     st->max_chain = maxlen;
     st->n_accept = h->host_pinned[0];

@@ -43,13 +43,14 @@ def test_analyze_matches_oracle(B, q):
     w, st = g.tmcmc_analyze(h, torch.tensor(th, device=DEV), torch.tensor(ll, device=DEV), q)
     torch.cuda.synchronize()
     st = st.cpu().numpy()
-    assert st[25] == 0.0
+    # layout: dq, q_next, log S, l_max, mu[4], Sigma[4][4], L[4][4], status (3 unknowns used)
+    assert st[40] == 0.0
     assert abs(st[0] - a["dq"]) <= 1e-12 * max(a["dq"], 1e-300)
     assert st[1] == pytest.approx(a["q_next"], rel=1e-12)
     assert st[2] == pytest.approx(a["log_s"], rel=1e-12)
     assert np.allclose(st[4:7], a["mu"], rtol=1e-11, atol=1e-14)
-    assert np.allclose(st[7:16].reshape(3, 3), a["sigma"], rtol=1e-10, atol=1e-16)
-    assert np.allclose(st[16:25].reshape(3, 3), a["chol"], rtol=1e-10, atol=1e-16)
+    assert np.allclose(st[8:24].reshape(4, 4)[:3, :3], a["sigma"], rtol=1e-10, atol=1e-16)
+    assert np.allclose(st[24:40].reshape(4, 4)[:3, :3], a["chol"], rtol=1e-10, atol=1e-16)
     assert np.allclose(w.cpu().numpy(), a["w"], rtol=1e-11, atol=0)
     h.close()
 
@@ -185,3 +186,35 @@ def test_sharded_stage_sums_to_the_whole_stage(world):
     loads = np.bincount(row_owner, minlength=world)
     assert np.all(np.abs(loads - B / world) <= counts.max())
     h.close()
+
+
+def test_tmcmc_with_the_noise_level_as_a_fourth_unknown():
+    # sigma/beta inferred (Sec. 3.1): theta = (alpha, log10 K_C, a, s), the sample's noise is
+    # s * beta.  FP64 path sample by sample against the oracle, whose likelihood reads the
+    # fourth column the same way
+    B, seed = 96, 43
+    D, sigma = _problem()
+    beta = sigma / 0.05
+    lo4, hi4 = np.append(LO, 0.01), np.append(HI, 0.2)
+    cfg = g.SwimmerConfig(n_max=BASE.n, b_max=B, length=BASE.length, dt=BASE.dt, steps=BASE.steps,
+                          obs_every=BASE.obs_every, precision=g.FP64, n_params=4)
+    h = g.swimmer_init(cfg)
+    th0 = torch.tensor(synthetic.prior_samples(seed, lo4, hi4, B), device=DEV)
+    log_g = []
+    st = g.tmcmc_run(h, th0, torch.tensor(D, device=DEV), beta, lo4, hi4,
+                     lambda j: synthetic.stage_randoms(seed, j, B, 4), log=log_g)
+    torch.cuda.synchronize()
+    th_g, ll_g = st.theta.cpu().numpy(), st.loglik.cpu().numpy()
+    h.close()
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(min(16, mp.cpu_count())) as pool:
+        fn = lambda th: sw.batch_log_likelihood(BASE, th, D, beta, pool=pool, chunk=4)
+        th_o, ll_o, log_o = tm.run(synthetic.prior_samples(seed, lo4, hi4, B), fn, lo4, hi4, seed,
+                                   randoms=lambda j: synthetic.stage_randoms(seed, j, B, 4))
+    assert th_g.shape == (B, 4)
+    assert [s["q"] for s in log_g] == pytest.approx(log_o.q, rel=1e-9)
+    assert np.allclose(th_g, th_o, rtol=1e-8, atol=1e-10)
+    assert np.allclose(ll_g, ll_o, rtol=1e-8, atol=1e-8)
+    # the noise level the data were made with (5 %) lies inside the posterior's bulk
+    s = th_g[:, 3]
+    assert np.quantile(s, 0.02) < 0.05 < np.quantile(s, 0.98)
