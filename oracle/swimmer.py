@@ -318,3 +318,27 @@ def batch_log_likelihood(base: SwimmerParams, thetas, D, sigma, pool=None, chunk
     parts = [(base, thetas[i:i + chunk], D, sigma) for i in range(0, len(thetas), chunk)]
     res = pool.map(_loglik_chunk, parts) if pool is not None else [_loglik_chunk(a) for a in parts]
     return np.concatenate(res) if res else np.zeros(0)
+
+
+# ---------------------------------------------------------------------------------------
+# flow and pressure at target points (Eqs. BrP, BrV with targets x other than the swimmer)
+# ---------------------------------------------------------------------------------------
+def pressure_kernel(r, delta):
+    """G_delta'(r)/r = M0(r)/r^2 (text after Eq. BrV), finite at r = 0: with R = sqrt(r^2 +
+    delta^2), M0/r^2 = (R^2 + R delta + delta^2) / (2 pi R^3 (R + delta))."""
+    r = np.asarray(r, dtype=np.float64)
+    R = np.hypot(r, delta)
+    return (R * R + R * delta + delta * delta) / (2.0 * np.pi * R ** 3 * (R + delta))
+
+
+def flow_field(X, F, grid, table, delta, mu=1.0):
+    """Velocity v(x) (Eq. BrV) and pressure p(x) = sum_j F_j . grad G_delta(|x - X_j|)
+    (Eq. BrP) at the target points grid [G, 2], from point forces F [N, 2] at X [N, 2]."""
+    grid = np.asarray(grid, dtype=np.float64)
+    d = grid[:, None, :] - X[None, :, :]
+    r = np.hypot(d[..., 0], d[..., 1])
+    g1, g2 = table(r)
+    fd = np.einsum("jc,gjc->gj", F, d)
+    v = (-np.einsum("gj,jc->gc", g1, F) + np.einsum("gj,gj,gjc->gc", fd, g2, d)) / mu
+    p = np.sum(fd * pressure_kernel(r, delta), axis=1)
+    return v, p
