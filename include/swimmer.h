@@ -190,6 +190,25 @@ int swimmer_autotune(swimmer_handle *h, int steps, const double *theta, int n_th
  * across handles or processes. */
 int swimmer_tuning(swimmer_handle *h, int precision, int *threads, int set);
 
+/* forward_batch that also returns each run's final state: final_state (device
+ * [B][n_max][4] FP64) = (x, y, F_x, F_y) of every point at t = steps dt, the forces
+ * recomputed there (Eq. Fenergy); rows past a sample's points and runs that stopped early are
+ * NaN.  Points: flagellum 0..n-1, then the head, then the second swimmer's.  Used for the
+ * flow field below.  Errors as forward_batch. */
+int forward_batch_state(swimmer_handle *h, int B, const double *theta, const int *n_pts, double *head_traj,
+                        double *mean_speed, int *status, double *final_state, void *stream);
+
+/* Velocity and pressure at target points (Eqs. BrP, BrV with targets x away from the
+ * swimmer): vel[g] = (1/mu) sum_j [-F_j g1(r) + (F_j . d) d g2(r)], pres[g] = sum_j (F_j . d)
+ * G_delta'(r)/r, d = x_g - X_j, from the n points of state (device [n][4] (x, y, F_x, F_y),
+ * e.g. one sample of forward_batch_state) for the kernel of (alpha, delta).  grid: device
+ * [G][2]; vel: device [G][2]; pres: device [G] (either may be NULL, not both).  r_max bounds
+ * every target-to-point distance (the FP64 table is built to it; farther distances are
+ * clamped).  Builds the table in the handle's sample slot 0.  Asynchronous on stream;
+ * SWIMMER_E_ARG on bad sizes or parameters (alpha r_max beyond the table's reach gives NaN). */
+int swimmer_flow_field(swimmer_handle *h, double alpha, double delta, double r_max, int n, const double *state,
+                       int G, const double *grid, double *vel, double *pres, void *stream);
+
 /* Batched log-likelihood (Sec. 3.1, Eqs. likelihood/fitness with Sigma = sigma^2 I):
  *   loglik[b] = -(m/2) ln(2 pi sigma^2) - sum_o |D_o - head_o(theta_b)|^2 / (2 sigma^2),
  * m = 2 n_obs, obs = D [n_obs][2] on the device, shared by all samples.  The residuals

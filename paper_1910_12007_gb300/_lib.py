@@ -47,6 +47,10 @@ SIGNATURES = [
     ("swimmer_autotune", c_int, [c_void_p, c_int, c_void_p, c_int, c_void_p]),
     ("swimmer_tuning", c_int, [c_void_p, c_int, c_void_p, c_int]),
     ("loglik_batch", c_int, [c_void_p, c_int, c_void_p, c_void_p, c_void_p, c_double, c_void_p, c_void_p, c_void_p]),
+    ("forward_batch_state", c_int, [c_void_p, c_int, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
+                                    c_void_p]),
+    ("swimmer_flow_field", c_int, [c_void_p, c_double, c_double, c_double, c_int, c_void_p, c_int, c_void_p,
+                                   c_void_p, c_void_p, c_void_p]),
     ("tmcmc_stage", c_int, [c_void_p, P(TmcmcStateC), c_void_p, c_void_p, c_int, c_void_p]),
     ("tmcmc_stage_shard", c_int, [c_void_p, P(TmcmcStateC), c_void_p, c_void_p, c_int, c_int, c_int, c_void_p]),
     ("tmcmc_tree_template", c_int, [c_int, c_double, c_int, c_void_p, c_void_p]),

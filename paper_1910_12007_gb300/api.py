@@ -135,6 +135,37 @@ def forward_batch(h: Handle, theta: torch.Tensor, n_pts=None, want_traj=True, st
     return traj, speed, status
 
 
+def forward_batch_state(h: Handle, theta: torch.Tensor, n_pts=None, stream=None):
+    """forward_batch plus each run's final state [B, n_max, 4] = (x, y, F_x, F_y) at the end
+    of the run (NaN rows past a sample's points).  Returns (head_traj, mean_speed, status,
+    state)."""
+    _dev(theta, torch.float64)
+    B = theta.shape[0]
+    dev = theta.device
+    traj = torch.empty((B, h.cfg.n_obs, 2), dtype=torch.float64, device=dev)
+    speed = torch.empty(B, dtype=torch.float64, device=dev)
+    status = torch.empty(B, dtype=torch.int32, device=dev)
+    state = torch.empty((B, h.cfg.n_max, 4), dtype=torch.float64, device=dev)
+    if n_pts is not None:
+        _dev(n_pts, torch.int32)
+    check(lib().forward_batch_state(h.ptr, B, _ptr(theta), _ptr(n_pts), _ptr(traj), _ptr(speed), _ptr(status),
+                                    _ptr(state), _stream(stream)))
+    return traj, speed, status, state
+
+
+def swimmer_flow_field(h: Handle, alpha, delta, r_max, state: torch.Tensor, grid: torch.Tensor, stream=None):
+    """Velocity [G, 2] and pressure [G] at the target points grid [G, 2] (device FP64) from
+    the points of state [n, 4] = (x, y, F_x, F_y) (device FP64)."""
+    _dev(state, torch.float64)
+    _dev(grid, torch.float64)
+    G = grid.shape[0]
+    vel = torch.empty((G, 2), dtype=torch.float64, device=grid.device)
+    pres = torch.empty(G, dtype=torch.float64, device=grid.device)
+    check(lib().swimmer_flow_field(h.ptr, float(alpha), float(delta), float(r_max), int(state.shape[0]),
+                                   _ptr(state), int(G), _ptr(grid), _ptr(vel), _ptr(pres), _stream(stream)))
+    return vel, pres
+
+
 def loglik_batch(h: Handle, theta, obs, sigma, n_pts=None, stream=None, out=None):
     """Gaussian log-likelihood of B samples against observations obs [n_obs, 2]."""
     _dev(theta, torch.float64)

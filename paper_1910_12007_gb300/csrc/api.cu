@@ -261,12 +261,12 @@ static int check_batch(swimmer_handle *h, int B, const double *theta, const int 
 
 int run_forward(swimmer_handle *h, int B, const double *theta, const int *n_pts, const double *obs,
                 double sigma, double *loglik, double *head_traj, double *mean_speed, int *status,
-                cudaStream_t s, int speculative) {
+                cudaStream_t s, int speculative, double *final_state) {
     int rc = launch_prepare(h, B, theta, n_pts, s);
     if (!rc) rc = launch_table_build(h, B, h->cfg.precision == SWIMMER_FP64, s);
     if (!rc)
         rc = launch_forward(h, B, obs, sigma, loglik, head_traj, mean_speed, status, h->cfg.precision, s, 0,
-                            speculative);
+                            speculative, final_state);
     return rc;
 }
 
@@ -377,7 +377,17 @@ extern "C" int forward_batch(swimmer_handle *h, int B, const double *theta, cons
     int rc = check_batch(h, B, theta, status);
     if (rc) return rc;
     return run_forward(h, B, theta, n_pts, nullptr, 0.0, nullptr, head_traj, mean_speed, status,
-                       (cudaStream_t)stream, 0);
+                       (cudaStream_t)stream, 0, nullptr);
+}
+
+extern "C" int forward_batch_state(swimmer_handle *h, int B, const double *theta, const int *n_pts,
+                                   double *head_traj, double *mean_speed, int *status, double *final_state,
+                                   void *stream) {
+    int rc = check_batch(h, B, theta, status);
+    if (rc) return rc;
+    ARG_CHECK(final_state != nullptr, "final_state is NULL");
+    return run_forward(h, B, theta, n_pts, nullptr, 0.0, nullptr, head_traj, mean_speed, status,
+                       (cudaStream_t)stream, 0, final_state);
 }
 
 extern "C" int loglik_batch(swimmer_handle *h, int B, const double *theta, const int *n_pts,
@@ -388,5 +398,6 @@ extern "C" int loglik_batch(swimmer_handle *h, int B, const double *theta, const
     ARG_CHECK(loglik != nullptr, "loglik is NULL");
     ARG_CHECK(sigma > 0.0, "sigma must be > 0");
     ARG_CHECK(h->cfg.steps / h->cfg.obs_every >= 1, "no observation within steps");
-    return run_forward(h, B, theta, n_pts, obs, sigma, loglik, nullptr, nullptr, status, (cudaStream_t)stream, 0);
+    return run_forward(h, B, theta, n_pts, obs, sigma, loglik, nullptr, nullptr, status, (cudaStream_t)stream, 0,
+                       nullptr);
 }

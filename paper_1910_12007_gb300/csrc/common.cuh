@@ -146,7 +146,7 @@ int launch_prepare(swimmer_handle *h, int B, const double *theta, const int *n_p
 int launch_table_build(swimmer_handle *h, int B, int need64, cudaStream_t s);
 int launch_forward(swimmer_handle *h, int B, const double *obs, double sigma, double *loglik,
                    double *head_traj, double *mean_speed, int *status, int precision,
-                   cudaStream_t s, int threads_override = 0, int speculative = 0);
+                   cudaStream_t s, int threads_override = 0, int speculative = 0, double *final_state = nullptr);
 int forward_threads(const swimmer_handle *h, int B, int precision);
 int tune_bucket(const swimmer_handle *h, int B);
 int forward_min_threads(const swimmer_handle *h, int precision);

@@ -33,6 +33,7 @@
 #include <math.h>
 
 #include "common.cuh"
+#include "table_eval.cuh"
 
 namespace {
 
@@ -56,6 +57,7 @@ struct FwdArgs {
     double *loglik;
     double *head_traj;
     double *speed;
+    double *final_state;  // optional [B][n_max][4]: (x, y, Fx, Fy) at the end of the run
     int *status;
     unsigned long long *work;      // [0] executed, [1] useful pair evaluations
     unsigned long long *run_work;  // per-run pair evaluations (speculative launches)
@@ -223,28 +225,6 @@ __device__ __forceinline__ void kern_f32(const float4 *__restrict__ tA, const fl
     g2 = fmaf(F, fmaf(F, c.y, c.x), a.w);
 }
 
-__device__ __forceinline__ void kern_f64(const double *__restrict__ tab, int P, int pmax, double u, double &g1,
-                                         double &g2) {
-    unsigned long long bits = (unsigned long long)__double_as_longlong(u);
-    unsigned long long p = (bits >> (52 - F64_SUB_LOG2)) - (1023ull << F64_SUB_LOG2);
-    if (p > (unsigned long long)pmax) p = pmax;
-    double f = __longlong_as_double(0x3ff0000000000000LL | (long long)((bits << F64_SUB_LOG2) & 0x000fffffffffffffull)) - 1.0;
-    double t = 2.0 * f - 1.0, t2 = 2.0 * t;
-    const double *c1 = tab + p * F64_NODES;
-    const double *c2 = tab + ((size_t)P + p) * F64_NODES;
-    double a1 = 0.0, a2 = 0.0, b1 = 0.0, b2 = 0.0;
-#pragma unroll
-    for (int k = F64_DEG; k >= 1; --k) {
-        double a0 = fma(t2, a1, c1[k] - a2);
-        a2 = a1;
-        a1 = a0;
-        double b0 = fma(t2, b1, c2[k] - b2);
-        b2 = b1;
-        b1 = b0;
-    }
-    g1 = fma(t, a1, c1[0] - a2);
-    g2 = fma(t, b1, c2[0] - b2);
-}
 
 // One FP32 pair unit of 16 diagonal steps: lane l holds target I*32 + l and at step
 // d = d0 .. d0+15 meets source J*32 + (l + d) mod 32; the source-side sums rotate one lane
@@ -528,7 +508,9 @@ __global__ void __launch_bounds__(1024) forward_kernel(FwdArgs a) {
                      g2unused);
         }
 
-        for (long long step = 0; step < a.steps; ++step) {
+        // with a final state requested, one more pass of the force phases at t = steps dt
+        const long long last = a.steps + (a.final_state ? 1 : 0);
+        for (long long step = 0; step < last; ++step) {
             const R tR = (R)(step * a.dt);
             int bad = 0;
             // ---- A+B: segments, tension, curvature stencils, relative positions.  Thread k
@@ -752,6 +734,17 @@ __global__ void __launch_bounds__(1024) forward_kernel(FwdArgs a) {
                 src[kd].w = fy;
             }
             __syncthreads();
+            if (step == a.steps) {  // final state: positions and the forces there
+                for (int k = tid; k < n; k += T) {
+                    const int ks = F64 ? k : ((k >> 5) << 6) + (k & 31);
+                    double *o = a.final_state + ((size_t)b * n_max + k) * 4;
+                    o[0] = (F64 ? sx[k] : (double)xh[k] + (double)xl[k]) + xref;
+                    o[1] = F64 ? sy[k] : (double)yh[k] + (double)yl[k];
+                    o[2] = (double)src[ks].z;
+                    o[3] = (double)src[ks].w;
+                }
+                break;
+            }
             // ---- D: pair sum
             double vxd = 0.0, vyd = 0.0;
             if (F64) {
@@ -907,6 +900,11 @@ __global__ void __launch_bounds__(1024) forward_kernel(FwdArgs a) {
             }
         }
         // ---- outputs
+        if (a.final_state) {  // rows past the sample's points, or of a run that stopped: NaN
+            const int k0 = status == SWIMMER_OK ? n : 0;
+            for (int k = k0 + tid; k < n_max; k += T)
+                for (int c = 0; c < 4; ++c) a.final_state[((size_t)b * n_max + k) * 4 + c] = nan("");
+        }
         if (a.speed && tid < 32) {
             // mean speed: x-displacement of the flagellum's centroid (which starts at 0 in the
             // stored coordinates) or, with a head, of the head centre, over the run's duration;
@@ -1024,7 +1022,7 @@ int forward_threads(const swimmer_handle *h, int B, int precision) {
 
 int launch_forward(swimmer_handle *h, int B, const double *obs, double sigma, double *loglik,
                    double *head_traj, double *mean_speed, int *status, int precision, cudaStream_t s,
-                   int threads_override, int speculative) {
+                   int threads_override, int speculative, double *final_state) {
     FwdArgs a;
     a.B = B;
     a.sp = h->sp;
@@ -1053,6 +1051,7 @@ int launch_forward(swimmer_handle *h, int B, const double *obs, double sigma, do
     a.loglik = loglik;
     a.head_traj = head_traj;
     a.speed = mean_speed;
+    a.final_state = final_state;
     a.status = status;
     a.work = h->work;
     a.run_work = h->run_work;

@@ -25,7 +25,7 @@
 
 int run_forward(swimmer_handle *h, int B, const double *theta, const int *n_pts, const double *obs,
                 double sigma, double *loglik, double *head_traj, double *mean_speed, int *status,
-                cudaStream_t s, int speculative);
+                cudaStream_t s, int speculative, double *final_state);
 int run_surrogate_loglik(swimmer_handle *h, int B, const double *theta, const double *obs, double sigma,
                          double *loglik, cudaStream_t s);
 
@@ -689,7 +689,7 @@ extern "C" int tmcmc_stage_shard(swimmer_handle *h, tmcmc_state *st, const doubl
             prof_count(h, 1);
         }
         int rc = run_forward(h, n, h->prop_theta, nullptr, st->obs, st->sigma, h->prop_ll, nullptr, nullptr,
-                             h->prop_status, s, 1);
+                             h->prop_status, s, 1, nullptr);
         if (rc) return rc;
         tree_resolve_kernel<<<(A + 127) / 128, 128, 0, s>>>(
             A, M, P, use_surrogate, h->live, h->chain_off, h->chain_len, h->chain_pos, h->cur_theta, h->cur_ll,
