@@ -211,14 +211,16 @@ def main():
     ap.add_argument("--profile-case", action="store_true",
                     help="run one forward batch of the workload (1024 samples, 200 steps) for ncu and exit")
     ap.add_argument("--workload", default="tmcmc",
-                    choices=["tmcmc", "uneven", "large", "surrogate", "shapes", "sperm", "sperm-tmcmc", "two-sperm"],
+                    choices=["tmcmc", "uneven", "large", "surrogate", "shapes", "sperm", "sperm-tmcmc", "two-sperm",
+                             "flow"],
                     help="tmcmc (default): TMCMC stages, 1024 samples, N=128; uneven: 4096 samples with "
                          "N in {64,128,256,512} in one graph-captured persistent launch; large: 256 samples "
                          "x N=1024 x 4e4 steps; surrogate: delayed-acceptance vs plain TMCMC, 4096 samples/stage; "
                          "shapes: forward-kernel time per step vs samples per SM and threads per sample; sperm: "
                          "1024 full sperm models (flagellum 50 + head 24 points, Table Tab:param) x one beat; "
                          "sperm-tmcmc: a whole TMCMC run on the full sperm model, head-centre velocities; "
-                         "two-sperm: 1024 pairs of sperm models 0.5 apart (148 points) x one beat, distances")
+                         "two-sperm: 1024 pairs of sperm models 0.5 apart (148 points) x one beat, distances; "
+                         "flow: velocity and pressure of a sperm model on a 1024 x 1024 grid")
     args = ap.parse_args()
 
     from paper_1910_12007_gb300 import ranks
@@ -241,6 +243,8 @@ def main():
         return shapes_workload(args, rank, local_rank)
     if args.workload == "sperm-tmcmc":
         return sperm_tmcmc_workload(args, rank, local_rank)
+    if args.workload == "flow":
+        return flow_workload(args, rank, local_rank)
 
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
@@ -610,6 +614,56 @@ def shapes_workload(args, rank, local_rank):
         rows.append({"samples": B, "samples_per_sm": B / sms, "us_per_step_by_threads": row})
     print(json.dumps({"workload": f"forward kernel, N={N_PTS}, {steps} steps, FP32C: microseconds per time step",
                       "sms": sms, "rows": rows}), flush=True)
+    h.close()
+    return 0
+
+
+# -------------------------------------------------------------------------------------
+# flow and pressure fields (Eqs. BrP, BrV on a grid) of the full sperm model
+# -------------------------------------------------------------------------------------
+def flow_workload(args, rank, local_rank):
+    import numpy as np
+    import torch
+
+    import paper_1910_12007_gb300 as g
+
+    if rank != 0:
+        return 0
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    cfg = g.SwimmerConfig(n_max=74, b_max=1, length=1.0, delta_over_ds=0.045 * 49, dt=1e-4 / 8, k_t=1e4,
+                          omega=4 * math.pi, steps=40000, obs_every=4000, precision=g.FP64, n_head=24,
+                          k_head_tens=1e4, k_head_c=0.8, k_neck_tens=500.0, k_neck_ang=1e4,
+                          obs_kind=g.OBS_HEAD_VELOCITY)
+    h = g.swimmer_init(cfg)
+    _, _, status, state = g.forward_batch_state(h, torch.tensor([[1.0, math.log10(8.0), 0.1]],
+                                                                dtype=torch.float64, device=dev))
+    st0 = state[0].contiguous()
+    n_grid = 1024
+    xs = torch.linspace(-0.5, 2.0, n_grid, dtype=torch.float64, device=dev)
+    ys = torch.linspace(-1.25, 1.25, n_grid, dtype=torch.float64, device=dev)
+    grid = torch.stack(torch.meshgrid(xs, ys, indexing="ij"), dim=-1).reshape(-1, 2).contiguous()
+    delta = 0.045
+    for _ in range(max(args.warmup, 1)):
+        g.swimmer_flow_field(h, 1.0, delta, 4.0, st0, grid)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        vel, pres = g.swimmer_flow_field(h, 1.0, delta, 4.0, st0, grid)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    evals = grid.shape[0] * 74
+    line = {"metric": METRIC, "value": evals / (ms * 1e-3), "unit": "target-source evaluations/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "velocity and pressure (Eqs. BrP, BrV) on a 1024 x 1024 grid from the final "
+                                   "state of one full sperm model (74 points) after one beat, FP64, table "
+                                   "build included"},
+            "status": int(status[0].item()), "max_speed": float(vel.norm(dim=1).max().item()),
+            "pressure_range": [float(pres.min().item()), float(pres.max().item())]}
+    print(json.dumps(line), flush=True)
     h.close()
     return 0
 
