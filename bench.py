@@ -38,10 +38,10 @@ THETA_TRUE = (1.0, 0.0, 0.1)
 PRIOR_LO = (0.0, -1.0, 0.05)
 PRIOR_HI = (10.0, 1.0, 0.2)
 NOISE = 0.05
-# FP32 flops of one unordered pair {i, j} in the symmetric pair sum: difference 2, r^2 3, u 2,
-# quadratic table 8 (shared by both directions), then per direction F.d 3, (F.d) g2 1 and the
-# velocity update 8
-FLOPS_PER_UNORDERED_PAIR = 39
+# FP32 flops of one unordered pair {i, j} in the symmetric pair sum (separations in units of
+# delta): difference 2, u = 1 + |e|^2 4, quadratic table 8, the symmetric 2x2 mobility 7 (all
+# shared by both directions), then per direction M F 8
+FLOPS_PER_UNORDERED_PAIR = 37
 
 
 def pair_sum_flops(ordered_pairs, unordered_per_ordered):

@@ -23,8 +23,9 @@ constexpr int NODES_MAX = F64_PANELS_MAX * F64_NODES;   // 1920
 // FP64 table per sample: [2][F64_PANELS_MAX][F64_NODES] Chebyshev coefficients
 constexpr int TAB64_STRIDE = 2 * F64_PANELS_MAX * F64_NODES;
 // FP32 table per sample (float4 units): part A [F32_PANELS_MAX] float4 = (g1 c0, g1 c1,
-// g1 c2, g2 c0) then part B [F32_PANELS_MAX] float2 = (g2 c1, g2 c2): monomial quadratic
-// coefficients in the local panel coordinate f in [0, 1)
+// g1 c2, h c0) then part B [F32_PANELS_MAX] float2 = (h c1, h c2), h = delta^2 g2: monomial
+// quadratic coefficients in G = 1 + f / F32_SUB, f in [0, 1) the local panel coordinate
+// (G is u's mantissa with the panel bits cleared)
 constexpr int TAB32_STRIDE = F32_PANELS_MAX + F32_PANELS_MAX / 2;
 constexpr int TAIL_MAX = 64;           // pieces of the integral of K0 phi s beyond the last node
 constexpr int K1_SCRATCH = 2 * NODES_MAX + TAIL_MAX;  // doubles of table-build scratch per sample

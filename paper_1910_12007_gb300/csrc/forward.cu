@@ -12,16 +12,18 @@
 //   C  point forces F = -dE/dX (Eq. Fenergy) gathered from the stencils;
 //   D  Brinkmanlet pair sum (Eq. BrV) v_i = (1/mu) sum_j [-F_j g1 + (F_j . d) d g2],
 //      d = X_i - X_j, with g1, g2 from the per-sample shared-memory table (quadratic in
-//      F = 1 + f in FP32, Chebyshev degree 9 in FP64).
+//      G = 1 + f/64 in FP32, Chebyshev degree 9 in FP64).
 //      FP32: every unordered pair once.  g1, g2 and (F . d) d are even in d, so one table
 //      lookup serves v_i and v_j.  The points form blocks of 32; a warp takes a block pair
 //      (I, J) along diagonals: lane l holds target I*32 + l and meets source
 //      J*32 + (l + d) mod 32 at step d, so all lanes look up nearly the same table panel
 //      (|d| ds apart on a smooth filament) and the loads broadcast, while the source-side
-//      sums travel one lane per step with warp shuffles.  Sources (x, y, Fx, Fy) are one
-//      float4 per point, each block stored twice in a row so that the walk needs no wrap
-//      test.  Per-warp partial sums are combined in a fixed order with TwoSum, so results
-//      do not depend on scheduling.
+//      sums travel one lane per step with warp shuffles.  Sources (x/delta, y/delta, Fx,
+//      Fy) are one float4 per point, each block stored twice in a row so that the walk
+//      needs no wrap test; a pair's term is the symmetric 2x2 mobility
+//      M = delta^2 g2 e e^T - g1 I (e = d/delta) applied to F_j and to F_i.  Per-warp
+//      partial sums are combined in a fixed order with TwoSum, so results do not depend
+//      on scheduling.
 //      FP64: target i meets source i + d at step d (the point list stored twice), the S
 //      threads of a target splitting the sources and combining with warp shuffles;
 //   E  forward Euler X += dt v: FP64 positions in the FP64 kernel, double-float (hi + lo
@@ -210,21 +212,40 @@ __host__ __device__ size_t smem_bytes(int n_max, int P, int threads) {
 }
 
 
-// g1, g2 from the FP32 table: quadratic in F = 1 + f in [1, 2), the mantissa of u
+// g1 and h = delta^2 g2 from the FP32 table: quadratic in G = 1 + f / 64, f in [0, 1) the
+// position of u within its panel
 __device__ __forceinline__ void kern_f32(const float4 *__restrict__ tA, const float2 *__restrict__ tB, int pmax,
                                          float u, float &g1, float &g2) {
     // u >= 1: the panel is (exponent - 127) * panels per octave + top mantissa bits; the
-    // exponent bias is subtracted after the clamp, where it folds into the load offsets
+    // exponent bias is subtracted after the clamp, where it folds into the load offsets.  G
+    // is u's mantissa with the panel bits cleared (one logic operation).
     constexpr int BIAS = 127 << F32_SUB_LOG2;
     const unsigned bits = __float_as_uint(u);
     const int p = (int)min(bits >> (23 - F32_SUB_LOG2), (unsigned)(pmax + BIAS));
-    const float F = __uint_as_float(0x3f800000u | ((bits << F32_SUB_LOG2) & 0x7fffffu));
+    const float G = __uint_as_float(0x3f800000u | (bits & ((1u << (23 - F32_SUB_LOG2)) - 1u)));
     const float4 a = tA[p - BIAS];
     const float2 c = tB[p - BIAS];
-    g1 = fmaf(F, fmaf(F, a.z, a.y), a.x);
-    g2 = fmaf(F, fmaf(F, c.y, c.x), a.w);
+    g1 = fmaf(G, fmaf(G, a.z, a.y), a.x);
+    g2 = fmaf(G, fmaf(G, c.y, c.x), a.w);
 }
 
+
+// One pair's 2x2 mobility M = h e e^T - g1 I (e = d / delta, h = delta^2 g2), symmetric
+// and even in e: v_i += M F_j and v_j += M F_i (Eq. BrV).  Sources and targets hold
+// positions in units of delta, so u = 1 + |e|^2 needs no scaling.
+struct Mob {
+    float m11, m12, m22;
+};
+__device__ __forceinline__ Mob pair_mob(const float4 *__restrict__ t1, const float2 *__restrict__ t2, int pmax,
+                                        float ex, float ey, float mask) {
+    const float u = fmaf(ex, ex, fmaf(ey, ey, 1.0f));
+    float g1, h;
+    kern_f32(t1, t2, pmax, u, g1, h);
+    g1 *= mask;
+    h *= mask;
+    const float hx = h * ex, hy = h * ey;
+    return Mob{fmaf(hx, ex, -g1), hx * ey, fmaf(hy, ey, -g1)};
+}
 
 // One FP32 pair unit of 16 diagonal steps: lane l holds target I*32 + l and at step
 // d = d0 .. d0+15 meets source J*32 + (l + d) mod 32; the source-side sums rotate one lane
@@ -232,8 +253,8 @@ __device__ __forceinline__ void kern_f32(const float4 *__restrict__ tA, const fl
 // (lanes l and l + 16 meet the same pair there).  Adds the unit's sums into the warp's
 // partial array.
 __device__ __forceinline__ void pair_unit(const float4 *__restrict__ s4, const float4 *__restrict__ t1,
-                                          const float2 *__restrict__ t2, int pmax, float fid2, int lane, int I,
-                                          int Jb, int d0, float2 *__restrict__ mypart) {
+                                          const float2 *__restrict__ t2, int pmax, int lane, int I, int Jb,
+                                          int d0, float2 *__restrict__ mypart) {
     const bool diag = I == Jb;
     const int nxt = (lane + 1) & 31;
     const float half_mask = lane < 16 ? 1.f : 0.f;
@@ -243,20 +264,11 @@ __device__ __forceinline__ void pair_unit(const float4 *__restrict__ s4, const f
 #pragma unroll
     for (int s = 0; s < 16; ++s) {
         const float4 q = sp[s];
-        const float dx = me.x - q.x, dy = me.y - q.y;
-        const float u = fmaf(fmaf(dx, dx, dy * dy), fid2, 1.0f);
-        float g1, g2;
-        kern_f32(t1, t2, pmax, u, g1, g2);
-        if (s == 15 && diag) {
-            g1 *= half_mask;
-            g2 *= half_mask;
-        }
-        const float wj = fmaf(q.z, dx, q.w * dy) * g2;
-        const float wi = fmaf(me.z, dx, me.w * dy) * g2;
-        vx = fmaf(wj, dx, fmaf(-q.z, g1, vx));
-        vy = fmaf(wj, dy, fmaf(-q.w, g1, vy));
-        ax = fmaf(wi, dx, fmaf(-me.z, g1, ax));
-        ay = fmaf(wi, dy, fmaf(-me.w, g1, ay));
+        const Mob M = pair_mob(t1, t2, pmax, me.x - q.x, me.y - q.y, (s == 15 && diag) ? half_mask : 1.f);
+        vx = fmaf(M.m11, q.z, fmaf(M.m12, q.w, vx));
+        vy = fmaf(M.m12, q.z, fmaf(M.m22, q.w, vy));
+        ax = fmaf(M.m11, me.z, fmaf(M.m12, me.w, ax));
+        ay = fmaf(M.m12, me.z, fmaf(M.m22, me.w, ay));
         ax = __shfl_sync(0xffffffffu, ax, nxt);
         ay = __shfl_sync(0xffffffffu, ay, nxt);
     }
@@ -474,6 +486,7 @@ __global__ void __launch_bounds__(1024) forward_kernel(FwdArgs a) {
         const R kc2ds = (R)(2.0 * p.kc * ds);
         const R r_amp = (R)p.amp, r_eta = (R)a.eta, r_omega = (R)a.omega, r_L = (R)L;
         const R inv_d2 = (R)(1.0 / (p.delta * p.delta));
+        const float inv_delta_f = (float)(1.0 / p.delta);
         const double dt_mu = a.dt / a.mu;
         const float dt_mu_f = (float)dt_mu, ds_f = (float)ds;
         // FP64 pair sum: thread -> (target, source split of S lanes)
@@ -557,8 +570,9 @@ __global__ void __launch_bounds__(1024) forward_kernel(FwdArgs a) {
                         lo = e + (yl[k] - yl[prev]);
                         emy = (R)(s + lo);
                     }
-                    qx = (R)(xh[k] + xl[k]);
-                    qy = (R)(yh[k] + yl[k]);
+                    // the pair sum measures separations in units of delta
+                    qx = (R)((xh[k] + xl[k]) * inv_delta_f);
+                    qy = (R)((yh[k] + yl[k]) * inv_delta_f);
                 }
                 if (next >= 0) {  // tension force vector of segment (k, next)
                     tvx[k] = tk * epx;
@@ -788,14 +802,13 @@ __global__ void __launch_bounds__(1024) forward_kernel(FwdArgs a) {
                 const float4 *s4 = (const float4 *)src;
                 const float4 *t1 = (const float4 *)tabraw;
                 const float2 *t2 = (const float2 *)(t1 + P);
-                const float fid2 = (float)inv_d2;
                 const int warp = tid >> 5;
                 float2 *mypart = part + warp * (nb << 5);
                 for (int k = lane; k < (nb << 5); k += 32) mypart[k] = make_float2(0.f, 0.f);
                 const int *units = (const int *)(tabraw + table_bytes<F64>(P));
                 for (int un = warp; un < n_units; un += n_pw) {
                     const int pk = units[un];
-                    pair_unit(s4, t1, t2, npan - 1, fid2, lane, pk & 255, (pk >> 8) & 255, pk >> 16, mypart);
+                    pair_unit(s4, t1, t2, npan - 1, lane, pk & 255, (pk >> 8) & 255, pk >> 16, mypart);
                 }
             }
             if (!F64) __syncthreads();
