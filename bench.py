@@ -210,6 +210,9 @@ def main():
                          "all-reduce per stage) instead of an independent TMCMC per rank (weak scaling)")
     ap.add_argument("--profile-case", action="store_true",
                     help="run one forward batch of the workload (1024 samples, 200 steps) for ncu and exit")
+    ap.add_argument("--shape", default=None,
+                    help="--profile-case launch shape: threads per sample, suffix w for two-target pair units "
+                         "(e.g. 128w); default: the untuned heuristic")
     ap.add_argument("--workload", default="tmcmc",
                     choices=["tmcmc", "uneven", "large", "surrogate", "shapes", "sperm", "sperm-tmcmc", "two-sperm",
                              "flow"],
@@ -264,6 +267,9 @@ def main():
     if args.profile_case:
         cfg.steps = 200
         h = g.swimmer_init(cfg)
+        if args.shape:
+            shape = int(args.shape.rstrip("w")) | (g.SHAPE_WIDE if args.shape.endswith("w") else 0)
+            g.swimmer_tuning(h, prec, [shape] * 17)
         th = torch.tensor(synthetic.prior_samples(5, PRIOR_LO, (10.0, 0.2, 0.2), B_STAGE), device=dev)
         for rep in range(2):
             g.swimmer_profile(h, 1)
@@ -272,6 +278,7 @@ def main():
         g.swimmer_profile(h, 0)
         torch.cuda.synchronize()
         print(json.dumps({"profile_case": f"{B_STAGE} samples x N={N_PTS} x {cfg.steps} steps",
+                          "shape": args.shape or "heuristic",
                           "k2_ms": k2_ms, "pair_evals_per_s": pairs / (k2_ms * 1e-3),
                           "tflops": pair_sum_flops(pairs, (N_PTS - 1) / (2.0 * N_PTS)) / (k2_ms * 1e-3) / 1e12}))
         h.close()
@@ -598,7 +605,7 @@ def shapes_workload(args, rank, local_rank):
         B = 1 if per == 0 else min(per * sms, B_STAGE)
         th = torch.tensor(synthetic.prior_samples(77, lo, hi, B), device=dev)
         row = {}
-        for T in (128, 256, 512, 1024):
+        for T in (128, 256, 512, 1024, 128 | g.SHAPE_WIDE, 256 | g.SHAPE_WIDE, 512 | g.SHAPE_WIDE):
             try:
                 g.swimmer_tuning(h, g.FP32C, [T] * 17)
             except RuntimeError:
@@ -610,10 +617,10 @@ def shapes_workload(args, rank, local_rank):
             ms, *_ = g.swimmer_profile(h, 2)
             g.swimmer_profile(h, 0)
             if bool((st == 0).all()):
-                row[str(T)] = round(ms * 1e3 / steps, 3)
+                row[f"{T & 0xFFFF}{'w' if T & g.SHAPE_WIDE else ''}"] = round(ms * 1e3 / steps, 3)
         rows.append({"samples": B, "samples_per_sm": B / sms, "us_per_step_by_threads": row})
     print(json.dumps({"workload": f"forward kernel, N={N_PTS}, {steps} steps, FP32C: microseconds per time step",
-                      "sms": sms, "rows": rows}), flush=True)
+                      "sms": sms, "shapes": "threads per sample, w: two-target pair units", "rows": rows}), flush=True)
     h.close()
     return 0
 

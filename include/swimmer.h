@@ -48,6 +48,11 @@ enum {
 
 enum { SWIMMER_FP64 = 0, SWIMMER_FP32C = 1 };
 
+/* Launch-shape flag (FP32C only), OR-ed into a threads-per-sample value: the pair sum takes
+ * two blocks of 32 targets per warp against one block of sources, so each source load and
+ * shuffle serves two pair evaluations. */
+#define SWIMMER_SHAPE_WIDE 0x10000
+
 /* Physical and numerical parameters (Table Tab:param fields).  POD, host memory. */
 typedef struct swimmer_config {
     int n_max;              /* largest number of points per sample (3 .. 1024) */
@@ -171,7 +176,8 @@ int forward_batch(swimmer_handle *h, int B, const double *theta, const int *n_pt
  * steps) with every admissible number of threads per sample (a
  * power of two from the smallest that covers n_max up to 1024 or the shared-memory limit;
  * the extra threads take more pair units in FP32 and split the source loop in FP64) and
- * stores the fastest in the handle.  The samples are the caller's theta (device, [n_theta][3]
+ * stores the fastest in the handle (in FP32C each threads value is timed with and without
+ * SWIMMER_SHAPE_WIDE; the stored shape may carry the flag).  The samples are the caller's theta (device, [n_theta][3]
  * FP64, rows repeated as needed) when given: batches whose runs differ in length (runs that
  * diverge and stop early) favour shapes with fewer resident samples, whose work queue
  * rebalances the SMs.  With theta NULL, b_max copies of a mid-prior swimmer are timed.
@@ -186,7 +192,8 @@ int swimmer_autotune(swimmer_handle *h, int steps, const double *theta, int n_th
  * k + 1 samples per SM (ceil(B / SMs) = k + 1; k = 16 also takes larger batches), host
  * array of 17.  0 means "use the heuristic".  Set
  * entries must be 0 or a power of two from 32 to 1024 whose shared memory fits the
- * device, else SWIMMER_E_ARG and nothing changes.  Lets a caller keep autotuned shapes
+ * device, in FP32C optionally OR-ed with SWIMMER_SHAPE_WIDE, else SWIMMER_E_ARG and
+ * nothing changes.  Lets a caller keep autotuned shapes
  * across handles or processes. */
 int swimmer_tuning(swimmer_handle *h, int precision, int *threads, int set);
 
@@ -282,6 +289,20 @@ int tmcmc_stage_shard(swimmer_handle *h, tmcmc_state *st, const double *uniforms
  * 2 depth + (1 if it is its parent's accept child), accept child, reject child} (-1 when
  * absent); *count = nodes built (fewer than M when the depth cap runs out). */
 int tmcmc_tree_template(int M, double p_accept, int depth_cap, int *nodes, int *count);
+
+/* The FP32 pair sum's work list for a sample of nb blocks of 32 points (host only, no
+ * device work; 1 <= nb <= 32).  Each unordered pair of points is evaluated once (Eq. BrV is
+ * even in the separation, so one kernel lookup serves both points).  A unit is 16 steps of
+ * a warp: lane l holds target I*32 + l (and, in a two-target unit, I2*32 + l) and at step
+ * d = d0 .. d0 + 15 meets source J*32 + (l + d) mod 32.  Packing: I | J << 8 | d0 << 16 |
+ * I2 << 24, I2 = 255 for one target block.  A diagonal unit (I = J, d0 = 1) takes
+ * d = 1 .. 16, lanes < 16 only at d = 16; an off-diagonal block pair is two units
+ * (d0 = 0, 16).  wide = 0: nb diagonal units, then every block pair {I, J} as one-target
+ * units in circulant order.  wide = 1: block pairs grouped two by two around a shared
+ * source block J ({I, J} with {I2, J}), at most one left as a one-target pair, then the
+ * diagonal units.  out: host, at least nb^2 unsigned; *count = units written.
+ * SWIMMER_E_ARG on bad arguments. */
+int swimmer_pair_units(int nb, int wide, unsigned *out, int *count);
 
 /* Stage pieces, exposed for testing (Algorithm 1 'Analyze' and 'Resample'):
  * tmcmc_analyze: from loglik[B] (device), theta[B][P] (device, P = n_params) and q (host)

@@ -54,6 +54,7 @@ SIGNATURES = [
     ("tmcmc_stage", c_int, [c_void_p, P(TmcmcStateC), c_void_p, c_void_p, c_int, c_void_p]),
     ("tmcmc_stage_shard", c_int, [c_void_p, P(TmcmcStateC), c_void_p, c_void_p, c_int, c_int, c_int, c_void_p]),
     ("tmcmc_tree_template", c_int, [c_int, c_double, c_int, c_void_p, c_void_p]),
+    ("swimmer_pair_units", c_int, [c_int, c_int, c_void_p, c_void_p]),
     ("tmcmc_analyze", c_int, [c_void_p, c_int, c_void_p, c_void_p, c_double, c_void_p, c_void_p, c_void_p]),
     ("tmcmc_resample", c_int, [c_void_p, c_int, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     ("mlp_workspace_bytes", ctypes.c_size_t, [c_int]),

@@ -204,6 +204,7 @@ extern "C" int swimmer_init(const swimmer_config *cfg, swimmer_handle **out) {
         }
     }
     rc = gl_init();
+    if (!rc) rc = upload_pair_units(h);
     if (rc) {
         swimmer_destroy(h);
         return rc;
@@ -220,7 +221,7 @@ extern "C" int swimmer_destroy(swimmer_handle *h) {
                     h->idx, h->counts, h->chain_id, h->chain_off, h->chain_len, h->aux,
                     h->cur_theta, h->cur_ll, h->cur_sl, h->prop_theta, h->prop_ll, h->prop_sl,
                     h->out_theta, h->out_ll, h->out_sl, h->prop_status, h->live, h->chain_pos, h->tmpl, h->cum, h->info, h->work, h->run_work,
-                    h->surr_norm, h->surr_params, h->surr_x, h->surr_y, h->surr_ws};
+                    h->surr_norm, h->surr_params, h->surr_x, h->surr_y, h->surr_ws, h->units};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (h->host_pinned) cudaFreeHost(h->host_pinned);
@@ -282,8 +283,11 @@ extern "C" int swimmer_tuning(swimmer_handle *h, int precision, int *threads, in
         return 0;
     }
     for (int k = 0; k < 17; ++k) {
-        const int t = threads[k];
-        ARG_CHECK(t == 0 || (t >= forward_min_threads(h, precision) && t <= 1024 && (t & (t - 1)) == 0),
+        const int t = threads[k] & SHAPE_THREADS;
+        ARG_CHECK((threads[k] & ~(SHAPE_THREADS | SHAPE_WIDE)) == 0 &&
+                      (precision != SWIMMER_FP64 || !(threads[k] & SHAPE_WIDE)),
+                  "threads[%d] = %d has flags other than SWIMMER_SHAPE_WIDE (FP32C only)", k, threads[k]);
+        ARG_CHECK(threads[k] == 0 || (t >= forward_min_threads(h, precision) && t <= 1024 && (t & (t - 1)) == 0),
                   "threads[%d] = %d is not 0 or a power of two in [%d, 1024]", k, t, forward_min_threads(h, precision));
         ARG_CHECK(t == 0 || forward_fits(h, t, precision), "threads[%d] = %d needs more shared memory than the device has", k, t);
     }
@@ -337,17 +341,20 @@ extern "C" int swimmer_autotune(swimmer_handle *h, int steps, const double *thet
         int bestT = T0;
         for (int T = T0; T <= 1024 && !rc; T <<= 1) {
             if (!forward_fits(h, T, prec)) break;
-            float ms = 0.f;
-            for (int rep = 0; rep < 2 && !rc; ++rep) {  // first run warms up
-                cudaEventRecord(e0, 0);
-                rc = launch_forward(h, B, nullptr, 0.0, nullptr, nullptr, nullptr, status, prec, 0, T);
-                cudaEventRecord(e1, 0);
-                cudaEventSynchronize(e1);
-                cudaEventElapsedTime(&ms, e0, e1);
-            }
-            if (ms < best) {
-                best = ms;
-                bestT = T;
+            for (int wide = 0; wide <= (prec == SWIMMER_FP64 ? 0 : 1) && !rc; ++wide) {
+                const int shape = T | (wide ? SHAPE_WIDE : 0);
+                float ms = 0.f;
+                for (int rep = 0; rep < 2 && !rc; ++rep) {  // first run warms up
+                    cudaEventRecord(e0, 0);
+                    rc = launch_forward(h, B, nullptr, 0.0, nullptr, nullptr, nullptr, status, prec, 0, shape);
+                    cudaEventRecord(e1, 0);
+                    cudaEventSynchronize(e1);
+                    cudaEventElapsedTime(&ms, e0, e1);
+                }
+                if (ms < best) {
+                    best = ms;
+                    bestT = shape;
+                }
             }
         }
         h->tune_threads[prec == SWIMMER_FP64 ? 0 : 1][tune_bucket(h, B)] = bestT;

@@ -32,6 +32,19 @@ constexpr int K1_SCRATCH = 2 * NODES_MAX + TAIL_MAX;  // doubles of table-build 
 constexpr double R_MAX_OVER_L = 1.25;  // table reach in units of the flagellum length
 constexpr double STRETCH_MAX = 0.20;   // segment stretch beyond which a run counts as diverged
 constexpr int N_PTS_MAX = 1024;
+// FP32 pair units (see forward.cu): one list per block count nb = ceil(n / 32) and per
+// decomposition (0: one target block per unit, 1: two target blocks sharing a source
+// block); the handle's device buffer starts with the lists' offsets [2][UNIT_NB_MAX + 1]
+constexpr int UNIT_NB_MAX = N_PTS_MAX / 32;
+constexpr int UNIT_HDR = 2 * (UNIT_NB_MAX + 1);
+constexpr int SHAPE_WIDE = SWIMMER_SHAPE_WIDE;  // launch-shape flag: two-target pair units
+constexpr int SHAPE_THREADS = SHAPE_WIDE - 1;
+// units in a list: nb diagonal units of 16 steps plus, per off-diagonal block pair, two
+// units of 16 steps (one target block) or, two block pairs at a time, two units (two)
+__host__ __device__ inline int unit_count(int nb, int wide) {
+    const int e = nb * (nb - 1) / 2;
+    return wide ? nb + 2 * ((e + 1) / 2) : nb * nb;
+}
 constexpr int P_THETA = 3;
 constexpr double X_MAX = 600.0;        // largest alpha * r the Bessel evaluations accept
 
@@ -80,7 +93,8 @@ struct swimmer_handle {
                                // kernel, [1] those a one-step-at-a-time TMCMC would also run
     unsigned long long *run_work;  // [b_max] pair evaluations of each run of the last launch
     // autotuned threads per sample for batch sizes in [2^k, 2^(k+1)), per precision; 0 = heuristic
-    int tune_threads[2][17];  // [FP64, FP32C][samples per SM - 1, capped at 16]
+    int tune_threads[2][17];  // [FP64, FP32C][samples per SM - 1, capped at 16]; launch shapes
+    unsigned *units;          // device: FP32 pair-unit lists (UNIT_HDR offsets, then the lists)
     int device;
     int num_sms;
     int max_smem;  // opt-in shared memory per block (bytes)
@@ -153,6 +167,7 @@ int tune_bucket(const swimmer_handle *h, int B);
 int forward_min_threads(const swimmer_handle *h, int precision);
 bool forward_fits(const swimmer_handle *h, int threads, int precision);
 int forward_slots(const swimmer_handle *h, int precision);
+int upload_pair_units(swimmer_handle *h);
 int launch_kernel_eval(swimmer_handle *h, int m, const double *r, double *g1, double *g2,
                        int precision, cudaStream_t s);
 int gl_init();

@@ -34,6 +34,9 @@
 // more than ds in one step, or a segment stretches beyond STRETCH_MAX.
 #include <math.h>
 
+#include <algorithm>
+#include <vector>
+
 #include "common.cuh"
 #include "table_eval.cuh"
 
@@ -67,6 +70,8 @@ struct FwdArgs {
     int n_max;
     int threads;
     int tab_panels;  // panels of the shared-memory table region (handle's octaves x panels/octave)
+    const unsigned *units;  // FP32 pair-unit lists (offsets header, then the lists)
+    int wide;               // FP32: two-target pair units
 };
 
 struct __align__(32) dbl4 {
@@ -204,7 +209,8 @@ __host__ __device__ size_t state_bytes(int n_max, int threads) {
     return align32(16 * (size_t)n_max) + 1024 * nbm + align32(forces > part ? forces : part);
 }
 
-// FP32: the sample's pair units (I | J << 8 | d0 << 16), ceil(n_max/32)^2 ints after the table
+// FP32: the sample's pair units (I | J << 8 | d0 << 16 | I2 << 24), at most ceil(n_max/32)^2
+// ints after the table
 template <bool F64>
 __host__ __device__ size_t smem_bytes(int n_max, int P, int threads) {
     const size_t nbm = (n_max + 31) / 32;
@@ -290,6 +296,50 @@ __device__ __forceinline__ void pair_unit(const float4 *__restrict__ s4, const f
         pa.y += ay;
         mypart[(Jb << 5) + lane] = pa;
     }
+}
+
+// Two-target pair unit: lane l holds targets I*32 + l and I2*32 + l (I, I2 and J distinct
+// blocks) and at step d = d0 .. d0+15 meets source J*32 + (l + d) mod 32, so one source load
+// and one rotation of the source-side sums serve two pair evaluations.
+__device__ __forceinline__ void pair_unit_wide(const float4 *__restrict__ s4, const float4 *__restrict__ t1,
+                                               const float2 *__restrict__ t2, int pmax, int lane, int I, int I2,
+                                               int Jb, int d0, float2 *__restrict__ mypart) {
+    const int nxt = (lane + 1) & 31;
+    const float4 m1 = s4[(I << 6) + lane];
+    const float4 m2 = s4[(I2 << 6) + lane];
+    const float4 *sp = s4 + (Jb << 6) + lane + d0;
+    float v1x = 0.f, v1y = 0.f, v2x = 0.f, v2y = 0.f, ax = 0.f, ay = 0.f;
+#pragma unroll
+    for (int s = 0; s < 16; ++s) {
+        const float4 q = sp[s];
+        const Mob M1 = pair_mob(t1, t2, pmax, m1.x - q.x, m1.y - q.y, 1.f);
+        const Mob M2 = pair_mob(t1, t2, pmax, m2.x - q.x, m2.y - q.y, 1.f);
+        v1x = fmaf(M1.m11, q.z, fmaf(M1.m12, q.w, v1x));
+        v1y = fmaf(M1.m12, q.z, fmaf(M1.m22, q.w, v1y));
+        v2x = fmaf(M2.m11, q.z, fmaf(M2.m12, q.w, v2x));
+        v2y = fmaf(M2.m12, q.z, fmaf(M2.m22, q.w, v2y));
+        ax = fmaf(M1.m11, m1.z, fmaf(M1.m12, m1.w, ax));
+        ay = fmaf(M1.m12, m1.z, fmaf(M1.m22, m1.w, ay));
+        ax = fmaf(M2.m11, m2.z, fmaf(M2.m12, m2.w, ax));
+        ay = fmaf(M2.m12, m2.z, fmaf(M2.m22, m2.w, ay));
+        ax = __shfl_sync(0xffffffffu, ax, nxt);
+        ay = __shfl_sync(0xffffffffu, ay, nxt);
+    }
+    const int from = (lane - d0 - 16) & 31;
+    ax = __shfl_sync(0xffffffffu, ax, from);
+    ay = __shfl_sync(0xffffffffu, ay, from);
+    float2 p1 = mypart[(I << 5) + lane];
+    p1.x += v1x;
+    p1.y += v1y;
+    mypart[(I << 5) + lane] = p1;
+    float2 p2 = mypart[(I2 << 5) + lane];
+    p2.x += v2x;
+    p2.y += v2y;
+    mypart[(I2 << 5) + lane] = p2;
+    float2 pa = mypart[(Jb << 5) + lane];
+    pa.x += ax;
+    pa.y += ay;
+    mypart[(Jb << 5) + lane] = pa;
 }
 
 // observations computed by warp 0 after a step (head-centre velocities, two-swimmer
@@ -394,31 +444,11 @@ __global__ void __launch_bounds__(1024) forward_kernel(FwdArgs a) {
                 t[i] = g[i];
                 tb[i] = gb[i];
             }
-            // pair units: diagonal blocks first (d = 1..16), then each off-diagonal block
-            // pair as two units (d = 0..15, 16..31) in circulant order: {r, r + k} for
-            // k = 1 .. (nb - 1) / 2, then {r, r + nb / 2} for r < nb / 2 (even nb)
+            // the sample's pair units, from the handle's list for its block count
             const int nbs = (n + 31) >> 5;
-            int *units = (int *)(tabraw + table_bytes<F64>(P));
-            for (int un = tid; un < nbs * nbs; un += T) {
-                int I, Jb, d0;
-                if (un < nbs) {
-                    I = Jb = un;
-                    d0 = 1;
-                } else {
-                    const int v = (un - nbs) >> 1, half = (nbs - 1) >> 1, full = nbs * half;
-                    d0 = ((un - nbs) & 1) << 4;
-                    if (v < full) {
-                        const int kk = v / nbs;
-                        I = v - kk * nbs;
-                        Jb = I + kk + 1;
-                        if (Jb >= nbs) Jb -= nbs;
-                    } else {
-                        I = v - full;
-                        Jb = I + (nbs >> 1);
-                    }
-                }
-                units[un] = I | (Jb << 8) | (d0 << 16);
-            }
+            const unsigned *ul = a.units + UNIT_HDR + a.units[a.wide * (UNIT_NB_MAX + 1) + nbs - 1];
+            unsigned *units = (unsigned *)(tabraw + table_bytes<F64>(P));
+            for (int un = tid; un < unit_count(nbs, a.wide); un += T) units[un] = ul[un];
         }
         // ---- initial straight filament X_k = (k ds, 0), stored relative to (L/2, 0); the
         //      head circle's centre H_r + dN to the right of the proximal point, head point m
@@ -495,9 +525,9 @@ __global__ void __launch_bounds__(1024) forward_kernel(FwdArgs a) {
         const int slot = tid / S, split = tid % S;
         const int tgt = slot;  // one target per slot
         const bool owner = (split == 0) && (tgt < n);
-        // FP32 pair sum: ceil(n/32)^2 units of 16 steps over the pair warps
-        const int nb = (n + 31) >> 5, n_units = nb * nb;
-        const int n_pw = pair_warps(n_max, T);
+        // FP32 pair sum: the sample's units of 16 steps over the pair warps
+        const int nb = (n + 31) >> 5, n_units = unit_count(nb, a.wide);
+        const int n_pw = min(pair_warps(n_max, T), unit_count(nbm, a.wide));
         // the thread that keeps the log-likelihood: thread 0 for head-centre velocities (one
         // warp reduces the head after each observation step), else the one that updates the
         // proximal flagellum point nf - 1 (the observed point)
@@ -797,18 +827,24 @@ __global__ void __launch_bounds__(1024) forward_kernel(FwdArgs a) {
                 // per step, so lane l always holds the sum of the source it meets.
                 // Diagonal units (I = J) run d = 1 .. 16 (at d = 16 only lanes < 16, since
                 // lanes l and l + 16 meet the same pair); off-diagonal blocks run d = 0 .. 31
-                // as two units.  Each warp adds its units' sums into its own partial array,
-                // in a fixed order, so the result does not depend on scheduling.
+                // as two units.  A two-target unit (wide launch shape) walks the block pairs
+                // {I, J} and {I2, J} together, sharing the source loads and rotations.  Each
+                // warp adds its units' sums into its own partial array, in a fixed order, so
+                // the result does not depend on scheduling.
                 const float4 *s4 = (const float4 *)src;
                 const float4 *t1 = (const float4 *)tabraw;
                 const float2 *t2 = (const float2 *)(t1 + P);
                 const int warp = tid >> 5;
                 float2 *mypart = part + warp * (nb << 5);
                 for (int k = lane; k < (nb << 5); k += 32) mypart[k] = make_float2(0.f, 0.f);
-                const int *units = (const int *)(tabraw + table_bytes<F64>(P));
+                const unsigned *units = (const unsigned *)(tabraw + table_bytes<F64>(P));
                 for (int un = warp; un < n_units; un += n_pw) {
-                    const int pk = units[un];
-                    pair_unit(s4, t1, t2, npan - 1, lane, pk & 255, (pk >> 8) & 255, pk >> 16, mypart);
+                    const unsigned pk = units[un];
+                    const int I = pk & 255, Jb = (pk >> 8) & 255, d0 = (pk >> 16) & 255, I2 = pk >> 24;
+                    if (I2 == 255)
+                        pair_unit(s4, t1, t2, npan - 1, lane, I, Jb, d0, mypart);
+                    else
+                        pair_unit_wide(s4, t1, t2, npan - 1, lane, I, I2, Jb, d0, mypart);
                 }
             }
             if (!F64) __syncthreads();
@@ -974,6 +1010,85 @@ ForwardKernel forward_kernel_for(bool f64, const swimmer_config &c) {
 
 }  // namespace
 
+// The pair-unit list of nb blocks (packing and order as swimmer_pair_units documents).
+// Two-target lists group the off-diagonal block pairs (edges of the complete graph on the
+// blocks) two by two around a shared block: blocks are visited from the last down, each
+// takes its edges to lower blocks plus those handed to it, and when their number is odd it
+// hands one edge to a lower block whose own count would otherwise be odd, so at most one
+// edge stays alone, at block 0.
+static std::vector<unsigned> build_pair_units(int nb, int wide) {
+    auto pack = [](int I, int J, int d0, int I2) {
+        return (unsigned)I | ((unsigned)J << 8) | ((unsigned)d0 << 16) | ((unsigned)I2 << 24);
+    };
+    std::vector<unsigned> out;
+    if (!wide) {
+        for (int i = 0; i < nb; ++i) out.push_back(pack(i, i, 1, 255));
+        // off-diagonal block pairs in circulant order: {r, r + k} for k = 1 .. (nb - 1) / 2,
+        // then {r, r + nb / 2} for r < nb / 2 (even nb)
+        for (int k = 1; k <= (nb - 1) / 2; ++k)
+            for (int r = 0; r < nb; ++r)
+                for (int d0 = 0; d0 <= 16; d0 += 16) out.push_back(pack(r, (r + k) % nb, d0, 255));
+        if (nb % 2 == 0)
+            for (int r = 0; r < nb / 2; ++r)
+                for (int d0 = 0; d0 <= 16; d0 += 16) out.push_back(pack(r, r + nb / 2, d0, 255));
+        return out;
+    }
+    std::vector<std::vector<int>> handed(nb);
+    std::vector<unsigned> single;
+    for (int J = nb - 1; J >= 0; --J) {
+        std::vector<int> other;  // the other blocks of the edges grouped at J
+        for (int i = 0; i < J; ++i) other.push_back(i);
+        for (int x : handed[J]) other.push_back(x);
+        if (other.size() % 2 == 1 && J > 0) {
+            int pick = 0;
+            for (int i = J - 1; i >= 0; --i)
+                if ((i + handed[i].size()) % 2 == 1) {
+                    pick = i;
+                    break;
+                }
+            other.erase(std::find(other.begin(), other.end(), pick));
+            handed[pick].push_back(J);
+        }
+        for (size_t k = 0; k + 1 < other.size(); k += 2)
+            for (int d0 = 0; d0 <= 16; d0 += 16) out.push_back(pack(other[k], J, d0, other[k + 1]));
+        if (other.size() % 2 == 1)
+            for (int d0 = 0; d0 <= 16; d0 += 16) single.push_back(pack(other.back(), J, d0, 255));
+    }
+    out.insert(out.end(), single.begin(), single.end());
+    for (int i = 0; i < nb; ++i) out.push_back(pack(i, i, 1, 255));
+    return out;
+}
+
+extern "C" int swimmer_pair_units(int nb, int wide, unsigned *out, int *count) {
+    ARG_CHECK(nb >= 1 && nb <= UNIT_NB_MAX, "nb must be in [1, %d]", UNIT_NB_MAX);
+    ARG_CHECK(wide == 0 || wide == 1, "wide must be 0 or 1");
+    ARG_CHECK(out != nullptr && count != nullptr, "out or count is NULL");
+    const std::vector<unsigned> u = build_pair_units(nb, wide);
+    std::copy(u.begin(), u.end(), out);
+    *count = (int)u.size();
+    return 0;
+}
+
+// Device copy of both decompositions for every block count up to the handle's n_max.
+int upload_pair_units(swimmer_handle *h) {
+    const int nbm = (h->cfg.n_max + 31) / 32;
+    std::vector<unsigned> all(UNIT_HDR, 0u), body;
+    for (int w = 0; w < 2; ++w)
+        for (int nb = 1; nb <= nbm; ++nb) {
+            const std::vector<unsigned> u = build_pair_units(nb, w);
+            if ((int)u.size() != unit_count(nb, w)) {
+                set_error("pair-unit list of %d blocks has %zu units", nb, u.size());
+                return SWIMMER_E_ARG;
+            }
+            all[w * (UNIT_NB_MAX + 1) + nb - 1] = (unsigned)body.size();
+            body.insert(body.end(), u.begin(), u.end());
+        }
+    all.insert(all.end(), body.begin(), body.end());
+    CUDA_TRY(cudaMalloc((void **)&h->units, sizeof(unsigned) * all.size()));
+    CUDA_TRY(cudaMemcpy(h->units, all.data(), sizeof(unsigned) * all.size(), cudaMemcpyHostToDevice));
+    return 0;
+}
+
 // Threads per sample: at least one per target (FP64) or one warp per pair unit (FP32);
 // more when the batch is too small to fill the GPU, so that the per-step latency of a lone
 // sample shrinks, as long as the shared memory fits.  The autotuned choice wins.
@@ -1021,8 +1136,9 @@ int forward_min_threads(const swimmer_handle *h, int precision) {
 int forward_threads(const swimmer_handle *h, int B, int precision) {
     const int bucket = tune_bucket(h, B);
     const int tuned = h->tune_threads[precision == SWIMMER_FP64 ? 0 : 1][bucket];
+    const int tT = tuned & SHAPE_THREADS;
     int T = forward_min_threads(h, precision);
-    if (tuned >= T && tuned <= 1024 && forward_fits(h, tuned, precision)) return tuned;
+    if (tT >= T && tT <= 1024 && forward_fits(h, tT, precision)) return tuned;
     int cap = 1024;
     if (precision != SWIMMER_FP64) {  // warps beyond the pair units only help the O(N) phases
         const int nbm = (h->cfg.n_max + 31) / 32;
@@ -1070,9 +1186,12 @@ int launch_forward(swimmer_handle *h, int B, const double *obs, double sigma, do
     a.run_work = h->run_work;
     a.speculative = speculative;
     a.n_max = h->cfg.n_max;
-    int T = threads_override > 0 ? threads_override : forward_threads(h, B, precision);
+    const int shape = threads_override > 0 ? threads_override : forward_threads(h, B, precision);
+    const int T = shape & SHAPE_THREADS;
     a.threads = T;
     const bool f64 = precision == SWIMMER_FP64;
+    a.units = h->units;
+    a.wide = !f64 && (shape & SHAPE_WIDE) ? 1 : 0;
     a.tab_panels = handle_octaves(h) * (f64 ? F64_SUB : F32_SUB);
     size_t smem = f64 ? smem_bytes<true>(a.n_max, a.tab_panels, T) : smem_bytes<false>(a.n_max, a.tab_panels, T);
     auto kern = forward_kernel_for(f64, h->cfg);

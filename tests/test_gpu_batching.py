@@ -34,10 +34,13 @@ def _batch(B, seed=4):
     return th, ns
 
 
-@pytest.mark.parametrize("precision,tol", [(0, 1e-10), (1, 1e-3)])
-def test_uneven_batch_matches_oracle(precision, tol):
+@pytest.mark.parametrize("precision,tol,shape", [(0, 1e-10, 0), (1, 1e-3, 0), (1, 1e-3, 128 | g.SHAPE_WIDE)])
+def test_uneven_batch_matches_oracle(precision, tol, shape):
+    # N in {6, 12, 24, 48}: one and two blocks of 32 (a lone off-diagonal block pair)
     th, ns = _batch(12)
     h = g.swimmer_init(_cfg(16, precision))
+    if shape:
+        g.swimmer_tuning(h, precision, [shape] * 17)
     traj, speed, status = g.forward_batch(h, torch.tensor(th, device=DEV), torch.tensor(ns, device=DEV))
     torch.cuda.synchronize()
     assert np.all(status.cpu().numpy() == 0)
@@ -89,7 +92,9 @@ def test_launch_shapes_agree_and_tuning_table_round_trips():
     th = torch.tensor(synthetic.prior_samples(9, (0.2, -0.5, 0.05), (8.0, 0.5, 0.15), 40), device=DEV)
     ns = torch.tensor(synthetic.choice_n(9, [40, 70, 96], 40).astype(np.int32), device=DEV)
     outs = {}
-    for T in (128, 256, 512):
+    W = g.SHAPE_WIDE
+    shapes = (128, 256, 512, 128 | W, 256 | W, 512 | W)
+    for T in shapes:
         g.swimmer_tuning(h, g.FP32C, [T] * 17)
         assert g.swimmer_tuning(h, g.FP32C) == [T] * 17
         traj, speed, st = g.forward_batch(h, th, ns)
@@ -97,14 +102,21 @@ def test_launch_shapes_agree_and_tuning_table_round_trips():
     ref_traj, ref_st = outs[128]
     assert np.all(ref_st == 0)
     scale = np.max(np.abs(ref_traj))
-    for T in (256, 512):
+    for T in shapes[1:]:
         # only the grouping of the FP32 partial sums changes with the number of pair warps
+        # and with the grouping of block pairs into units
         assert np.array_equal(outs[T][1], ref_st)
         assert np.max(np.abs(outs[T][0] - ref_traj)) <= 1e-5 * scale
     with pytest.raises(RuntimeError):
         g.swimmer_tuning(h, g.FP32C, [96] * 17)  # not a power of two
+    with pytest.raises(RuntimeError):
+        g.swimmer_tuning(h, g.FP32C, [128 | 0x20000] * 17)  # unknown flag
+    h64 = g.swimmer_init(replace(cfg, precision=g.FP64))
+    with pytest.raises(RuntimeError):
+        g.swimmer_tuning(h64, g.FP64, [128 | W] * 17)  # two-target units are FP32 only
+    h64.close()
     tuned = g.swimmer_autotune(h, steps=20)
-    assert set(tuned) and all(v in (128, 256, 512, 1024) for v in tuned.values())
+    assert set(tuned) and all(v & ~W in (128, 256, 512, 1024) for v in tuned.values())
     table = g.swimmer_tuning(h, g.FP32C)
     assert table[0] == tuned[1]
     h.close()

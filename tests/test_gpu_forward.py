@@ -241,7 +241,7 @@ def workload_batch():
     return th, _oracle_batch(WORKLOAD, [tuple(th[i]) for i in PICK])
 
 
-@pytest.mark.parametrize("threads", [128, 256, 512])
+@pytest.mark.parametrize("threads", [128, 256, 512, 128 | g.SHAPE_WIDE, 256 | g.SHAPE_WIDE])
 def test_tmcmc_workload_full_batch_sampled(threads, workload_batch):
     # the TMCMC workload's sizes in the launch configurations its autotuner picks: 1024 samples
     # of N = 128 (four blocks of 32: diagonal, circulant and opposite block pairs) in one
@@ -266,13 +266,16 @@ def test_tmcmc_workload_full_batch_sampled(threads, workload_batch):
 
 
 def test_tmcmc_workload_velocities_n128():
-    # per-step head velocities at N = 128 (1e-4 relative), FP32 and FP64 kernels
+    # per-step head velocities at N = 128 (1e-4 relative), FP32 kernel with one- and
+    # two-target pair units, and the FP64 kernel
     p = sw.SwimmerParams(n=128, dt=1e-4 / 64, steps=200, obs_every=1, k_t=1e3)
     thetas = [(1.0, 0.0, 0.1), (6.5, -0.6, 0.17), (0.0, 0.1, 0.06)]
     ps, obs, xc, st = _oracle_batch(p, thetas)
     x0 = np.array([[p.length, 0.0]])
-    for prec, tol in [(g.FP32C, 1e-4), (g.FP64, 1e-9)]:
+    for prec, tol, shape in [(g.FP32C, 1e-4, 0), (g.FP32C, 1e-4, 128 | g.SHAPE_WIDE), (g.FP64, 1e-9, 0)]:
         h = g.swimmer_init(_cfg(p, 4, prec))
+        if shape:
+            g.swimmer_tuning(h, prec, [shape] * 17)
         traj, _, status = g.forward_batch(h, _theta(ps))
         torch.cuda.synchronize()
         for b in range(len(ps)):
