@@ -154,6 +154,7 @@ extern "C" int swimmer_init(const swimmer_config *cfg, swimmer_handle **out) {
     CUDA_TRY(cudaGetDevice(&h->device));
     CUDA_TRY(cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device));
     CUDA_TRY(cudaDeviceGetAttribute(&h->max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device));
+    CUDA_TRY(cudaDeviceGetAttribute(&h->regs_per_sm, cudaDevAttrMaxRegistersPerMultiprocessor, h->device));
     const int B = cfg->b_max;
     ALLOC(h->tab64, (size_t)B * TAB64_STRIDE);
     ALLOC(h->k1_scratch, (size_t)B * K1_SCRATCH);

@@ -98,6 +98,7 @@ struct swimmer_handle {
     int device;
     int num_sms;
     int max_smem;  // opt-in shared memory per block (bytes)
+    int regs_per_sm;  // 32-bit registers per SM
     // per-sample workspace (b_max samples)
     double *tab64;          // [b_max][TAB64_STRIDE]
     double *k1_scratch;     // [b_max][K1_SCRATCH] interval integrals of the table build

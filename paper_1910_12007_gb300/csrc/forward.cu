@@ -370,9 +370,12 @@ __device__ __forceinline__ void head_centre(const double *sx, const double *sy, 
 }
 
 // MODEL 0: the flagellum; 1: the full sperm model (head points and neck); 2: two sperm models
-// coupled by the fluid.  Code for models a launch does not run compiles out.
-template <bool F64, int MODEL>
-__global__ void __launch_bounds__(1024) forward_kernel(FwdArgs a) {
+// coupled by the fluid.  Code for models a launch does not run compiles out.  BIG: compiled
+// for at most 512 threads and one CTA per SM (up to 128 registers a thread), for launches
+// whose shared memory already holds them to that few threads per SM (large N): the pair
+// loop then keeps more loads in flight.
+template <bool F64, int MODEL, bool BIG = false>
+__global__ void __launch_bounds__(BIG ? 512 : 1024, 1) forward_kernel(FwdArgs a) {
     constexpr bool HEAD = MODEL >= 1, TWO = MODEL == 2;
     typedef typename Types<F64>::R R;
     typedef typename Types<F64>::R4 R4;
@@ -1002,9 +1005,13 @@ __global__ void __launch_bounds__(1024) forward_kernel(FwdArgs a) {
 
 typedef void (*ForwardKernel)(FwdArgs);
 
-ForwardKernel forward_kernel_for(bool f64, const swimmer_config &c) {
+ForwardKernel forward_kernel_for(bool f64, const swimmer_config &c, bool big = false) {
     const int model = c.n_swimmers == 2 ? 2 : c.n_head > 0 ? 1 : 0;
     if (f64) return model == 2 ? forward_kernel<true, 2> : model == 1 ? forward_kernel<true, 1> : forward_kernel<true, 0>;
+    if (big)
+        return model == 2 ? forward_kernel<false, 2, true>
+               : model == 1 ? forward_kernel<false, 1, true>
+                            : forward_kernel<false, 0, true>;
     return model == 2 ? forward_kernel<false, 2> : model == 1 ? forward_kernel<false, 1> : forward_kernel<false, 0>;
 }
 
@@ -1200,6 +1207,17 @@ int launch_forward(swimmer_handle *h, int B, const double *obs, double sigma, do
                                   cudaSharedmemCarveoutMaxShared));
     int per_sm = 0;
     CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, T, smem));
+    // FP32 with shared memory for so few threads per SM that each could hold 128 registers:
+    // the instantiation compiled for that register budget (same CTAs per SM)
+    if (!f64 && T <= 512 && per_sm >= 1 && (long long)per_sm * T * 128 <= h->regs_per_sm) {
+        auto big = forward_kernel_for(f64, h->cfg, true);
+        int per_big = 0;
+        CUDA_TRY(cudaFuncSetAttribute(big, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        CUDA_TRY(cudaFuncSetAttribute(big, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                      cudaSharedmemCarveoutMaxShared));
+        CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_big, big, T, smem));
+        if (per_big >= per_sm) kern = big;
+    }
     if (per_sm < 1) {
         set_error("forward kernel does not fit on an SM (threads %d, smem %zu)", T, smem);
         return SWIMMER_E_CUDA;

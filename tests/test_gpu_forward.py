@@ -284,3 +284,67 @@ def test_tmcmc_workload_velocities_n128():
             err = np.max(np.linalg.norm(vg - vr, axis=1)) / np.max(np.linalg.norm(vr, axis=1))
             assert err < tol, (prec, b, err)
         h.close()
+
+
+# ---------------------------------------------------------------------------------
+# full-size workloads: the large sweep (256 x N = 1024, alpha in [0, 50]) and the uneven
+# batch (4096 samples, N in {64, 128, 256, 512} at fixed ds) in the launch shapes their
+# autotuner chooses from; sampled runs against the oracle, per-step head velocities
+# ---------------------------------------------------------------------------------
+LARGE = sw.SwimmerParams(n=1024, dt=1e-4 / 2 ** 15, steps=100, obs_every=1, k_t=1e3)
+LARGE_PICK = [0, 97, 255]
+
+
+@pytest.fixture(scope="module")
+def large_batch():
+    th = synthetic.prior_samples(3000, (0.0, -1.0, 0.05), (50.0, 0.0, 0.2), 256)
+    return th, _oracle_batch(LARGE, [tuple(th[i]) for i in LARGE_PICK])
+
+
+def _velocity_error(traj_b, obs_b, x0, dt):
+    vr = np.diff(np.concatenate([x0, obs_b]), axis=0) / dt
+    vg = np.diff(np.concatenate([x0, traj_b]), axis=0) / dt
+    return np.max(np.linalg.norm(vg - vr, axis=1)) / np.max(np.linalg.norm(vr, axis=1))
+
+
+@pytest.mark.parametrize("shape", [512 | g.SHAPE_WIDE, 512, 256 | g.SHAPE_WIDE, 128])
+def test_large_sweep_sampled(shape, large_batch):
+    # 512 threads: one CTA per SM, the 128-register instantiation; 128: the 64-register one
+    th, (ps, obs, xc, st) = large_batch
+    assert np.all(st == 0)
+    p = LARGE
+    h = g.swimmer_init(g.SwimmerConfig(n_max=1024, b_max=256, dt=p.dt, steps=p.steps, obs_every=1, k_t=p.k_t,
+                                       precision=g.FP32C))
+    g.swimmer_tuning(h, g.FP32C, [shape] * 17)
+    traj, _, status = g.forward_batch(h, torch.tensor(th, device=DEV))
+    torch.cuda.synchronize()
+    traj = traj.cpu().numpy()
+    x0 = np.array([[p.length, 0.0]])
+    for k, i in enumerate(LARGE_PICK):
+        assert status[i].item() == 0
+        err = _velocity_error(traj[i], obs[k], x0, p.dt)
+        assert err < 1e-4, (shape, i, err)
+    h.close()
+
+
+def test_uneven_full_batch_sampled():
+    # 4096 samples, fixed ds = 1/255 (L = (N - 1) ds), longest first in one launch, autotuned
+    ds, B, steps = 1.0 / 255, 4096, 100
+    ns = synthetic.choice_n(2000, [64, 128, 256, 512], B).astype(np.int32)
+    th = synthetic.prior_samples(2000, (0.0, -1.0, 0.05), (10.0, 0.0, 0.2), B)
+    h = g.swimmer_init(g.SwimmerConfig(n_max=512, b_max=B, ds_fixed=ds, dt=1e-4 / 512, steps=steps, obs_every=1,
+                                       precision=g.FP32C))
+    tuned = g.swimmer_autotune(h, steps=20)
+    traj, _, status = g.forward_batch(h, torch.tensor(th, device=DEV), torch.tensor(ns, device=DEV))
+    torch.cuda.synchronize()
+    traj = traj.cpu().numpy()
+    pick = [int(np.nonzero(ns == n)[0][0]) for n in (64, 128, 256, 512)] + [B - 1]
+    base = sw.SwimmerParams(n=512, dt=1e-4 / 512, steps=steps, obs_every=1)
+    ps = [replace(base.with_theta(tuple(th[i])), n=int(ns[i]), length=(int(ns[i]) - 1) * ds) for i in pick]
+    obs, _, _, st = sw.run_c_batch(ps)
+    assert np.all(st == 0)
+    for k, i in enumerate(pick):
+        assert status[i].item() == 0
+        err = _velocity_error(traj[i], obs[k], np.array([[ps[k].length, 0.0]]), base.dt)
+        assert err < 1e-4, (i, int(ns[i]), tuned, err)
+    h.close()
