@@ -215,7 +215,7 @@ def main():
                          "(e.g. 128w); default: the untuned heuristic")
     ap.add_argument("--workload", default="tmcmc",
                     choices=["tmcmc", "uneven", "large", "surrogate", "shapes", "sperm", "sperm-tmcmc", "two-sperm",
-                             "flow"],
+                             "flow", "posterior"],
                     help="tmcmc (default): TMCMC stages, 1024 samples, N=128; uneven: 4096 samples with "
                          "N in {64,128,256,512} in one graph-captured persistent launch; large: 256 samples "
                          "x N=1024 x 4e4 steps; surrogate: delayed-acceptance vs plain TMCMC, 4096 samples/stage; "
@@ -223,7 +223,8 @@ def main():
                          "1024 full sperm models (flagellum 50 + head 24 points, Table Tab:param) x one beat; "
                          "sperm-tmcmc: a whole TMCMC run on the full sperm model, head-centre velocities; "
                          "two-sperm: 1024 pairs of sperm models 0.5 apart (148 points) x one beat, distances; "
-                         "flow: velocity and pressure of a sperm model on a 1024 x 1024 grid")
+                         "flow: velocity and pressure of a sperm model on a 1024 x 1024 grid; posterior: whole "
+                         "TMCMC runs to q = 1 on the TMCMC workload, FP32 vs FP64 kernel, posterior moments")
     args = ap.parse_args()
 
     from paper_1910_12007_gb300 import ranks
@@ -248,6 +249,8 @@ def main():
         return sperm_tmcmc_workload(args, rank, local_rank)
     if args.workload == "flow":
         return flow_workload(args, rank, local_rank)
+    if args.workload == "posterior":
+        return posterior_workload(args, rank, local_rank)
 
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
@@ -730,6 +733,66 @@ def sperm_tmcmc_workload(args, rank, local_rank):
             "q": [s["q"] for s in log]}
     print(json.dumps(line), flush=True)
     h.close()
+    return 0
+
+
+# -------------------------------------------------------------------------------------
+# whole TMCMC runs to q = 1 at the TMCMC workload's full size, FP32 kernel vs FP64 kernel
+# -------------------------------------------------------------------------------------
+def posterior_workload(args, rank, local_rank):
+    import numpy as np
+    import torch
+
+    import paper_1910_12007_gb300 as g
+    import synthetic
+
+    if rank != 0:
+        return 0  # a comparison of two precisions on one GPU: rank 0 alone runs it
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    seed = 600
+    results = {}
+    obs = sigma = None
+    for name, prec in (("fp64", g.FP64), ("fp32c", g.FP32C)):
+        cfg = g.SwimmerConfig(n_max=N_PTS, b_max=B_STAGE, length=1.0, dt=DT, steps=STEPS, obs_every=OBS_EVERY,
+                              precision=prec)
+        h = g.swimmer_init(cfg)
+        th_tune = torch.tensor(synthetic.prior_samples(4242, PRIOR_LO, PRIOR_HI, B_STAGE), device=dev)
+        g.swimmer_autotune(h, steps=200, theta=th_tune)
+        if obs is None:  # one data set (the FP64 model at theta* plus 5 % noise) for both
+            xi = g.forward_batch(h, torch.tensor([THETA_TRUE], dtype=torch.float64, device=dev))[0][0].cpu().numpy()
+            sigma = NOISE * float(np.mean(np.abs(xi)))
+            D = xi + sigma * synthetic.normals(1234, synthetic.NOISE, 0, xi.size).reshape(xi.shape)
+            obs = torch.tensor(D, dtype=torch.float64, device=dev)
+        th0 = torch.tensor(synthetic.prior_samples(seed, PRIOR_LO, PRIOR_HI, B_STAGE), device=dev)
+        log = []
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        st = g.tmcmc_run(h, th0, obs, sigma, PRIOR_LO, PRIOR_HI,
+                         lambda j: synthetic.stage_randoms(seed, j, B_STAGE, 3), log=log)
+        torch.cuda.synchronize()
+        el = time.perf_counter() - t0
+        th = st.theta.cpu().numpy()
+        results[name] = {"seconds": el, "stages": len(log), "samples_per_s": B_STAGE * len(log) / el,
+                         "q": [s["q"] for s in log], "log_evidence": log[-1]["log_evidence"],
+                         "posterior_mean": th.mean(0).tolist(), "posterior_sd": th.std(0).tolist()}
+        h.close()
+    r64, r32 = results["fp64"], results["fp32c"]
+    m64, s64 = np.array(r64["posterior_mean"]), np.array(r64["posterior_sd"])
+    m32, s32 = np.array(r32["posterior_mean"]), np.array(r32["posterior_sd"])
+    line = {"metric": METRIC, "value": r32["samples_per_s"], "unit": "TMCMC samples/s", "n_gpus": 1, "steps": 1,
+            "warmup": 0, "ms_per_step": 1e3 * r32["seconds"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "whole TMCMC runs to q = 1 on the TMCMC workload (1024 samples/stage, N=128, 2e4 "
+                                   "steps per run, head x,y every 100 steps, 5% noise), FP32 kernel vs FP64 kernel "
+                                   "(the FP64 kernel equals the FP64 oracle to 1e-8 sample by sample in the tests)"},
+            "fp32c": r32, "fp64": r64,
+            "mean_rel_diff": (np.abs(m32 - m64) / np.abs(m64)).tolist(),
+            "sd_rel_diff": (np.abs(s32 - s64) / s64).tolist(),
+            "within_2pct": bool(np.all(np.abs(m32 - m64) <= 0.02 * np.abs(m64)) and
+                                np.all(np.abs(s32 - s64) <= 0.02 * s64)),
+            "speedup_fp32_over_fp64": r32["samples_per_s"] / r64["samples_per_s"]}
+    print(json.dumps(line), flush=True)
     return 0
 
 
