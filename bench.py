@@ -211,8 +211,8 @@ def main():
     ap.add_argument("--profile-case", action="store_true",
                     help="run one forward batch of the workload (1024 samples, 200 steps) for ncu and exit")
     ap.add_argument("--shape", default=None,
-                    help="--profile-case launch shape: threads per sample, suffix w for two-target pair units "
-                         "(e.g. 128w); default: the untuned heuristic")
+                    help="--profile-case launch shape: threads per sample, suffix w (q) for two- (four-) target "
+                         "pair units (e.g. 128w); default: the untuned heuristic")
     ap.add_argument("--workload", default="tmcmc",
                     choices=["tmcmc", "uneven", "large", "surrogate", "shapes", "sperm", "sperm-tmcmc", "two-sperm",
                              "flow", "posterior"],
@@ -271,7 +271,7 @@ def main():
         cfg.steps = 200
         h = g.swimmer_init(cfg)
         if args.shape:
-            shape = int(args.shape.rstrip("w")) | (g.SHAPE_WIDE if args.shape.endswith("w") else 0)
+            shape = int(args.shape.rstrip("wq")) | {"w": g.SHAPE_WIDE, "q": g.SHAPE_QUAD}.get(args.shape[-1], 0)
             g.swimmer_tuning(h, prec, [shape] * 17)
         th = torch.tensor(synthetic.prior_samples(5, PRIOR_LO, (10.0, 0.2, 0.2), B_STAGE), device=dev)
         for rep in range(2):
@@ -608,7 +608,7 @@ def shapes_workload(args, rank, local_rank):
         B = 1 if per == 0 else min(per * sms, B_STAGE)
         th = torch.tensor(synthetic.prior_samples(77, lo, hi, B), device=dev)
         row = {}
-        for T in (128, 256, 512, 1024, 128 | g.SHAPE_WIDE, 256 | g.SHAPE_WIDE, 512 | g.SHAPE_WIDE):
+        for T in (128, 256, 512, 1024, 128 | g.SHAPE_WIDE, 256 | g.SHAPE_WIDE, 512 | g.SHAPE_WIDE, 512 | g.SHAPE_QUAD):
             try:
                 g.swimmer_tuning(h, g.FP32C, [T] * 17)
             except RuntimeError:
@@ -620,10 +620,10 @@ def shapes_workload(args, rank, local_rank):
             ms, *_ = g.swimmer_profile(h, 2)
             g.swimmer_profile(h, 0)
             if bool((st == 0).all()):
-                row[f"{T & 0xFFFF}{'w' if T & g.SHAPE_WIDE else ''}"] = round(ms * 1e3 / steps, 3)
+                row[f"{T & 0xFFFF}{'w' if T & g.SHAPE_WIDE else 'q' if T & g.SHAPE_QUAD else ''}"] = round(ms * 1e3 / steps, 3)
         rows.append({"samples": B, "samples_per_sm": B / sms, "us_per_step_by_threads": row})
     print(json.dumps({"workload": f"forward kernel, N={N_PTS}, {steps} steps, FP32C: microseconds per time step",
-                      "sms": sms, "shapes": "threads per sample, w: two-target pair units", "rows": rows}), flush=True)
+                      "sms": sms, "shapes": "threads per sample, w/q: two-/four-target pair units", "rows": rows}), flush=True)
     h.close()
     return 0
 

@@ -48,10 +48,13 @@ enum {
 
 enum { SWIMMER_FP64 = 0, SWIMMER_FP32C = 1 };
 
-/* Launch-shape flag (FP32C only), OR-ed into a threads-per-sample value: the pair sum takes
- * two blocks of 32 targets per warp against one block of sources, so each source load and
- * shuffle serves two pair evaluations. */
+/* Launch-shape flags (FP32C only, at most one), OR-ed into a threads-per-sample value: the
+ * pair sum takes two (WIDE) or four (QUAD) blocks of 32 targets per warp against one block of
+ * sources, so each source load and shuffle serves two or four pair evaluations.  QUAD units
+ * need 128 registers a thread: a launch whose shared memory allows more than 64K / 128
+ * registers' worth of threads per SM runs WIDE units instead. */
 #define SWIMMER_SHAPE_WIDE 0x10000
+#define SWIMMER_SHAPE_QUAD 0x20000
 
 /* Physical and numerical parameters (Table Tab:param fields).  POD, host memory. */
 typedef struct swimmer_config {
@@ -176,8 +179,8 @@ int forward_batch(swimmer_handle *h, int B, const double *theta, const int *n_pt
  * steps) with every admissible number of threads per sample (a
  * power of two from the smallest that covers n_max up to 1024 or the shared-memory limit;
  * the extra threads take more pair units in FP32 and split the source loop in FP64) and
- * stores the fastest in the handle (in FP32C each threads value is timed with and without
- * SWIMMER_SHAPE_WIDE; the stored shape may carry the flag).  The samples are the caller's theta (device, [n_theta][3]
+ * stores the fastest in the handle (in FP32C each threads value is timed plain, with
+ * SWIMMER_SHAPE_WIDE and with SWIMMER_SHAPE_QUAD; the stored shape may carry a flag).  The samples are the caller's theta (device, [n_theta][3]
  * FP64, rows repeated as needed) when given: batches whose runs differ in length (runs that
  * diverge and stop early) favour shapes with fewer resident samples, whose work queue
  * rebalances the SMs.  With theta NULL, b_max copies of a mid-prior swimmer are timed.
@@ -192,8 +195,8 @@ int swimmer_autotune(swimmer_handle *h, int steps, const double *theta, int n_th
  * k + 1 samples per SM (ceil(B / SMs) = k + 1; k = 16 also takes larger batches), host
  * array of 17.  0 means "use the heuristic".  Set
  * entries must be 0 or a power of two from 32 to 1024 whose shared memory fits the
- * device, in FP32C optionally OR-ed with SWIMMER_SHAPE_WIDE, else SWIMMER_E_ARG and
- * nothing changes.  Lets a caller keep autotuned shapes
+ * device, in FP32C optionally OR-ed with SWIMMER_SHAPE_WIDE or SWIMMER_SHAPE_QUAD, else
+ * SWIMMER_E_ARG and nothing changes.  Lets a caller keep autotuned shapes
  * across handles or processes. */
 int swimmer_tuning(swimmer_handle *h, int precision, int *threads, int set);
 
@@ -293,16 +296,17 @@ int tmcmc_tree_template(int M, double p_accept, int depth_cap, int *nodes, int *
 /* The FP32 pair sum's work list for a sample of nb blocks of 32 points (host only, no
  * device work; 1 <= nb <= 32).  Each unordered pair of points is evaluated once (Eq. BrV is
  * even in the separation, so one kernel lookup serves both points).  A unit is 16 steps of
- * a warp: lane l holds target I*32 + l (and, in a two-target unit, I2*32 + l) and at step
- * d = d0 .. d0 + 15 meets source J*32 + (l + d) mod 32.  Packing: I | J << 8 | d0 << 16 |
- * I2 << 24, I2 = 255 for one target block.  A diagonal unit (I = J, d0 = 1) takes
- * d = 1 .. 16, lanes < 16 only at d = 16; an off-diagonal block pair is two units
- * (d0 = 0, 16).  wide = 0: nb diagonal units, then every block pair {I, J} as one-target
- * units in circulant order.  wide = 1: block pairs grouped two by two around a shared
- * source block J ({I, J} with {I2, J}), at most one left as a one-target pair, then the
- * diagonal units.  out: host, at least nb^2 unsigned; *count = units written.
- * SWIMMER_E_ARG on bad arguments. */
-int swimmer_pair_units(int nb, int wide, unsigned *out, int *count);
+ * a warp: lane l holds target I*32 + l (and I2*32 + l, ... in a multi-target unit) and at
+ * step d = d0 .. d0 + 15 meets source J*32 + (l + d) mod 32.  Packing (5-bit fields):
+ * I | J << 5 | I2 << 10 | I3 << 15 | I4 << 20 | code << 25 | kind << 27, code 0: d0 = 0,
+ * 1: d0 = 16, 2: a diagonal unit (I = J, d = 1 .. 16, lanes < 16 only at d = 16); kind 0, 1,
+ * 2: 1, 2 or 4 target blocks.  An off-diagonal block pair is two units (d0 = 0, 16).
+ * mode 0: nb diagonal units, then every block pair {I, J} as one-target units in circulant
+ * order.  mode 1 (2): block pairs grouped two (four) at a time around a shared source block
+ * J, the rest as pairs, at most one left as a one-target pair, then the diagonal units.
+ * out: host, at least nb^2 unsigned; *count = units written.  SWIMMER_E_ARG on bad
+ * arguments. */
+int swimmer_pair_units(int nb, int mode, unsigned *out, int *count);
 
 /* Stage pieces, exposed for testing (Algorithm 1 'Analyze' and 'Resample'):
  * tmcmc_analyze: from loglik[B] (device), theta[B][P] (device, P = n_params) and q (host)

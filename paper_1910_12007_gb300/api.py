@@ -16,6 +16,7 @@ from ._lib import SwimmerConfigC, TmcmcStateC, check, lib
 FP64 = 0
 FP32C = 1
 SHAPE_WIDE = 0x10000  # launch-shape flag (FP32C): two target blocks per pair unit
+SHAPE_QUAD = 0x20000  # launch-shape flag (FP32C): four target blocks per pair unit
 
 
 OBS_HEAD_POINT, OBS_HEAD_VELOCITY, OBS_PAIR_DISTANCES = 0, 1, 2
@@ -257,13 +258,20 @@ def tmcmc_tree_template(M, p_accept, depth_cap):
             for v in range(count.value)]
 
 
-def swimmer_pair_units(nb, wide):
+def swimmer_pair_units(nb, mode):
     """The FP32 pair sum's work list for nb blocks of 32 points (host only): list of
-    (I, J, d0, I2) per unit of 16 steps, I2 = 255 for a one-target unit."""
+    (targets, J, d0) per unit of 16 steps: the target blocks (1, 2 or 4), the source block
+    and the first step (d0 = 1 marks a diagonal unit, steps 1 .. 16)."""
     buf = (ctypes.c_uint * max(1, nb * nb))()
     count = ctypes.c_int(0)
-    check(lib().swimmer_pair_units(int(nb), int(wide), buf, ctypes.byref(count)))
-    return [(buf[k] & 255, (buf[k] >> 8) & 255, (buf[k] >> 16) & 255, buf[k] >> 24) for k in range(count.value)]
+    check(lib().swimmer_pair_units(int(nb), int(mode), buf, ctypes.byref(count)))
+    out = []
+    for k in range(count.value):
+        u = buf[k]
+        kind, code = (u >> 27) & 3, (u >> 25) & 3
+        blocks = [u & 31, (u >> 10) & 31, (u >> 15) & 31, (u >> 20) & 31][: (1, 2, 4)[kind]]
+        out.append((tuple(blocks), (u >> 5) & 31, 1 if code == 2 else 16 * code))
+    return out
 
 
 def tmcmc_stage(h: Handle, st: TmcmcState, uniforms, normals, use_surrogate=False, stream=None, rank=0, world=1):
@@ -401,7 +409,8 @@ def swimmer_autotune(h: Handle, steps=200, theta=None):
 def swimmer_tuning(h: Handle, precision=None, threads=None):
     """Get (threads=None) or set the launch-shape table of one precision: a list of 17
     threads-per-sample entries, entry k for batches of k + 1 samples per SM, 0 = heuristic;
-    FP32C entries may carry SHAPE_WIDE (two target blocks per pair unit)."""
+    FP32C entries may carry SHAPE_WIDE or SHAPE_QUAD (two or four target blocks per pair
+    unit)."""
     prec = h.cfg.precision if precision is None else precision
     buf = (ctypes.c_int * 17)()
     if threads is None:

@@ -285,9 +285,10 @@ extern "C" int swimmer_tuning(swimmer_handle *h, int precision, int *threads, in
     }
     for (int k = 0; k < 17; ++k) {
         const int t = threads[k] & SHAPE_THREADS;
-        ARG_CHECK((threads[k] & ~(SHAPE_THREADS | SHAPE_WIDE)) == 0 &&
-                      (precision != SWIMMER_FP64 || !(threads[k] & SHAPE_WIDE)),
-                  "threads[%d] = %d has flags other than SWIMMER_SHAPE_WIDE (FP32C only)", k, threads[k]);
+        const int flags = threads[k] & ~SHAPE_THREADS;
+        ARG_CHECK(flags == 0 || (precision != SWIMMER_FP64 && (flags == SHAPE_WIDE || flags == SHAPE_QUAD)),
+                  "threads[%d] = %d: flags must be none, SWIMMER_SHAPE_WIDE or SWIMMER_SHAPE_QUAD (FP32C only)", k,
+                  threads[k]);
         ARG_CHECK(threads[k] == 0 || (t >= forward_min_threads(h, precision) && t <= 1024 && (t & (t - 1)) == 0),
                   "threads[%d] = %d is not 0 or a power of two in [%d, 1024]", k, t, forward_min_threads(h, precision));
         ARG_CHECK(t == 0 || forward_fits(h, t, precision), "threads[%d] = %d needs more shared memory than the device has", k, t);
@@ -342,8 +343,8 @@ extern "C" int swimmer_autotune(swimmer_handle *h, int steps, const double *thet
         int bestT = T0;
         for (int T = T0; T <= 1024 && !rc; T <<= 1) {
             if (!forward_fits(h, T, prec)) break;
-            for (int wide = 0; wide <= (prec == SWIMMER_FP64 ? 0 : 1) && !rc; ++wide) {
-                const int shape = T | (wide ? SHAPE_WIDE : 0);
+            for (int mode = 0; mode <= (prec == SWIMMER_FP64 ? 0 : 2) && !rc; ++mode) {
+                const int shape = T | (mode == 1 ? SHAPE_WIDE : mode == 2 ? SHAPE_QUAD : 0);
                 float ms = 0.f;
                 for (int rep = 0; rep < 2 && !rc; ++rep) {  // first run warms up
                     cudaEventRecord(e0, 0);

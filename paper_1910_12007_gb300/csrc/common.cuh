@@ -32,18 +32,21 @@ constexpr int K1_SCRATCH = 2 * NODES_MAX + TAIL_MAX;  // doubles of table-build 
 constexpr double R_MAX_OVER_L = 1.25;  // table reach in units of the flagellum length
 constexpr double STRETCH_MAX = 0.20;   // segment stretch beyond which a run counts as diverged
 constexpr int N_PTS_MAX = 1024;
-// FP32 pair units (see forward.cu): one list per block count nb = ceil(n / 32) and per
-// decomposition (0: one target block per unit, 1: two target blocks sharing a source
-// block); the handle's device buffer starts with the lists' offsets [2][UNIT_NB_MAX + 1]
+// FP32 pair units (see forward.cu): one list per block count nb = ceil(n / 32) and per mode
+// (0: one target block per unit, 1: two target blocks sharing a source block, 2: four); the
+// handle's device buffer starts with [UNIT_MODES][UNIT_NB_MAX + 1] offsets (list nb of mode m
+// spans [hdr[m][nb - 1], hdr[m][nb]) after the header), at most nb^2 units a list
 constexpr int UNIT_NB_MAX = N_PTS_MAX / 32;
-constexpr int UNIT_HDR = 2 * (UNIT_NB_MAX + 1);
+constexpr int UNIT_MODES = 3;
+constexpr int UNIT_HDR = UNIT_MODES * (UNIT_NB_MAX + 1);
 constexpr int SHAPE_WIDE = SWIMMER_SHAPE_WIDE;  // launch-shape flag: two-target pair units
+constexpr int SHAPE_QUAD = SWIMMER_SHAPE_QUAD;  // launch-shape flag: four-target pair units
 constexpr int SHAPE_THREADS = SHAPE_WIDE - 1;
-// units in a list: nb diagonal units of 16 steps plus, per off-diagonal block pair, two
-// units of 16 steps (one target block) or, two block pairs at a time, two units (two)
-__host__ __device__ inline int unit_count(int nb, int wide) {
-    const int e = nb * (nb - 1) / 2;
-    return wide ? nb + 2 * ((e + 1) / 2) : nb * nb;
+// unit packing: I [0, 5), J [5, 10), I2, I3, I4 [10, 25), step code [25, 27) (0: d0 = 0,
+// 1: d0 = 16, 2: diagonal block, d = 1 .. 16), kind [27, 29) (0, 1, 2: 1, 2, 4 target blocks)
+__host__ __device__ inline unsigned unit_pack(int kind, int code, int J, int I, int I2 = 0, int I3 = 0, int I4 = 0) {
+    return (unsigned)I | ((unsigned)J << 5) | ((unsigned)I2 << 10) | ((unsigned)I3 << 15) | ((unsigned)I4 << 20) |
+           ((unsigned)code << 25) | ((unsigned)kind << 27);
 }
 constexpr int P_THETA = 3;
 constexpr double X_MAX = 600.0;        // largest alpha * r the Bessel evaluations accept

@@ -71,7 +71,7 @@ struct FwdArgs {
     int threads;
     int tab_panels;  // panels of the shared-memory table region (handle's octaves x panels/octave)
     const unsigned *units;  // FP32 pair-unit lists (offsets header, then the lists)
-    int wide;               // FP32: two-target pair units
+    int mode;               // FP32 pair units: 0 one-, 1 two-, 2 four-target
 };
 
 struct __align__(32) dbl4 {
@@ -209,8 +209,7 @@ __host__ __device__ size_t state_bytes(int n_max, int threads) {
     return align32(16 * (size_t)n_max) + 1024 * nbm + align32(forces > part ? forces : part);
 }
 
-// FP32: the sample's pair units (I | J << 8 | d0 << 16 | I2 << 24), at most ceil(n_max/32)^2
-// ints after the table
+// FP32: the sample's pair units (unit_pack), at most ceil(n_max/32)^2 ints after the table
 template <bool F64>
 __host__ __device__ size_t smem_bytes(int n_max, int P, int threads) {
     const size_t nbm = (n_max + 31) / 32;
@@ -298,44 +297,49 @@ __device__ __forceinline__ void pair_unit(const float4 *__restrict__ s4, const f
     }
 }
 
-// Two-target pair unit: lane l holds targets I*32 + l and I2*32 + l (I, I2 and J distinct
-// blocks) and at step d = d0 .. d0+15 meets source J*32 + (l + d) mod 32, so one source load
-// and one rotation of the source-side sums serve two pair evaluations.
-__device__ __forceinline__ void pair_unit_wide(const float4 *__restrict__ s4, const float4 *__restrict__ t1,
-                                               const float2 *__restrict__ t2, int pmax, int lane, int I, int I2,
-                                               int Jb, int d0, float2 *__restrict__ mypart) {
+// Multi-target pair unit: lane l holds targets I_r*32 + l, r < R (the I_r and J distinct
+// blocks), and at step d = d0 .. d0+15 meets source J*32 + (l + d) mod 32, so one source
+// load and one rotation of the source-side sums serve R pair evaluations.
+template <int R>
+__device__ __forceinline__ void pair_unit_multi(const float4 *__restrict__ s4, const float4 *__restrict__ t1,
+                                                const float2 *__restrict__ t2, int pmax, int lane, int I0, int I1,
+                                                int I2, int I3, int Jb, int d0, float2 *__restrict__ mypart) {
+    const int I[4] = {I0, I1, I2, I3};
     const int nxt = (lane + 1) & 31;
-    const float4 m1 = s4[(I << 6) + lane];
-    const float4 m2 = s4[(I2 << 6) + lane];
+    float4 m[R];
+    float vx[R], vy[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        m[r] = s4[(I[r] << 6) + lane];
+        vx[r] = 0.f;
+        vy[r] = 0.f;
+    }
     const float4 *sp = s4 + (Jb << 6) + lane + d0;
-    float v1x = 0.f, v1y = 0.f, v2x = 0.f, v2y = 0.f, ax = 0.f, ay = 0.f;
+    float ax = 0.f, ay = 0.f;
 #pragma unroll
     for (int s = 0; s < 16; ++s) {
         const float4 q = sp[s];
-        const Mob M1 = pair_mob(t1, t2, pmax, m1.x - q.x, m1.y - q.y, 1.f);
-        const Mob M2 = pair_mob(t1, t2, pmax, m2.x - q.x, m2.y - q.y, 1.f);
-        v1x = fmaf(M1.m11, q.z, fmaf(M1.m12, q.w, v1x));
-        v1y = fmaf(M1.m12, q.z, fmaf(M1.m22, q.w, v1y));
-        v2x = fmaf(M2.m11, q.z, fmaf(M2.m12, q.w, v2x));
-        v2y = fmaf(M2.m12, q.z, fmaf(M2.m22, q.w, v2y));
-        ax = fmaf(M1.m11, m1.z, fmaf(M1.m12, m1.w, ax));
-        ay = fmaf(M1.m12, m1.z, fmaf(M1.m22, m1.w, ay));
-        ax = fmaf(M2.m11, m2.z, fmaf(M2.m12, m2.w, ax));
-        ay = fmaf(M2.m12, m2.z, fmaf(M2.m22, m2.w, ay));
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const Mob M = pair_mob(t1, t2, pmax, m[r].x - q.x, m[r].y - q.y, 1.f);
+            vx[r] = fmaf(M.m11, q.z, fmaf(M.m12, q.w, vx[r]));
+            vy[r] = fmaf(M.m12, q.z, fmaf(M.m22, q.w, vy[r]));
+            ax = fmaf(M.m11, m[r].z, fmaf(M.m12, m[r].w, ax));
+            ay = fmaf(M.m12, m[r].z, fmaf(M.m22, m[r].w, ay));
+        }
         ax = __shfl_sync(0xffffffffu, ax, nxt);
         ay = __shfl_sync(0xffffffffu, ay, nxt);
     }
     const int from = (lane - d0 - 16) & 31;
     ax = __shfl_sync(0xffffffffu, ax, from);
     ay = __shfl_sync(0xffffffffu, ay, from);
-    float2 p1 = mypart[(I << 5) + lane];
-    p1.x += v1x;
-    p1.y += v1y;
-    mypart[(I << 5) + lane] = p1;
-    float2 p2 = mypart[(I2 << 5) + lane];
-    p2.x += v2x;
-    p2.y += v2y;
-    mypart[(I2 << 5) + lane] = p2;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        float2 pv = mypart[(I[r] << 5) + lane];
+        pv.x += vx[r];
+        pv.y += vy[r];
+        mypart[(I[r] << 5) + lane] = pv;
+    }
     float2 pa = mypart[(Jb << 5) + lane];
     pa.x += ax;
     pa.y += ay;
@@ -449,9 +453,10 @@ __global__ void __launch_bounds__(BIG ? 512 : 1024, 1) forward_kernel(FwdArgs a)
             }
             // the sample's pair units, from the handle's list for its block count
             const int nbs = (n + 31) >> 5;
-            const unsigned *ul = a.units + UNIT_HDR + a.units[a.wide * (UNIT_NB_MAX + 1) + nbs - 1];
+            const unsigned *hdr = a.units + a.mode * (UNIT_NB_MAX + 1);
+            const unsigned *ul = a.units + UNIT_HDR + hdr[nbs - 1];
             unsigned *units = (unsigned *)(tabraw + table_bytes<F64>(P));
-            for (int un = tid; un < unit_count(nbs, a.wide); un += T) units[un] = ul[un];
+            for (int un = tid; un < (int)(hdr[nbs] - hdr[nbs - 1]); un += T) units[un] = ul[un];
         }
         // ---- initial straight filament X_k = (k ds, 0), stored relative to (L/2, 0); the
         //      head circle's centre H_r + dN to the right of the proximal point, head point m
@@ -529,8 +534,9 @@ __global__ void __launch_bounds__(BIG ? 512 : 1024, 1) forward_kernel(FwdArgs a)
         const int tgt = slot;  // one target per slot
         const bool owner = (split == 0) && (tgt < n);
         // FP32 pair sum: the sample's units of 16 steps over the pair warps
-        const int nb = (n + 31) >> 5, n_units = unit_count(nb, a.wide);
-        const int n_pw = min(pair_warps(n_max, T), unit_count(nbm, a.wide));
+        const unsigned *uhdr = a.units + a.mode * (UNIT_NB_MAX + 1);
+        const int nb = (n + 31) >> 5, n_units = F64 ? 0 : (int)(uhdr[nb] - uhdr[nb - 1]);
+        const int n_pw = F64 ? 0 : min(pair_warps(n_max, T), (int)(uhdr[nbm] - uhdr[nbm - 1]));
         // the thread that keeps the log-likelihood: thread 0 for head-centre velocities (one
         // warp reduces the head after each observation step), else the one that updates the
         // proximal flagellum point nf - 1 (the observed point)
@@ -830,8 +836,9 @@ __global__ void __launch_bounds__(BIG ? 512 : 1024, 1) forward_kernel(FwdArgs a)
                 // per step, so lane l always holds the sum of the source it meets.
                 // Diagonal units (I = J) run d = 1 .. 16 (at d = 16 only lanes < 16, since
                 // lanes l and l + 16 meet the same pair); off-diagonal blocks run d = 0 .. 31
-                // as two units.  A two-target unit (wide launch shape) walks the block pairs
-                // {I, J} and {I2, J} together, sharing the source loads and rotations.  Each
+                // as two units.  A two- or four-target unit (wide and quad launch shapes)
+                // walks the block pairs {I, J}, {I2, J} (, {I3, J}, {I4, J}) together, sharing
+                // the source loads and rotations.  Each
                 // warp adds its units' sums into its own partial array, in a fixed order, so
                 // the result does not depend on scheduling.
                 const float4 *s4 = (const float4 *)src;
@@ -843,11 +850,19 @@ __global__ void __launch_bounds__(BIG ? 512 : 1024, 1) forward_kernel(FwdArgs a)
                 const unsigned *units = (const unsigned *)(tabraw + table_bytes<F64>(P));
                 for (int un = warp; un < n_units; un += n_pw) {
                     const unsigned pk = units[un];
-                    const int I = pk & 255, Jb = (pk >> 8) & 255, d0 = (pk >> 16) & 255, I2 = pk >> 24;
-                    if (I2 == 255)
+                    const int I = pk & 31, Jb = (pk >> 5) & 31, code = (pk >> 25) & 3, kind = (pk >> 27) & 3;
+                    const int d0 = code == 2 ? 1 : code << 4;
+                    const int I2 = (pk >> 10) & 31, I3 = (pk >> 15) & 31, I4 = (pk >> 20) & 31;
+                    if (kind == 0) {
                         pair_unit(s4, t1, t2, npan - 1, lane, I, Jb, d0, mypart);
-                    else
-                        pair_unit_wide(s4, t1, t2, npan - 1, lane, I, I2, Jb, d0, mypart);
+                    } else if (BIG && kind == 2) {
+                        pair_unit_multi<4>(s4, t1, t2, npan - 1, lane, I, I2, I3, I4, Jb, d0, mypart);
+                    } else {
+                        pair_unit_multi<2>(s4, t1, t2, npan - 1, lane, I, I2, 0, 0, Jb, d0, mypart);
+                        // the host gives four-target lists to the 128-register instantiation
+                        // only; a run that meets one here ends as diverged, not with pairs missing
+                        if (kind == 2) bad = 1;
+                    }
                 }
             }
             if (!F64) __syncthreads();
@@ -1018,35 +1033,33 @@ ForwardKernel forward_kernel_for(bool f64, const swimmer_config &c, bool big = f
 }  // namespace
 
 // The pair-unit list of nb blocks (packing and order as swimmer_pair_units documents).
-// Two-target lists group the off-diagonal block pairs (edges of the complete graph on the
-// blocks) two by two around a shared block: blocks are visited from the last down, each
-// takes its edges to lower blocks plus those handed to it, and when their number is odd it
-// hands one edge to a lower block whose own count would otherwise be odd, so at most one
-// edge stays alone, at block 0.
-static std::vector<unsigned> build_pair_units(int nb, int wide) {
-    auto pack = [](int I, int J, int d0, int I2) {
-        return (unsigned)I | ((unsigned)J << 8) | ((unsigned)d0 << 16) | ((unsigned)I2 << 24);
-    };
+// Multi-target lists group the off-diagonal block pairs (edges of the complete graph on the
+// blocks) around a shared block: blocks are visited from the last down, each takes its edges
+// to lower blocks plus those handed to it, and when their number is odd it hands one edge to
+// a lower block whose own count would otherwise be odd, so at most one edge stays alone, at
+// block 0.  Mode 2 hands edges down until a block's count is a multiple of four (as far as its
+// own edges to lower blocks allow) and takes them four at a time, the rest in pairs and alone.
+static std::vector<unsigned> build_pair_units(int nb, int mode) {
     std::vector<unsigned> out;
-    if (!wide) {
-        for (int i = 0; i < nb; ++i) out.push_back(pack(i, i, 1, 255));
+    if (mode == 0) {
+        for (int i = 0; i < nb; ++i) out.push_back(unit_pack(0, 2, i, i));
         // off-diagonal block pairs in circulant order: {r, r + k} for k = 1 .. (nb - 1) / 2,
         // then {r, r + nb / 2} for r < nb / 2 (even nb)
         for (int k = 1; k <= (nb - 1) / 2; ++k)
             for (int r = 0; r < nb; ++r)
-                for (int d0 = 0; d0 <= 16; d0 += 16) out.push_back(pack(r, (r + k) % nb, d0, 255));
+                for (int c = 0; c < 2; ++c) out.push_back(unit_pack(0, c, (r + k) % nb, r));
         if (nb % 2 == 0)
             for (int r = 0; r < nb / 2; ++r)
-                for (int d0 = 0; d0 <= 16; d0 += 16) out.push_back(pack(r, r + nb / 2, d0, 255));
+                for (int c = 0; c < 2; ++c) out.push_back(unit_pack(0, c, r + nb / 2, r));
         return out;
     }
     std::vector<std::vector<int>> handed(nb);
-    std::vector<unsigned> single;
+    std::vector<unsigned> quad, pair, single;
     for (int J = nb - 1; J >= 0; --J) {
         std::vector<int> other;  // the other blocks of the edges grouped at J
         for (int i = 0; i < J; ++i) other.push_back(i);
         for (int x : handed[J]) other.push_back(x);
-        if (other.size() % 2 == 1 && J > 0) {
+        if (mode == 1 && other.size() % 2 == 1 && J > 0) {
             int pick = 0;
             for (int i = J - 1; i >= 0; --i)
                 if ((i + handed[i].size()) % 2 == 1) {
@@ -1056,40 +1069,65 @@ static std::vector<unsigned> build_pair_units(int nb, int wide) {
             other.erase(std::find(other.begin(), other.end(), pick));
             handed[pick].push_back(J);
         }
-        for (size_t k = 0; k + 1 < other.size(); k += 2)
-            for (int d0 = 0; d0 <= 16; d0 += 16) out.push_back(pack(other[k], J, d0, other[k + 1]));
-        if (other.size() % 2 == 1)
-            for (int d0 = 0; d0 <= 16; d0 += 16) single.push_back(pack(other.back(), J, d0, 255));
+        // mode 2: hand edges down until the count is a multiple of four, each to the lower
+        // block whose own count comes closest to a multiple of four by it
+        for (int hand = mode == 2 && J > 0 ? (int)(other.size() % 4) : 0; hand > 0; --hand) {
+            int pick = -1, best = -1;
+            for (int i = J - 1; i >= 0; --i) {
+                if (std::find(other.begin(), other.end(), i) == other.end()) continue;  // handed already
+                const int score = (int)((i + handed[i].size()) % 4);  // 3 is best: +1 makes 0 mod 4
+                if (score > best) {
+                    best = score;
+                    pick = i;
+                }
+            }
+            if (pick < 0) break;
+            other.erase(std::find(other.begin(), other.end(), pick));
+            handed[pick].push_back(J);
+        }
+        size_t k = 0;
+        if (mode == 2)
+            for (; k + 3 < other.size(); k += 4)
+                for (int c = 0; c < 2; ++c)
+                    quad.push_back(unit_pack(2, c, J, other[k], other[k + 1], other[k + 2], other[k + 3]));
+        for (; k + 1 < other.size(); k += 2)
+            for (int c = 0; c < 2; ++c) pair.push_back(unit_pack(1, c, J, other[k], other[k + 1]));
+        if (k < other.size())
+            for (int c = 0; c < 2; ++c) single.push_back(unit_pack(0, c, J, other[k]));
     }
+    out.insert(out.end(), quad.begin(), quad.end());
+    out.insert(out.end(), pair.begin(), pair.end());
     out.insert(out.end(), single.begin(), single.end());
-    for (int i = 0; i < nb; ++i) out.push_back(pack(i, i, 1, 255));
+    for (int i = 0; i < nb; ++i) out.push_back(unit_pack(0, 2, i, i));
     return out;
 }
 
-extern "C" int swimmer_pair_units(int nb, int wide, unsigned *out, int *count) {
+extern "C" int swimmer_pair_units(int nb, int mode, unsigned *out, int *count) {
     ARG_CHECK(nb >= 1 && nb <= UNIT_NB_MAX, "nb must be in [1, %d]", UNIT_NB_MAX);
-    ARG_CHECK(wide == 0 || wide == 1, "wide must be 0 or 1");
+    ARG_CHECK(mode >= 0 && mode < UNIT_MODES, "mode must be 0, 1 or 2");
     ARG_CHECK(out != nullptr && count != nullptr, "out or count is NULL");
-    const std::vector<unsigned> u = build_pair_units(nb, wide);
+    const std::vector<unsigned> u = build_pair_units(nb, mode);
     std::copy(u.begin(), u.end(), out);
     *count = (int)u.size();
     return 0;
 }
 
-// Device copy of both decompositions for every block count up to the handle's n_max.
+// Device copy of every mode's lists for every block count up to the handle's n_max.
 int upload_pair_units(swimmer_handle *h) {
     const int nbm = (h->cfg.n_max + 31) / 32;
     std::vector<unsigned> all(UNIT_HDR, 0u), body;
-    for (int w = 0; w < 2; ++w)
+    for (int m = 0; m < UNIT_MODES; ++m) {
         for (int nb = 1; nb <= nbm; ++nb) {
-            const std::vector<unsigned> u = build_pair_units(nb, w);
-            if ((int)u.size() != unit_count(nb, w)) {
+            const std::vector<unsigned> u = build_pair_units(nb, m);
+            if ((int)u.size() > nb * nb) {
                 set_error("pair-unit list of %d blocks has %zu units", nb, u.size());
                 return SWIMMER_E_ARG;
             }
-            all[w * (UNIT_NB_MAX + 1) + nb - 1] = (unsigned)body.size();
+            all[m * (UNIT_NB_MAX + 1) + nb - 1] = (unsigned)body.size();
             body.insert(body.end(), u.begin(), u.end());
         }
+        all[m * (UNIT_NB_MAX + 1) + nbm] = (unsigned)body.size();
+    }
     all.insert(all.end(), body.begin(), body.end());
     CUDA_TRY(cudaMalloc((void **)&h->units, sizeof(unsigned) * all.size()));
     CUDA_TRY(cudaMemcpy(h->units, all.data(), sizeof(unsigned) * all.size(), cudaMemcpyHostToDevice));
@@ -1198,7 +1236,7 @@ int launch_forward(swimmer_handle *h, int B, const double *obs, double sigma, do
     a.threads = T;
     const bool f64 = precision == SWIMMER_FP64;
     a.units = h->units;
-    a.wide = !f64 && (shape & SHAPE_WIDE) ? 1 : 0;
+    a.mode = f64 ? 0 : (shape & SHAPE_QUAD) ? 2 : (shape & SHAPE_WIDE) ? 1 : 0;
     a.tab_panels = handle_octaves(h) * (f64 ? F64_SUB : F32_SUB);
     size_t smem = f64 ? smem_bytes<true>(a.n_max, a.tab_panels, T) : smem_bytes<false>(a.n_max, a.tab_panels, T);
     auto kern = forward_kernel_for(f64, h->cfg);
@@ -1218,6 +1256,8 @@ int launch_forward(swimmer_handle *h, int B, const double *obs, double sigma, do
         CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_big, big, T, smem));
         if (per_big >= per_sm) kern = big;
     }
+    // four-target units need the 128-register budget; elsewhere the launch runs two-target ones
+    if (a.mode == 2 && kern == forward_kernel_for(f64, h->cfg)) a.mode = 1;
     if (per_sm < 1) {
         set_error("forward kernel does not fit on an SM (threads %d, smem %zu)", T, smem);
         return SWIMMER_E_CUDA;

@@ -2,10 +2,10 @@
 
 The pair sum evaluates each unordered pair of points once (Eq. BrV is even in the
 separation d = X_i - X_j, so one kernel lookup serves both points).  A unit is 16 steps of a
-warp: lane l holds target I*32 + l (and I2*32 + l in a two-target unit) and at step d meets
-source J*32 + (l + d) mod 32.  Whatever the grouping, the lists must cover every unordered
-pair of the nb*32 points exactly once and no point with itself; a two-target unit must name
-three distinct blocks (its three partial sums go to three different rows).
+warp: lane l holds target I*32 + l for each of its 1, 2 or 4 target blocks I and at step d
+meets source J*32 + (l + d) mod 32.  Whatever the grouping, the lists must cover every
+unordered pair of the nb*32 points exactly once and no point with itself; a multi-target
+unit must name distinct blocks (its partial sums go to different rows).
 """
 import os
 from collections import Counter
@@ -27,10 +27,9 @@ def api():
 def _pairs(units):
     """Unordered point pairs each unit evaluates, by simulating the warp's walk."""
     seen = Counter()
-    for I, J, d0, I2 in units:
-        diag = I == J
+    for targets, J, d0 in units:
+        diag = d0 == 1
         steps = range(1, 17) if diag else range(d0, d0 + 16)
-        targets = [I] + ([] if I2 == 255 else [I2])
         for d in steps:
             for lane in range(32):
                 if diag and d == 16 and lane >= 16:
@@ -42,12 +41,13 @@ def _pairs(units):
     return seen
 
 
-@pytest.mark.parametrize("wide", [0, 1])
+@pytest.mark.parametrize("mode", [0, 1, 2])
 @pytest.mark.parametrize("nb", [1, 2, 3, 4, 5, 6, 7, 8, 9, 13, 16, 31, 32])
-def test_every_unordered_pair_once(api, nb, wide):
-    units = api.swimmer_pair_units(nb, wide)
-    e = nb * (nb - 1) // 2
-    assert len(units) == (nb + 2 * ((e + 1) // 2) if wide else nb * nb)
+def test_every_unordered_pair_once(api, nb, mode):
+    units = api.swimmer_pair_units(nb, mode)
+    assert len(units) <= nb * nb
+    if mode == 0:
+        assert len(units) == nb * nb
     seen = _pairs(units)
     n = nb * 32
     assert all(i != j for i, j in seen), "a point met itself"
@@ -55,23 +55,32 @@ def test_every_unordered_pair_once(api, nb, wide):
     assert set(seen.values()) == {1}
 
 
+@pytest.mark.parametrize("mode", [1, 2])
 @pytest.mark.parametrize("nb", list(range(1, 33)))
-def test_wide_grouping(api, nb):
-    units = api.swimmer_pair_units(nb, 1)
-    wide = [u for u in units if u[3] != 255]
-    single = [u for u in units if u[3] == 255 and u[0] != u[1]]
+def test_grouping(api, nb, mode):
+    units = api.swimmer_pair_units(nb, mode)
+    off = [u for u in units if u[2] != 1]
     e = nb * (nb - 1) // 2
-    assert len(wide) == 2 * (e // 2) and len(single) == 2 * (e % 2)
-    for I, J, d0, I2 in wide:
-        assert len({I, J, I2}) == 3 and d0 in (0, 16)
+    singles = [u for u in off if len(u[0]) == 1]
+    if mode == 1:
+        assert len(singles) == 2 * (e % 2)  # at most one block pair stays alone
+        assert all(len(u[0]) in (1, 2) for u in off)
+    else:
+        # four-target units carry nearly every block pair once there are a few blocks
+        assert len(singles) <= 4
+        if nb >= 8:
+            quads = [u for u in off if len(u[0]) == 4]
+            assert 4 * len(quads) // 2 >= 0.9 * e
+    for targets, J, d0 in off:
+        assert len(set(targets) | {J}) == len(targets) + 1 and d0 in (0, 16)
     # each unit's two halves (d0 = 0 and 16) come together
-    for k in range(0, len(wide), 2):
-        assert wide[k][:2] + wide[k][3:] == wide[k + 1][:2] + wide[k + 1][3:]
-        assert (wide[k][2], wide[k + 1][2]) == (0, 16)
-    assert all(0 <= b < nb for u in units for b in (u[0], u[1]))
+    for k in range(0, len(off), 2):
+        assert off[k][:2] == off[k + 1][:2] and (off[k][2], off[k + 1][2]) == (0, 16)
+    assert all(0 <= b < nb for u in units for b in u[0] + (u[1],))
+    assert [u for u in units if u[2] == 1] == [((i,), i, 1) for i in range(nb)]
 
 
 def test_rejects_bad_arguments(api):
-    for nb, wide in ((0, 0), (33, 0), (4, 2)):
+    for nb, mode in ((0, 0), (33, 0), (4, 3), (4, -1)):
         with pytest.raises(Exception):
-            api.swimmer_pair_units(nb, wide)
+            api.swimmer_pair_units(nb, mode)

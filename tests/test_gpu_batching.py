@@ -92,8 +92,9 @@ def test_launch_shapes_agree_and_tuning_table_round_trips():
     th = torch.tensor(synthetic.prior_samples(9, (0.2, -0.5, 0.05), (8.0, 0.5, 0.15), 40), device=DEV)
     ns = torch.tensor(synthetic.choice_n(9, [40, 70, 96], 40).astype(np.int32), device=DEV)
     outs = {}
-    W = g.SHAPE_WIDE
-    shapes = (128, 256, 512, 128 | W, 256 | W, 512 | W)
+    W, Q = g.SHAPE_WIDE, g.SHAPE_QUAD
+    # (at N <= 96 every launch keeps the 64-register kernel, so QUAD runs two-target units)
+    shapes = (128, 256, 512, 128 | W, 256 | W, 512 | W, 128 | Q)
     for T in shapes:
         g.swimmer_tuning(h, g.FP32C, [T] * 17)
         assert g.swimmer_tuning(h, g.FP32C) == [T] * 17
@@ -110,13 +111,15 @@ def test_launch_shapes_agree_and_tuning_table_round_trips():
     with pytest.raises(RuntimeError):
         g.swimmer_tuning(h, g.FP32C, [96] * 17)  # not a power of two
     with pytest.raises(RuntimeError):
-        g.swimmer_tuning(h, g.FP32C, [128 | 0x20000] * 17)  # unknown flag
+        g.swimmer_tuning(h, g.FP32C, [128 | 0x40000] * 17)  # unknown flag
+    with pytest.raises(RuntimeError):
+        g.swimmer_tuning(h, g.FP32C, [128 | W | Q] * 17)  # one flag at most
     h64 = g.swimmer_init(replace(cfg, precision=g.FP64))
     with pytest.raises(RuntimeError):
         g.swimmer_tuning(h64, g.FP64, [128 | W] * 17)  # two-target units are FP32 only
     h64.close()
     tuned = g.swimmer_autotune(h, steps=20)
-    assert set(tuned) and all(v & ~W in (128, 256, 512, 1024) for v in tuned.values())
+    assert set(tuned) and all(v & ~(W | Q) in (128, 256, 512, 1024) for v in tuned.values())
     table = g.swimmer_tuning(h, g.FP32C)
     assert table[0] == tuned[1]
     h.close()

@@ -307,9 +307,10 @@ def _velocity_error(traj_b, obs_b, x0, dt):
     return np.max(np.linalg.norm(vg - vr, axis=1)) / np.max(np.linalg.norm(vr, axis=1))
 
 
-@pytest.mark.parametrize("shape", [512 | g.SHAPE_WIDE, 512, 256 | g.SHAPE_WIDE, 128])
+@pytest.mark.parametrize("shape", [512 | g.SHAPE_QUAD, 512 | g.SHAPE_WIDE, 512, 256 | g.SHAPE_QUAD, 128])
 def test_large_sweep_sampled(shape, large_batch):
-    # 512 threads: one CTA per SM, the 128-register instantiation; 128: the 64-register one
+    # 512 threads: one CTA per SM, the 128-register instantiation (four-target units run
+    # there); 128: the 64-register one
     th, (ps, obs, xc, st) = large_batch
     assert np.all(st == 0)
     p = LARGE
