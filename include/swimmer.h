@@ -68,7 +68,7 @@ typedef struct swimmer_config {
     double k_t;             /* tension stiffness K_T */
     double eta;             /* wavenumber */
     double omega;           /* angular frequency */
-    long long steps;        /* time steps per forward run */
+    long long steps;        /* time steps per forward run, 1 .. 2^31 - 2 */
     long long obs_every;    /* observation of the head point every obs_every steps */
     int precision;          /* SWIMMER_FP64 or SWIMMER_FP32C */
     /* Full sperm model (Appendix, Table Tab:param): a circular head of n_head points joined

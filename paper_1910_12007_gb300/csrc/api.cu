@@ -111,7 +111,7 @@ static int check_config(const swimmer_config *c) {
     ARG_CHECK(c->delta_over_ds > 0.0, "delta_over_ds must be > 0");
     ARG_CHECK(c->dt > 0.0, "dt must be > 0");
     ARG_CHECK(c->k_t >= 0.0, "k_t must be >= 0");
-    ARG_CHECK(c->steps >= 1, "steps must be >= 1");
+    ARG_CHECK(c->steps >= 1 && c->steps < (1LL << 31) - 1, "steps must be in [1, 2^31 - 1)");
     ARG_CHECK(c->obs_every >= 1, "obs_every must be >= 1");
     ARG_CHECK(c->precision == SWIMMER_FP64 || c->precision == SWIMMER_FP32C, "precision must be 0 or 1");
     ARG_CHECK(c->n_head == 0 || (c->n_head >= 4 && c->n_head <= 256 && c->n_head % 2 == 0),

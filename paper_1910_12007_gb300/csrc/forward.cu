@@ -32,6 +32,7 @@
 //      squared residual accumulated in FP64 (Eq. fitness).
 // A run stops early, with status DIVERGED, when a velocity is not finite, a point moves
 // more than ds in one step, or a segment stretches beyond STRETCH_MAX.
+#include <limits.h>
 #include <math.h>
 
 #include <algorithm>
@@ -562,8 +563,15 @@ __global__ void __launch_bounds__(BIG ? 512 : 1024, 1) forward_kernel(FwdArgs a)
 
         // with a final state requested, one more pass of the force phases at t = steps dt
         const long long last = a.steps + (a.final_state ? 1 : 0);
-        for (long long step = 0; step < last; ++step) {
-            const R tR = (R)(step * a.dt);
+        // 32-bit step count (steps < 2^31 - 1 by the argument checks), observation steps by a
+        // countdown (no 64-bit division in the loop), and the FP32 kernel's time in FP32, so
+        // that the loop issues no FP64 instruction outside observation steps
+        const int obs_every = (int)min(a.obs_every, (long long)INT_MAX);  // > steps: no observation
+        int obs_left = obs_every, obs_idx = 0;
+        const float dt_f = (float)a.dt;
+        for (int step = 0; step < (int)last; ++step) {
+            const R tR = F64 ? (R)((double)step * a.dt) : (R)((float)step * dt_f);
+            const bool obs_step = --obs_left == 0;
             int bad = 0;
             // ---- A+B: segments, tension, curvature stencils, relative positions.  Thread k
             //      forms e_k (tension of the segment to its next point) and again e_{k-1}
@@ -868,15 +876,11 @@ __global__ void __launch_bounds__(BIG ? 512 : 1024, 1) forward_kernel(FwdArgs a)
             if (!F64) __syncthreads();
             // ---- E: Euler step, divergence, observations
             for (int k = F64 ? (owner ? tgt : n) : tid; k < n; k += F64 ? n : T) {
-                const bool head_obs = !vel_obs(a, nh) && (k == nf - 1) && ((step + 1) % a.obs_every == 0);
-                double hxo = 0.0, hyo = 0.0;
                 if (F64) {
                     double dx = vxd * dt_mu, dy = vyd * dt_mu;  // displacement this step
                     if (!isfinite(dx) || !isfinite(dy) || fmax(fabs(dx), fabs(dy)) > ds) bad = 1;
                     sx[k] += dx;
                     sy[k] += dy;
-                    hxo = sx[k];
-                    hyo = sy[k];
                 } else {
                     // v_k = self term + the pair warps' partial sums, compensated
                     const float4 me = ((const float4 *)src)[((k >> 5) << 6) + (k & 31)];
@@ -897,21 +901,23 @@ __global__ void __launch_bounds__(BIG ? 512 : 1024, 1) forward_kernel(FwdArgs a)
                     two_sum(s, yl[k] + e, nh, nl);
                     yh[k] = nh;
                     yl[k] = nl;
-                    if (head_obs) {
-                        hxo = (double)xh[k] + (double)xl[k];
-                        hyo = (double)yh[k] + (double)yl[k];
-                    }
                 }
-                if (head_obs) {
-                    long long o = (step + 1) / a.obs_every - 1;
-                    hxo += xref;
-                    if (a.obs) {
-                        double rx = a.obs[2 * o] - hxo, ry = (a.obs[2 * o + 1] - hyo) / a.sigma_ratio;
-                        J = fma(rx, rx, fma(ry, ry, J));
-                    }
-                    if (a.head_traj) {
-                        a.head_traj[((size_t)b * n_obs + o) * 2] = hxo;
-                        a.head_traj[((size_t)b * n_obs + o) * 2 + 1] = hyo;
+                // the head point's observation: squared residual into J (FP64), trajectory row;
+                // obs_step is the same for every thread, so other steps branch around it
+                if (obs_step) {
+                    if (!vel_obs(a, nh) && k == nf - 1) {
+                        double hxo = F64 ? sx[k] : (double)xh[k] + (double)xl[k];
+                        const double hyo = F64 ? sy[k] : (double)yh[k] + (double)yl[k];
+                        const long long o = obs_idx;
+                        hxo += xref;
+                        if (a.obs) {
+                            double rx = a.obs[2 * o] - hxo, ry = (a.obs[2 * o + 1] - hyo) / a.sigma_ratio;
+                            J = fma(rx, rx, fma(ry, ry, J));
+                        }
+                        if (a.head_traj) {
+                            a.head_traj[((size_t)b * n_obs + o) * 2] = hxo;
+                            a.head_traj[((size_t)b * n_obs + o) * 2 + 1] = hyo;
+                        }
                     }
                 }
             }
@@ -920,7 +926,7 @@ __global__ void __launch_bounds__(BIG ? 512 : 1024, 1) forward_kernel(FwdArgs a)
                 steps_done = step + 1;
                 break;
             }
-            if (vel_obs(a, nh) && (step + 1) % a.obs_every == 0 && tid < 32) {
+            if (vel_obs(a, nh) && obs_step && tid < 32) {
                 double ox, oy;
                 if (TWO && a.obs_kind == SWIMMER_OBS_PAIR_DISTANCES) {
                     // distances between the tail tips and between the head centres (Sec. 4.2)
@@ -954,7 +960,7 @@ __global__ void __launch_bounds__(BIG ? 512 : 1024, 1) forward_kernel(FwdArgs a)
                     }
                 }
                 if (tid == 0) {
-                    const long long o = (step + 1) / a.obs_every - 1;
+                    const long long o = obs_idx;
                     if (a.obs) {
                         const double rx = a.obs[2 * o] - ox, ry = (a.obs[2 * o + 1] - oy) / a.sigma_ratio;
                         J = fma(rx, rx, fma(ry, ry, J));
@@ -964,6 +970,10 @@ __global__ void __launch_bounds__(BIG ? 512 : 1024, 1) forward_kernel(FwdArgs a)
                         a.head_traj[((size_t)b * n_obs + o) * 2 + 1] = oy;
                     }
                 }
+            }
+            if (obs_step) {
+                obs_left = obs_every;
+                ++obs_idx;
             }
         }
         // ---- outputs
