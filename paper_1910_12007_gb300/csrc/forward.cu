@@ -110,6 +110,19 @@ __device__ __forceinline__ void acc_two_sum(float &s, float &e, float b) {
     s = t;
 }
 
+// Integer to float and round-to-integer with FP32 adds alone (IEEE bias trick: adding 2^23 to
+// an integer-valued float, or 1.5 * 2^23 to a float, leaves it in the binade whose spacing is
+// 1), so the per-step O(N) work stays off GB300's narrow conversion pipe.
+__device__ __forceinline__ float small_int_to_float(int i) {  // exact for 0 <= i < 2^23
+    return __int_as_float(0x4B000000 | i) - 8388608.0f;
+}
+__device__ __forceinline__ float int_to_float(int i) {  // 0 <= i < 2^31, rounded to nearest
+    return fmaf(small_int_to_float(i >> 16), 65536.0f, small_int_to_float(i & 0xffff));
+}
+__device__ __forceinline__ float round_to_int(float t) {  // nearest integer, |t| < 2^22
+    return __fsub_rn(__fadd_rn(t, 12582912.0f), 12582912.0f);
+}
+
 // X_j - X_i of double-float coordinates (hi, lo) as a double-float (dh, dl)
 __device__ __forceinline__ void df_sub(const float *h, const float *l, int i, int j, float &dh, float &dl) {
     float s, e;
@@ -403,6 +416,10 @@ __global__ void __launch_bounds__(BIG ? 512 : 1024, 1) forward_kernel(FwdArgs a)
     // gap (end to H(pi))) as RestF64 or RestF32 records; then 1/(2 ds_H), 1/ds_H^2, 1/H_r,
     // 2 K_HC ds_H, 2 K_NA; [23, 25) the head centre at the previous observation
     __shared__ double s_model[26];
+    // FP32 kernel: the sample's single-precision constants (see below)
+    enum { F_DS, F_INV2DS, F_INVDS2, F_KC2DS, F_AMP, F_ETA, F_OMEGA, F_COS, F_ETA2, F_DSL, F_INVDELTA, F_DTMU, F_DT,
+           F_COUNT };
+    __shared__ float s_f32[F64 ? 1 : 16];
     const RestF32 *rest32 = (const RestF32 *)s_model;
     const RestF64 *rest64 = (const RestF64 *)s_model;
     enum { M_I2H = 18, M_IH2, M_IHR, M_KHC, M_KANG, M_CX, M_CY };
@@ -520,14 +537,25 @@ __global__ void __launch_bounds__(BIG ? 512 : 1024, 1) forward_kernel(FwdArgs a)
                 src[ks + 32] = R4{0, 0, 0, 0};
             }
         }
-        const double inv_ds2 = 1.0 / (ds * ds);
-        const R r_ds = (R)ds, r_inv2ds = (R)(0.5 / ds), r_invds2 = (R)inv_ds2;
-        const R kc2ds = (R)(2.0 * p.kc * ds);
-        const R r_amp = (R)p.amp, r_eta = (R)a.eta, r_omega = (R)a.omega, r_L = (R)L;
-        const R inv_d2 = (R)(1.0 / (p.delta * p.delta));
-        const float inv_delta_f = (float)(1.0 / p.delta);
+        // FP32 kernel: the sample's single-precision constants, made once here in FP64 and read
+        // from shared memory in the step loop (where, short of registers, the compiler would
+        // otherwise recompute them from the FP64 parameters every step)
+        if (!F64 && tid == 0) {
+            s_f32[F_DS] = (float)ds;
+            s_f32[F_INV2DS] = (float)(0.5 / ds);
+            s_f32[F_INVDS2] = (float)(1.0 / (ds * ds));
+            s_f32[F_KC2DS] = (float)(2.0 * p.kc * ds);
+            s_f32[F_AMP] = (float)p.amp;
+            s_f32[F_ETA] = (float)a.eta;
+            s_f32[F_OMEGA] = (float)a.omega;
+            s_f32[F_COS] = (float)(2.0 * a.eta / L);  // preferred curvature: 2 eta / L,
+            s_f32[F_ETA2] = (float)(a.eta * a.eta);   // eta^2,
+            s_f32[F_DSL] = (float)(ds / L);           // ds / L
+            s_f32[F_INVDELTA] = (float)(1.0 / p.delta);
+            s_f32[F_DTMU] = (float)(a.dt / a.mu);
+            s_f32[F_DT] = (float)a.dt;
+        }
         const double dt_mu = a.dt / a.mu;
-        const float dt_mu_f = (float)dt_mu, ds_f = (float)ds;
         // FP64 pair sum: thread -> (target, source split of S lanes)
         int S = 1;
         while (S < 32 && 2 * S * n <= T) S <<= 1;
@@ -546,6 +574,12 @@ __global__ void __launch_bounds__(BIG ? 512 : 1024, 1) forward_kernel(FwdArgs a)
         int status = SWIMMER_OK;
         long long steps_done = a.steps;
         __syncthreads();
+        const R r_ds = F64 ? (R)ds : (R)s_f32[F_DS], r_inv2ds = F64 ? (R)(0.5 / ds) : (R)s_f32[F_INV2DS];
+        const R r_invds2 = F64 ? (R)(1.0 / (ds * ds)) : (R)s_f32[F_INVDS2];
+        const R kc2ds = F64 ? (R)(2.0 * p.kc * ds) : (R)s_f32[F_KC2DS];
+        const R r_amp = F64 ? (R)p.amp : (R)s_f32[F_AMP], r_eta = F64 ? (R)a.eta : (R)s_f32[F_ETA];
+        const R r_omega = F64 ? (R)a.omega : (R)s_f32[F_OMEGA], r_L = (R)L;
+        const R inv_d2 = (R)(1.0 / (p.delta * p.delta));
         if (vel_obs(a, nh) && tid < 32) {  // head centre at the previous observation
             double cx, cy;
             head_centre<F64>(sx, sy, xh, xl, yh, yl, nf, nh, lane, cx, cy);
@@ -568,9 +602,8 @@ __global__ void __launch_bounds__(BIG ? 512 : 1024, 1) forward_kernel(FwdArgs a)
         // that the loop issues no FP64 instruction outside observation steps
         const int obs_every = (int)min(a.obs_every, (long long)INT_MAX);  // > steps: no observation
         int obs_left = obs_every, obs_idx = 0;
-        const float dt_f = (float)a.dt;
         for (int step = 0; step < (int)last; ++step) {
-            const R tR = F64 ? (R)((double)step * a.dt) : (R)((float)step * dt_f);
+            const R tR = F64 ? (R)((double)step * a.dt) : (R)(int_to_float(step) * s_f32[F_DT]);
             const bool obs_step = --obs_left == 0;
             int bad = 0;
             // ---- A+B: segments, tension, curvature stencils, relative positions.  Thread k
@@ -618,8 +651,8 @@ __global__ void __launch_bounds__(BIG ? 512 : 1024, 1) forward_kernel(FwdArgs a)
                         emy = (R)(s + lo);
                     }
                     // the pair sum measures separations in units of delta
-                    qx = (R)((xh[k] + xl[k]) * inv_delta_f);
-                    qy = (R)((yh[k] + yl[k]) * inv_delta_f);
+                    qx = (R)((xh[k] + xl[k]) * s_f32[F_INVDELTA]);
+                    qy = (R)((yh[k] + yl[k]) * s_f32[F_INVDELTA]);
                 }
                 if (next >= 0) {  // tension force vector of segment (k, next)
                     tvx[k] = tk * epx;
@@ -649,24 +682,22 @@ __global__ void __launch_bounds__(BIG ? 512 : 1024, 1) forward_kernel(FwdArgs a)
                     if (hd) {
                         zhat = (R)s_model[M_IHR];  // preferred head curvature 1/H_r
                     } else {
-                        R s = (R)kl * r_ds;
-                        R ph = r_eta * s - r_omega * tR;
-                        R sn, cs;
                         if (F64) {
+                            const R s = (R)kl * r_ds;
+                            const R ph = r_eta * s - r_omega * tR;
                             double sd, cd;
                             sincos((double)ph, &sd, &cd);
-                            sn = (R)sd;
-                            cs = (R)cd;
+                            zhat = -r_amp * ((R)2 * r_eta / r_L * (R)cd + ((R)1 - s / r_L) * r_eta * r_eta * (R)sd);
                         } else {
+                            const float klf = small_int_to_float(kl);
+                            float ph = (float)r_eta * (klf * (float)r_ds) - (float)r_omega * (float)tR;
                             // reduce to [-pi, pi], then the fast hardware approximation
-                            float pf = (float)ph;
-                            pf = fmaf(-6.28318530717958648f, rintf(pf * 0.159154943091895336f), pf);
+                            ph = fmaf(-6.28318530717958648f, round_to_int(ph * 0.159154943091895336f), ph);
                             float sf, cf;
-                            __sincosf(pf, &sf, &cf);
-                            sn = (R)sf;
-                            cs = (R)cf;
+                            __sincosf(ph, &sf, &cf);
+                            zhat = (R)(-(float)r_amp *
+                                       (s_f32[F_COS] * cf + (1.0f - klf * s_f32[F_DSL]) * s_f32[F_ETA2] * sf));
                         }
-                        zhat = -r_amp * ((R)2 * r_eta / r_L * cs + ((R)1 - s / r_L) * r_eta * r_eta * sn);
                     }
                     R ck = (hd ? (R)s_model[M_KHC] : kc2ds) * (zeta - zhat);
                     R za = D * S15 - (R)3 * A * cross * S25;
@@ -890,8 +921,8 @@ __global__ void __launch_bounds__(BIG ? 512 : 1024, 1) forward_kernel(FwdArgs a)
                         acc_two_sum(hx, lx, pv.x);
                         acc_two_sum(hy, ly, pv.y);
                     }
-                    float dx = (hx + lx) * dt_mu_f, dy = (hy + ly) * dt_mu_f;
-                    if (!isfinite(dx) || !isfinite(dy) || fmaxf(fabsf(dx), fabsf(dy)) > ds_f) bad = 1;
+                    float dx = (hx + lx) * s_f32[F_DTMU], dy = (hy + ly) * s_f32[F_DTMU];
+                    if (!isfinite(dx) || !isfinite(dy) || fmaxf(fabsf(dx), fabsf(dy)) > s_f32[F_DS]) bad = 1;
                     float s, e, nh, nl;
                     two_sum(xh[k], dx, s, e);
                     two_sum(s, xl[k] + e, nh, nl);
