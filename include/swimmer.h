@@ -180,7 +180,8 @@ int forward_batch(swimmer_handle *h, int B, const double *theta, const int *n_pt
  * power of two from the smallest that covers n_max up to 1024 or the shared-memory limit;
  * the extra threads take more pair units in FP32 and split the source loop in FP64) and
  * stores the fastest in the handle (in FP32C each threads value is timed plain, with
- * SWIMMER_SHAPE_WIDE and with SWIMMER_SHAPE_QUAD; the stored shape may carry a flag).  The samples are the caller's theta (device, [n_theta][3]
+ * SWIMMER_SHAPE_WIDE and with SWIMMER_SHAPE_QUAD; a flagged shape must be 2 % faster than the
+ * best so far to be kept; the stored shape may carry a flag).  The samples are the caller's theta (device, [n_theta][3]
  * FP64, rows repeated as needed) when given: batches whose runs differ in length (runs that
  * diverge and stop early) favour shapes with fewer resident samples, whose work queue
  * rebalances the SMs.  With theta NULL, b_max copies of a mid-prior swimmer are timed.
@@ -303,7 +304,8 @@ int tmcmc_tree_template(int M, double p_accept, int depth_cap, int *nodes, int *
  * 2: 1, 2 or 4 target blocks.  An off-diagonal block pair is two units (d0 = 0, 16).
  * mode 0: nb diagonal units, then every block pair {I, J} as one-target units in circulant
  * order.  mode 1 (2): block pairs grouped two (four) at a time around a shared source block
- * J, the rest as pairs, at most one left as a one-target pair, then the diagonal units.
+ * J, the rest as pairs, at most one left as a one-target pair, then the diagonal units; below
+ * 8 blocks mode 2 gives the mode 1 list.
  * out: host, at least nb^2 unsigned; *count = units written.  SWIMMER_E_ARG on bad
  * arguments. */
 int swimmer_pair_units(int nb, int mode, unsigned *out, int *count);

@@ -353,7 +353,8 @@ extern "C" int swimmer_autotune(swimmer_handle *h, int steps, const double *thet
                     cudaEventSynchronize(e1);
                     cudaEventElapsedTime(&ms, e0, e1);
                 }
-                if (ms < best) {
+                // a shape with more target blocks per unit has to win by 2 % (timing noise)
+                if (mode == 0 ? ms < best : ms < 0.98f * best) {
                     best = ms;
                     bestT = shape;
                 }

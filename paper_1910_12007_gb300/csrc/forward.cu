@@ -1078,9 +1078,13 @@ ForwardKernel forward_kernel_for(bool f64, const swimmer_config &c, bool big = f
 // blocks) around a shared block: blocks are visited from the last down, each takes its edges
 // to lower blocks plus those handed to it, and when their number is odd it hands one edge to
 // a lower block whose own count would otherwise be odd, so at most one edge stays alone, at
-// block 0.  Mode 2 hands edges down until a block's count is a multiple of four (as far as its
-// own edges to lower blocks allow) and takes them four at a time, the rest in pairs and alone.
+// block 0.  Mode 2 (from 8 blocks on) hands edges down until a block's count is a multiple of
+// four (as far as its own edges to lower blocks allow) and takes them four at a time, the rest
+// in pairs and alone.
 static std::vector<unsigned> build_pair_units(int nb, int mode) {
+    // below 8 blocks the edges of a block are too few to form four-target units; there mode 2
+    // takes the two-target list
+    if (mode == 2 && nb < 8) mode = 1;
     std::vector<unsigned> out;
     if (mode == 0) {
         for (int i = 0; i < nb; ++i) out.push_back(unit_pack(0, 2, i, i));

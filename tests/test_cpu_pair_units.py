@@ -65,12 +65,14 @@ def test_grouping(api, nb, mode):
     if mode == 1:
         assert len(singles) == 2 * (e % 2)  # at most one block pair stays alone
         assert all(len(u[0]) in (1, 2) for u in off)
+    elif nb < 8:
+        # too few blocks for four-target units: the two-target list
+        assert units == api.swimmer_pair_units(nb, 1)
     else:
-        # four-target units carry nearly every block pair once there are a few blocks
+        # four-target units carry nearly every block pair
         assert len(singles) <= 4
-        if nb >= 8:
-            quads = [u for u in off if len(u[0]) == 4]
-            assert 4 * len(quads) // 2 >= 0.9 * e
+        quads = [u for u in off if len(u[0]) == 4]
+        assert 4 * len(quads) // 2 >= 0.9 * e
     for targets, J, d0 in off:
         assert len(set(targets) | {J}) == len(targets) + 1 and d0 in (0, 16)
     # each unit's two halves (d0 = 0 and 16) come together
