@@ -21,9 +21,13 @@
 //      sums travel one lane per step with warp shuffles.  Sources (x/delta, y/delta, Fx,
 //      Fy) are one float4 per point, each block stored twice in a row so that the walk
 //      needs no wrap test; a pair's term is the symmetric 2x2 mobility
-//      M = delta^2 g2 e e^T - g1 I (e = d/delta) applied to F_j and to F_i.  Per-warp
-//      partial sums are combined in a fixed order with TwoSum, so results do not depend
-//      on scheduling.
+//      M = delta^2 g2 e e^T - g1 I (e = d/delta) applied to F_j and to F_i.  Launch
+//      shapes may group two or four block pairs {I, J} that share the source block J into
+//      one unit (each source load and rotation then serves two or four targets per lane);
+//      the host builds the unit lists per block count.  Per-warp partial sums are combined
+//      in a fixed order with TwoSum, so results do not depend on scheduling.  Launches
+//      whose shared memory holds an SM to one CTA of at most 512 threads use an
+//      instantiation compiled for 128 registers a thread.
 //      FP64: target i meets source i + d at step d (the point list stored twice), the S
 //      threads of a target splitting the sources and combining with warp shuffles;
 //   E  forward Euler X += dt v: FP64 positions in the FP64 kernel, double-float (hi + lo
