@@ -267,23 +267,26 @@ __global__ void prepare_kernel(int B, const double *__restrict__ theta, const in
     order[b] = b;
 }
 
-// Longest-first processing order for batches of uneven size (largest n first, the classic
-// LPT rule for the persistent work queue): counting sort by n in one CTA.  Samples with a
-// bad status go last (they do no work).
+// Longest-first processing order for the persistent work queue (the classic LPT rule):
+// batches of uneven size by n, largest first (a run costs n^2 per step); batches of one size
+// by ascending bending stiffness K_C, whose growth lowers forward Euler's stability limit, so
+// that the runs likely to stop early (DIVERGED) come last and the queue, which deals runs to
+// the SMs in turn, spreads them over the SMs.  Counting sort in one CTA (log10 K_C in 1024
+// buckets over [-5, 5]); samples with a bad status go last (they do no work).
 constexpr int SORT_THREADS = 1024;
+__device__ __forceinline__ int order_key(const SampleParams &p, bool by_kc) {
+    if (p.status != SWIMMER_OK) return N_PTS_MAX + 1;
+    if (by_kc) return min(max((int)floor((log10(p.kc) + 5.0) * 102.4), 0), N_PTS_MAX);
+    return N_PTS_MAX + 1 - min(max(p.n, 0), N_PTS_MAX);
+}
 __global__ void __launch_bounds__(SORT_THREADS) order_kernel(int B, const SampleParams *__restrict__ sp,
-                                                           int *__restrict__ order) {
+                                                           int *__restrict__ order, int by_kc) {
     __shared__ int cnt[N_PTS_MAX + 2];
     __shared__ int start[N_PTS_MAX + 2];
     const int tid = threadIdx.x;
     for (int i = tid; i < N_PTS_MAX + 2; i += SORT_THREADS) cnt[i] = 0;
     __syncthreads();
-    // key: bucket N_PTS_MAX + 1 - n for good samples (descending n), bucket N_PTS_MAX + 1 last
-    for (int b = tid; b < B; b += SORT_THREADS) {
-        const SampleParams p = sp[b];
-        int key = p.status == SWIMMER_OK ? N_PTS_MAX + 1 - min(max(p.n, 0), N_PTS_MAX) : N_PTS_MAX + 1;
-        atomicAdd(&cnt[key], 1);
-    }
+    for (int b = tid; b < B; b += SORT_THREADS) atomicAdd(&cnt[order_key(sp[b], by_kc)], 1);
     __syncthreads();
     if (tid == 0) {
         int acc = 0;
@@ -293,11 +296,7 @@ __global__ void __launch_bounds__(SORT_THREADS) order_kernel(int B, const Sample
         }
     }
     __syncthreads();
-    for (int b = tid; b < B; b += SORT_THREADS) {
-        const SampleParams p = sp[b];
-        int key = p.status == SWIMMER_OK ? N_PTS_MAX + 1 - min(max(p.n, 0), N_PTS_MAX) : N_PTS_MAX + 1;
-        order[atomicAdd(&start[key], 1)] = b;
-    }
+    for (int b = tid; b < B; b += SORT_THREADS) order[atomicAdd(&start[order_key(sp[b], by_kc)], 1)] = b;
 }
 
 // ---------------------------------------------------------------------------------
@@ -702,8 +701,8 @@ int launch_prepare(swimmer_handle *h, int B, const double *theta, const int *n_p
     prepare_kernel<<<(B + 127) / 128, 128, 0, s>>>(B, theta, n_pts, h->cfg, h->sp, h->order);
     CUDA_TRY(cudaGetLastError());
     prof_count(h, 1);
-    if (n_pts) {  // uneven sizes: longest first
-        order_kernel<<<1, SORT_THREADS, 0, s>>>(B, h->sp, h->order);
+    {  // longest first: by n for uneven sizes, else by K_C
+        order_kernel<<<1, SORT_THREADS, 0, s>>>(B, h->sp, h->order, n_pts ? 0 : 1);
         CUDA_TRY(cudaGetLastError());
         prof_count(h, 1);
     }

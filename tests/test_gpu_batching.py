@@ -69,6 +69,22 @@ def test_uneven_batch_independent_of_grouping():
     h.close()
 
 
+def test_uniform_batch_independent_of_processing_order():
+    # batches of one size are processed in ascending K_C (the runs likely to stop early last);
+    # a sample's result must not depend on that order or on which CTA takes it
+    B = 64
+    th = synthetic.prior_samples(12, (0.2, -1.0, 0.05), (8.0, 1.0, 0.15), B)
+    h = g.swimmer_init(_cfg(B, 1))
+    thd = torch.tensor(th, device=DEV)
+    traj, speed, st = g.forward_batch(h, thd)
+    perm = torch.tensor(np.random.default_rng(3).permutation(B), device=DEV)
+    traj_p, speed_p, st_p = g.forward_batch(h, thd[perm].contiguous())
+    torch.cuda.synchronize()
+    same = lambda a, b: torch.equal(torch.nan_to_num(a, nan=7.0), torch.nan_to_num(b, nan=7.0))  # noqa: E731
+    assert same(traj_p, traj[perm]) and torch.equal(st_p, st[perm]) and same(speed_p, speed[perm])
+    h.close()
+
+
 def test_graph_replay_equals_eager():
     th, ns = _batch(32, seed=5)
     h = g.swimmer_init(_cfg(32, 1))
