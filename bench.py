@@ -820,6 +820,11 @@ def posterior_workload(args, rank, local_rank):
     r64, r32 = results["fp64"], results["fp32c"]
     m64, s64 = np.array(r64["posterior_mean"]), np.array(r64["posterior_sd"])
     m32, s32 = np.array(r32["posterior_mean"]), np.array(r32["posterior_sd"])
+    # Monte Carlo standard error of the difference of two runs' means and sds: TMCMC keeps
+    # the weights' COV at 1, an effective sample size of B / 2 per population
+    ess = B_STAGE / 2.0
+    se_mean = np.sqrt(2.0) * s64 / np.sqrt(ess)
+    se_sd = np.sqrt(2.0) * s64 / np.sqrt(2.0 * ess)
     line = {"metric": METRIC, "value": r32["samples_per_s"], "unit": "TMCMC samples/s", "n_gpus": 1, "steps": 1,
             "warmup": 0, "ms_per_step": 1e3 * r32["seconds"], "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
@@ -831,6 +836,12 @@ def posterior_workload(args, rank, local_rank):
             "sd_rel_diff": (np.abs(s32 - s64) / s64).tolist(),
             "within_2pct": bool(np.all(np.abs(m32 - m64) <= 0.02 * np.abs(m64)) and
                                 np.all(np.abs(s32 - s64) <= 0.02 * s64)),
+            "mean_diff_in_mc_se": (np.abs(m32 - m64) / se_mean).tolist(),
+            "sd_diff_in_mc_se": (np.abs(s32 - s64) / se_sd).tolist(),
+            "within_2_mc_se": bool(np.all(np.abs(m32 - m64) <= 2 * se_mean) and np.all(np.abs(s32 - s64) <= 2 * se_sd)),
+            "note": "the runs share random streams; once one Metropolis decision differs (FP32 and FP64 "
+                    "log-likelihoods differ by rounding) the chains decorrelate and the moments differ by Monte "
+                    "Carlo error, ~4.4 % of a posterior sd for the mean at 1024 samples",
             "speedup_fp32_over_fp64": r32["samples_per_s"] / r64["samples_per_s"]}
     print(json.dumps(line), flush=True)
     return 0
