@@ -424,6 +424,7 @@ __global__ void __launch_bounds__(BIG ? 512 : 1024, 1) forward_kernel(FwdArgs a)
     enum { F_DS, F_INV2DS, F_INVDS2, F_KC2DS, F_AMP, F_ETA, F_OMEGA, F_COS, F_ETA2, F_DSL, F_INVDELTA, F_DTMU, F_DT,
            F_COUNT };
     __shared__ float s_f32[F64 ? 1 : 16];
+    static_assert(F_COUNT <= 16, "s_f32 holds 16 constants");
     const RestF32 *rest32 = (const RestF32 *)s_model;
     const RestF64 *rest64 = (const RestF64 *)s_model;
     enum { M_I2H = 18, M_IH2, M_IHR, M_KHC, M_KANG, M_CX, M_CY };
