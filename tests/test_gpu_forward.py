@@ -349,3 +349,28 @@ def test_uneven_full_batch_sampled():
         err = _velocity_error(traj[i], obs[k], np.array([[ps[k].length, 0.0]]), base.dt)
         assert err < 1e-4, (i, int(ns[i]), tuned, err)
     h.close()
+
+
+@pytest.mark.parametrize("shape", [512 | g.SHAPE_QUAD, 256 | g.SHAPE_WIDE])
+def test_ragged_sizes_multi_target_units(shape):
+    # sizes that are not multiples of 32 (a padded last block) up to the 1024-point maximum,
+    # in one launch whose shared memory makes it a 128-register launch; four- and two-target
+    # units over 1 .. 32 blocks; every run against the oracle, per-step head velocities
+    ds, steps = 1.0 / 255, 60
+    ns = np.array([1000, 777, 545, 300, 1024, 33, 65, 129], dtype=np.int32)
+    th = synthetic.prior_samples(21, (0.0, -1.0, 0.05), (10.0, 0.0, 0.2), len(ns))
+    dt = 1e-4 / 2 ** 12
+    h = g.swimmer_init(g.SwimmerConfig(n_max=1024, b_max=len(ns), ds_fixed=ds, dt=dt, steps=steps, obs_every=1,
+                                       precision=g.FP32C))
+    g.swimmer_tuning(h, g.FP32C, [shape] * 17)
+    traj, _, status = g.forward_batch(h, torch.tensor(th, device=DEV), torch.tensor(ns, device=DEV))
+    torch.cuda.synchronize()
+    traj = traj.cpu().numpy()
+    base = sw.SwimmerParams(n=1024, dt=dt, steps=steps, obs_every=1)
+    ps = [replace(base.with_theta(tuple(t)), n=int(n), length=(int(n) - 1) * ds) for t, n in zip(th, ns)]
+    obs, _, _, st = sw.run_c_batch(ps)
+    assert np.all(st == 0) and np.all(status.cpu().numpy() == 0)
+    for b in range(len(ns)):
+        err = _velocity_error(traj[b], obs[b], np.array([[ps[b].length, 0.0]]), dt)
+        assert err < 1e-4, (shape, int(ns[b]), err)
+    h.close()
