@@ -224,7 +224,11 @@ __host__ __device__ size_t state_bytes(int n_max, int threads) {
     if (F64) return align32(16 * (size_t)n_max) + 2 * 32 * (size_t)n_max + 8 * 8 * (size_t)n_max;
     const size_t nbm = (n_max + 31) / 32;
     size_t forces = 32 * (size_t)n_max, part = 256 * nbm * (size_t)pair_warps(n_max, threads);
-    return align32(16 * (size_t)n_max) + 1024 * nbm + align32(forces > part ? forces : part);
+    // (the same bytes are the pair-unit assignment's scratch at the start of a sample)
+    const size_t assign = 4 * (2 * nbm * nbm + 2 * 32);
+    size_t region = forces > part ? forces : part;
+    if (assign > region) region = assign;
+    return align32(16 * (size_t)n_max) + 1024 * nbm + align32(region);
 }
 
 // FP32: the sample's pair units (unit_pack), at most ceil(n_max/32)^2 ints after the table
@@ -364,6 +368,39 @@ __device__ __forceinline__ void pair_unit_multi(const float4 *__restrict__ s4, c
     mypart[(Jb << 5) + lane] = pa;
 }
 
+// The sample's pair units over its n_pw pair warps, longest processing time first: the list
+// runs from the heaviest kind down and each unit goes to the least loaded warp (ties to the
+// lower warp); the list is then regrouped warp by warp and wstart[w] .. wstart[w + 1] are warp
+// w's units.  A fixed assignment, so results stay independent of scheduling.  Costs: a unit's
+// pair evaluations per step relative to a one-target unit, as measured (two targets 1.8, four
+// 3.4).  scratch (shared memory): 2 n_units + 2 n_pw words.  One thread, once per sample.
+__device__ __forceinline__ void assign_units(unsigned *units, int n_units, int n_pw, unsigned *scratch,
+                                             int *wstart) {
+    unsigned *own = scratch, *tmp = scratch + n_units;
+    float *load = (float *)(tmp + n_units);
+    int *cnt = (int *)(load + n_pw);
+    for (int w = 0; w < n_pw; ++w) {
+        load[w] = 0.f;
+        cnt[w] = 0;
+    }
+    for (int u = 0; u < n_units; ++u) {
+        const int kind = (units[u] >> 27) & 3;
+        int best = 0;
+        for (int w = 1; w < n_pw; ++w)
+            if (load[w] < load[best]) best = w;
+        load[best] += kind == 0 ? 1.0f : kind == 1 ? 1.8f : 3.4f;
+        own[u] = best;
+        ++cnt[best];
+    }
+    wstart[0] = 0;
+    for (int w = 0; w < n_pw; ++w) {
+        wstart[w + 1] = wstart[w] + cnt[w];
+        cnt[w] = wstart[w];  // next slot of warp w
+    }
+    for (int u = 0; u < n_units; ++u) tmp[cnt[own[u]]++] = units[u];
+    for (int u = 0; u < n_units; ++u) units[u] = tmp[u];
+}
+
 // observations computed by warp 0 after a step (head-centre velocities, two-swimmer
 // distances) rather than by the thread that updates the proximal point
 __device__ __forceinline__ bool vel_obs(const FwdArgs &a, int nh) {
@@ -424,6 +461,8 @@ __global__ void __launch_bounds__(BIG ? 512 : 1024, 1) forward_kernel(FwdArgs a)
     enum { F_DS, F_INV2DS, F_INVDS2, F_KC2DS, F_AMP, F_ETA, F_OMEGA, F_COS, F_ETA2, F_DSL, F_INVDELTA, F_DTMU, F_DT,
            F_COUNT };
     __shared__ float s_f32[F64 ? 1 : 16];
+    // FP32 pair sum: warp w processes units [s_wstart[w], s_wstart[w + 1]) of the sample's list
+    __shared__ int s_wstart[F64 ? 1 : 33];
     static_assert(F_COUNT <= 16, "s_f32 holds 16 constants");
     const RestF32 *rest32 = (const RestF32 *)s_model;
     const RestF64 *rest64 = (const RestF64 *)s_model;
@@ -578,6 +617,9 @@ __global__ void __launch_bounds__(BIG ? 512 : 1024, 1) forward_kernel(FwdArgs a)
         double J = 0.0;
         int status = SWIMMER_OK;
         long long steps_done = a.steps;
+        __syncthreads();
+        if (!F64 && tid == 0)
+            assign_units((unsigned *)(tabraw + table_bytes<F64>(P)), n_units, n_pw, (unsigned *)part, s_wstart);
         __syncthreads();
         const R r_ds = F64 ? (R)ds : (R)s_f32[F_DS], r_inv2ds = F64 ? (R)(0.5 / ds) : (R)s_f32[F_INV2DS];
         const R r_invds2 = F64 ? (R)(1.0 / (ds * ds)) : (R)s_f32[F_INVDS2];
@@ -882,7 +924,8 @@ __global__ void __launch_bounds__(BIG ? 512 : 1024, 1) forward_kernel(FwdArgs a)
                 // lanes l and l + 16 meet the same pair); off-diagonal blocks run d = 0 .. 31
                 // as two units.  A two- or four-target unit (wide and quad launch shapes)
                 // walks the block pairs {I, J}, {I2, J} (, {I3, J}, {I4, J}) together, sharing
-                // the source loads and rotations.  Each
+                // the source loads and rotations.  Units go to warps by the sample's fixed
+                // longest-processing-time assignment (above).  Each
                 // warp adds its units' sums into its own partial array, in a fixed order, so
                 // the result does not depend on scheduling.
                 const float4 *s4 = (const float4 *)src;
@@ -892,7 +935,7 @@ __global__ void __launch_bounds__(BIG ? 512 : 1024, 1) forward_kernel(FwdArgs a)
                 float2 *mypart = part + warp * (nb << 5);
                 for (int k = lane; k < (nb << 5); k += 32) mypart[k] = make_float2(0.f, 0.f);
                 const unsigned *units = (const unsigned *)(tabraw + table_bytes<F64>(P));
-                for (int un = warp; un < n_units; un += n_pw) {
+                for (int un = s_wstart[warp]; un < s_wstart[warp + 1]; ++un) {
                     const unsigned pk = units[un];
                     const int I = pk & 31, Jb = (pk >> 5) & 31, code = (pk >> 25) & 3, kind = (pk >> 27) & 3;
                     const int d0 = code == 2 ? 1 : code << 4;
@@ -1186,7 +1229,8 @@ int upload_pair_units(swimmer_handle *h) {
 
 // Threads per sample: at least one per target (FP64) or one warp per pair unit (FP32);
 // more when the batch is too small to fill the GPU, so that the per-step latency of a lone
-// sample shrinks, as long as the shared memory fits.  The autotuned choice wins.
+// sample shrinks, as long as the shared memory fits; FP32 pair units as measured best for
+// the sample size.  The autotuned choice wins.
 bool forward_fits(const swimmer_handle *h, int threads, int precision) {
     const bool f64 = precision == SWIMMER_FP64;
     const int P = handle_octaves(h) * (f64 ? F64_SUB : F32_SUB);
@@ -1241,6 +1285,10 @@ int forward_threads(const swimmer_handle *h, int B, int precision) {
     }
     while (T < cap && (long long)B * T * 2 <= (long long)h->num_sms * 1024 && forward_fits(h, 2 * T, precision))
         T <<= 1;
+    // two-target units (measured): from 8 blocks of 32 points at every thread count, and from 4
+    // blocks when the batch fills the GPU (the heuristic stays at 128 threads only then)
+    const int nbm = (h->cfg.n_max + 31) / 32;
+    if (precision != SWIMMER_FP64 && (nbm >= 8 || (nbm >= 4 && T == 128))) return T | SHAPE_WIDE;
     return T;
 }
 
