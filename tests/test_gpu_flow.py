@@ -1,5 +1,5 @@
 """GPU parity of the final state and of the flow and pressure at target points (Eqs. BrP,
-BrV; SURVEY next row NEXT-4) against the oracle through the C ABI: final positions and the
+BrV) against the oracle through the C ABI: final positions and the
 forces there (FP64 1e-10, FP32 1e-3 on displacement), the flow field from a GPU final state
 (FP64 table against the oracle's, 1e-9), and the flow of the sperm model's final state."""
 import math

@@ -1,5 +1,4 @@
-"""Pins of the oracle's flow and pressure at target points (Eqs. BrP, BrV; SURVEY next row
-NEXT-4): the pressure kernel against quadrature of the blob, its singular far field, the
+"""Pins of the oracle's flow and pressure at target points (Eqs. BrP, BrV): the pressure kernel against quadrature of the blob, its singular far field, the
 velocity field's zero divergence (incompressible Brinkman flow), and agreement with the pair
 sum at the swimmer's own points."""
 import math
