@@ -433,8 +433,14 @@ def swimmer_kernel_eval_noalloc(alpha, delta, r_max, r: torch.Tensor, precision=
     _dev(r, torch.float64)
     g1 = torch.empty_like(r) if g1 is None else g1
     g2 = torch.empty_like(r) if g2 is None else g2
-    check(lib().swimmer_kernel_eval_noalloc(float(alpha), float(delta), float(r_max), r.numel(), _ptr(r),
-                                            _ptr(g1), _ptr(g2), int(precision), _stream(stream)))
+    # the kernel writes r.numel() doubles into each output on r's device
+    for name, t in (("g1", g1), ("g2", g2)):
+        _dev(t, torch.float64)
+        if t.numel() != r.numel() or t.device != r.device:
+            raise ValueError(f"{name} must hold {r.numel()} doubles on {r.device}")
+    with torch.cuda.device(r.device):
+        check(lib().swimmer_kernel_eval_noalloc(float(alpha), float(delta), float(r_max), r.numel(), _ptr(r),
+                                                _ptr(g1), _ptr(g2), int(precision), _stream(stream)))
     return g1, g2
 
 

@@ -778,6 +778,13 @@ int noalloc_setup(int dev, NoallocPtrs *out) {
         CUDA_TRY(cudaGetSymbolAddress((void **)&p.sp, g_noalloc_sp));
         CUDA_TRY(cudaFuncSetAttribute(table_build_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)(4 * (size_t)NODES_MAX * sizeof(double))));
+        // load every kernel of the call now: with lazy module loading a kernel first launched
+        // later (kernel_eval_kernel after calls with m = 0) would load its code then
+        cudaFuncAttributes fa;
+        CUDA_TRY(cudaFuncGetAttributes(&fa, set_sample_kernel));
+        CUDA_TRY(cudaFuncGetAttributes(&fa, table_integrals_kernel));
+        CUDA_TRY(cudaFuncGetAttributes(&fa, table_build_kernel));
+        CUDA_TRY(cudaFuncGetAttributes(&fa, kernel_eval_kernel));
         p.ready = true;
     }
     *out = p;

@@ -95,3 +95,21 @@ def test_seeded_inputs_are_deterministic():
     z = synthetic.normals(7, synthetic.PROPOSAL, 0, 20000)
     assert abs(z.mean()) < 0.03 and abs(z.std() - 1) < 0.03
     assert not np.array_equal(a, synthetic.uniforms(7, synthetic.RESAMPLE, 4, 1000))
+
+
+def test_noalloc_binding_rejects_host_buffers_before_any_call(monkeypatch):
+    """The allocation-free entry point's binding checks every buffer on the host: tensors that
+    are not contiguous FP64 device memory are refused before the library is called."""
+    torch = pytest.importorskip("torch")
+    from paper_1910_12007_gb300 import _lib, api
+
+    def no_library():
+        raise AssertionError("the library must not be called")
+
+    monkeypatch.setattr(_lib, "lib", no_library)
+    monkeypatch.setattr(api, "lib", no_library)
+    r = torch.zeros(8, dtype=torch.float64)
+    with pytest.raises(TypeError):
+        api.swimmer_kernel_eval_noalloc(1.0, 0.02, 1.0, r)
+    with pytest.raises(TypeError):
+        api.swimmer_kernel_eval_noalloc(1.0, 0.02, 1.0, r.float())

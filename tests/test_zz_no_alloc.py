@@ -51,3 +51,36 @@ def test_noalloc_rejects_sizes_beyond_its_limit():
     r = torch.zeros(4, dtype=torch.float64, device=DEV)
     with pytest.raises(RuntimeError, match="beyond"):
         g.swimmer_kernel_eval_noalloc(1.0, 1e-4, 1.0, r)  # r_max/delta = 1e4 > 4000
+
+
+def test_noalloc_leaves_device_memory_unchanged():
+    """After the first call on the device (its one-time set-up), further calls with
+    preallocated outputs take no device memory: the free memory the driver reports stays the
+    same over repeated calls."""
+    delta, r_max = 1.5 / 127, 1.25
+    r = _points(delta, r_max, 3)
+    out1, out2 = torch.empty_like(r), torch.empty_like(r)
+    g.swimmer_kernel_eval_noalloc(1.0, delta, r_max, r, 1, g1=out1, g2=out2)
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    for alpha in (0.5, 3.0, 7.5, 0.0):
+        for precision in (0, 1):
+            g.swimmer_kernel_eval_noalloc(alpha, delta, r_max, r, precision, g1=out1, g2=out2)
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0
+    assert torch.isfinite(out1).all() and torch.isfinite(out2).all()
+
+
+def test_noalloc_rejects_bad_outputs_before_launch():
+    r = torch.linspace(0.0, 1.0, 16, dtype=torch.float64, device=DEV)
+    good = torch.full_like(r, float("nan"))
+    bad = [torch.empty(16, dtype=torch.float32, device=DEV),  # wrong dtype
+           torch.empty(15, dtype=torch.float64, device=DEV),  # too short
+           torch.empty(32, dtype=torch.float64, device=DEV)[::2],  # not contiguous
+           torch.empty(16, dtype=torch.float64)]  # host memory
+    for b in bad:
+        with pytest.raises((TypeError, ValueError)):
+            g.swimmer_kernel_eval_noalloc(1.0, 0.02, 1.0, r, 0, g1=good, g2=b)
+    torch.cuda.synchronize()
+    assert torch.isnan(good).all()  # nothing ran
