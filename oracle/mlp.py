@@ -8,7 +8,7 @@ normalized (alpha, log10 K_C, a, log10 K_T, omega) to 40 normalized head positio
 
 Parameters are a list of (W[out, in], b[out]).  GELU(x) = x Phi(x) = x (1 + erf(x/sqrt 2))/2.
 
-Pins (tests/test_oracle_mlp.py): gradients against central finite differences of the
+Pins (in tests/test_oracle_tmcmc.py, the MLP tests): gradients against central finite differences of the
 loss; GELU derivative against finite differences; an Adam step against its textbook
 formula on one scalar.
 """
@@ -95,3 +95,37 @@ def bf16_round(a):
     lsb = (u >> np.uint64(16)) & np.uint64(1)
     u = (u + np.uint64(0x7FFF) + lsb) & np.uint64(0xFFFF0000)
     return u.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def surrogate_inputs(theta, in_lo, in_hi, log10_kt, omega):
+    """The network's inputs for theta rows (alpha, log10 K_C, a[, s]): the vector
+    (alpha, log10 K_C, a, log10 K_T, omega) mapped affinely from [in_lo, in_hi] to [-1, 1]
+    (0 where the range is empty), rounded to FP32 as the network receives them."""
+    th = np.asarray(theta, dtype=np.float64)
+    v = np.concatenate([th[:, :3], np.full((th.shape[0], 1), log10_kt), np.full((th.shape[0], 1), omega)], 1)
+    lo = np.asarray(in_lo, dtype=np.float64)
+    hi = np.asarray(in_hi, dtype=np.float64)
+    span = hi - lo
+    x = np.where(span > 0, 2.0 * (v - lo) / np.where(span > 0, span, 1.0) - 1.0, 0.0)
+    return x.astype(np.float32).astype(np.float64)
+
+
+def surrogate_loglik(params, theta, in_lo, in_hi, out_mean, out_std, obs_stride, log10_kt, omega, D, sigma):
+    """Surrogate log-likelihood used by delayed acceptance (not in the paper).
+
+    The network predicts the head position at 40 observation times, rows
+    o * obs_stride + obs_stride - 1 of the observation record D [n_obs, 2]:
+    p = out_mean + out_std * y.  The misfit over those rows is scaled to the full record,
+    J = (n_obs / 40) sum |D_row - p|^2, and enters the Gaussian log-likelihood of Sec. 3.1
+    (Eqs. likelihood, fitness): -(m/2) ln(2 pi sigma^2) - J / (2 sigma^2), m = 2 n_obs.
+    With a fourth unknown the sample's sigma is theta[3] times sigma."""
+    th = np.asarray(theta, dtype=np.float64)
+    y = forward(params, surrogate_inputs(th, in_lo, in_hi, log10_kt, omega))
+    pred = np.asarray(out_mean)[None, :] + np.asarray(out_std)[None, :] * y
+    D = np.asarray(D, dtype=np.float64)
+    n_obs = D.shape[0]
+    k = pred.shape[1] // 2
+    rows = np.arange(k) * obs_stride + obs_stride - 1
+    J = np.sum((D[rows][None, :, :] - pred.reshape(-1, k, 2)) ** 2, axis=(1, 2)) * (n_obs / k)
+    s = sigma * th[:, 3] if th.shape[1] == 4 else np.full(th.shape[0], float(sigma))
+    return -n_obs * np.log(2.0 * math.pi * s * s) - 0.5 * J / (s * s)

@@ -111,3 +111,27 @@ def test_log_likelihood_hand_computed():
     expect = -0.5 * 6 * math.log(2 * math.pi * 0.04) - 0.5 * J
     assert abs(sw.log_likelihood(g, D, sigma) - expect) < 1e-12
     assert sw.noise_sigma(np.array([1.0, -3.0]), 0.05) == pytest.approx(0.1)
+
+
+@pytest.mark.parametrize("alpha", [0.0, 1.0, 5.0])
+def test_energy_decreases_along_the_flow_with_a_static_preferred_shape(alpha):
+    """With omega = 0 the preferred curvature does not move, so E(X) (Eqs. EFB, EFT) is a
+    fixed function of the positions and dE/dt = grad E . v = -F . M F <= 0: the Brinkmanlet
+    mobility of Eq. BrV is positive semi-definite (its Fourier symbol is the blob's positive
+    transform times the Brinkman propagator).  Forward Euler at a step well inside its
+    stability bound keeps the decrease step by step.  A flipped velocity (v = -M F) would
+    raise the energy at every step."""
+    p = sw.SwimmerParams(n=24, dt=5e-5, omega=0.0, amp=0.1, alpha=alpha, k_c=1.0)
+    table = sw.kernel_table(p)
+    X = sw.initial_shape(p)
+    E = [sw.energy(X, p, 0.0)]
+    for _ in range(150):
+        F = sw.forces(X, p, 0.0)
+        X = X + p.dt * sw.velocity(X, F, table, p.mu)
+        E.append(sw.energy(X, p, 0.0))
+    E = np.array(E)
+    assert np.all(np.diff(E) <= 1e-12 * E[0])
+    assert E[-1] < 0.5 * E[0]  # the filament relaxes toward its preferred shape
+    # and the same run through the oracle's own time loop ends in the same state
+    _, X_loop, status = sw.run_numpy(replace(p, steps=150, obs_every=150), table)
+    assert status == 0 and np.allclose(X_loop, X, rtol=0, atol=1e-14)

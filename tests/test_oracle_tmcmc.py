@@ -196,3 +196,33 @@ def test_bf16_rounding():
     assert r[1] == 1.0          # halfway, rounds to even
     assert r[2] == 1.0078125    # above halfway rounds up
     assert abs(r[3] / v[3] - 1) < 2 ** -8
+
+
+def test_surrogate_loglik_reduces_to_the_gaussian_likelihood():
+    """With all weights and biases zero the network outputs 0, so the surrogate predicts
+    out_mean: its log-likelihood is then the Gaussian likelihood (Sec. 3.1) of that fixed
+    trajectory.  With 80 observation rows and stride 2 the misfit over the 40 used rows is
+    doubled, which is the full-record likelihood when both rows of each pair agree."""
+    from oracle import mlp as om
+    from oracle import swimmer as sw
+
+    rng = np.random.default_rng(4)
+    zero = [(np.zeros_like(W), np.zeros_like(b)) for W, b in om.init_params(rng)]
+    lo, hi = [0.0, -1.0, 0.05, 3.0, 6.0], [10.0, 1.0, 0.2, 3.0, 6.0]
+    theta = rng.uniform([0.0, -1.0, 0.05], [10.0, 1.0, 0.2], size=(5, 3))
+    pred = rng.normal(size=80)
+    D40 = pred.reshape(40, 2) + 0.01 * rng.normal(size=(40, 2))
+    ll = om.surrogate_loglik(zero, theta, lo, hi, pred, np.ones(80), 1, 3.0, 6.0, D40, 0.02)
+    ref = sw.log_likelihood(pred.reshape(40, 2), D40, 0.02)
+    assert np.allclose(ll, ref, rtol=1e-13)
+    D80 = np.repeat(D40, 2, axis=0)  # rows 1, 3, 5, ... are the ones used with stride 2
+    ll2 = om.surrogate_loglik(zero, theta, lo, hi, pred, np.ones(80), 2, 3.0, 6.0, D80, 0.02)
+    ref2 = sw.log_likelihood(np.repeat(pred.reshape(40, 2), 2, axis=0), D80, 0.02)
+    assert np.allclose(ll2, ref2, rtol=1e-13)
+    # a fourth unknown scales sigma per sample
+    th4 = np.column_stack([theta, np.full(5, 0.5)])
+    ll4 = om.surrogate_loglik(zero, th4, lo, hi, pred, np.ones(80), 1, 3.0, 6.0, D40, 0.04)
+    assert np.allclose(ll4, ref, rtol=1e-13)
+    # the inputs: box ends map to -1 and +1, an empty range to 0, rounded to FP32
+    x = om.surrogate_inputs(np.array([[0.0, 1.0, 0.125]]), lo, hi, 3.0, 6.0)
+    assert np.allclose(x, [[-1.0, 1.0, 0.0, 0.0, 0.0]], rtol=0, atol=1e-15)
