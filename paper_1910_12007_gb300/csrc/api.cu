@@ -159,6 +159,7 @@ extern "C" int swimmer_init(const swimmer_config *cfg, swimmer_handle **out) {
     ALLOC(h->tab64, (size_t)B * TAB64_STRIDE);
     ALLOC(h->k1_scratch, (size_t)B * K1_SCRATCH);
     ALLOC(h->tab32, (size_t)B * TAB32_STRIDE);
+    ALLOC(h->pq, (size_t)B * cfg->n_max);
     ALLOC(h->sp, B);
     ALLOC(h->order, B);
     ALLOC(h->queue, 4);
@@ -218,7 +219,7 @@ extern "C" int swimmer_init(const swimmer_config *cfg, swimmer_handle **out) {
 extern "C" int swimmer_destroy(swimmer_handle *h) {
     if (!h) return 0;
     cudaDeviceSynchronize();
-    void *ptrs[] = {h->tab64, h->k1_scratch, h->tab32, h->sp, h->order, h->queue, h->speed_tmp, h->w, h->stats,
+    void *ptrs[] = {h->tab64, h->k1_scratch, h->tab32, h->pq, h->sp, h->order, h->queue, h->speed_tmp, h->w, h->stats,
                     h->idx, h->counts, h->chain_id, h->chain_off, h->chain_len, h->aux,
                     h->cur_theta, h->cur_ll, h->cur_sl, h->prop_theta, h->prop_ll, h->prop_sl,
                     h->out_theta, h->out_ll, h->out_sl, h->prop_status, h->live, h->chain_pos, h->tmpl, h->cum, h->info, h->work, h->run_work,

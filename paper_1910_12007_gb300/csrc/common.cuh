@@ -106,6 +106,7 @@ struct swimmer_handle {
     double *tab64;          // [b_max][TAB64_STRIDE]
     double *k1_scratch;     // [b_max][K1_SCRATCH] interval integrals of the table build
     float4 *tab32;          // [b_max][TAB32_STRIDE]
+    float2 *pq;             // [b_max][n_max] FP32 kernel: preferred-curvature coefficients
     SampleParams *sp;       // [b_max]
     int *order;             // [b_max] processing order (longest first)
     int *queue;             // [4] work counters

@@ -7,8 +7,10 @@
 //      the double-float positions in the FP32 kernel);
 //   B  (same pass) nonlinear curvature zeta_k (Eq. curva) from central differences,
 //      preferred curvature zeta^_k(t), and c_k d zeta_k / d X_{k-1,k,k+1} with
-//      c_k = 2 K_C ds (zeta - zeta^) (gradient of Eq. EFB); the FP32 kernel uses the
-//      hardware reciprocal square root and, after reduction to [-pi, pi], sine/cosine;
+//      c_k = 2 K_C ds (zeta - zeta^) (gradient of Eq. EFB).  The FP32 kernel takes the
+//      second differences from the double-float segments before rounding them, uses the
+//      hardware reciprocal square root, and forms zeta^_k = P_k cos(omega t) +
+//      Q_k sin(omega t) from per-run FP64 coefficients and an FP64 rotation of the phase;
 //   C  point forces F = -dE/dX (Eq. Fenergy) gathered from the stencils;
 //   D  Brinkmanlet pair sum (Eq. BrV) v_i = (1/mu) sum_j [-F_j g1 + (F_j . d) d g2],
 //      d = X_i - X_j, with g1, g2 from the per-sample shared-memory table (quadratic in
@@ -18,9 +20,10 @@
 //      (I, J) along diagonals: lane l holds target I*32 + l and meets source
 //      J*32 + (l + d) mod 32 at step d, so all lanes look up nearly the same table panel
 //      (|d| ds apart on a smooth filament) and the loads broadcast, while the source-side
-//      sums travel one lane per step with warp shuffles.  Sources (x/delta, y/delta, Fx,
-//      Fy) are one float4 per point, each block stored twice in a row so that the walk
-//      needs no wrap test; a pair's term is the symmetric 2x2 mobility
+//      sums travel down the lanes with warp shuffles.  Two consecutive steps run together
+//      in the packed FP32 instructions (fma/mul .f32x2: two FMAs per issued instruction),
+//      the sources (x/delta, y/delta, Fx, Fy) stored as pair records of a point and its
+//      successor in the block; a pair's term is the symmetric 2x2 mobility
 //      M = delta^2 g2 e e^T - g1 I (e = d/delta) applied to F_j and to F_i.  Launch
 //      shapes may group two or four block pairs {I, J} that share the source block J into
 //      one unit (each source load and rotation then serves two or four targets per lane);
@@ -56,6 +59,7 @@ struct FwdArgs {
     int *queue;
     const double *tab64;
     const float4 *tab32;
+    float2 *pq;  // FP32 kernel: [B][n_max] preferred-curvature coefficients (P_k, Q_k) per run
     double mu, dt, kt, eta, omega;
     double hr_over_ds, gap_over_ds, k_head_tens, k_head_c, k_neck_tens, k_neck_ang;  // head model
     int obs_kind;
@@ -114,19 +118,6 @@ __device__ __forceinline__ void acc_two_sum(float &s, float &e, float b) {
     s = t;
 }
 
-// Integer to float and round-to-integer with FP32 adds alone (IEEE bias trick: adding 2^23 to
-// an integer-valued float, or 1.5 * 2^23 to a float, leaves it in the binade whose spacing is
-// 1), so the per-step O(N) work stays off GB300's narrow conversion pipe.
-__device__ __forceinline__ float small_int_to_float(int i) {  // exact for 0 <= i < 2^23
-    return __int_as_float(0x4B000000 | i) - 8388608.0f;
-}
-__device__ __forceinline__ float int_to_float(int i) {  // 0 <= i < 2^31, rounded to nearest
-    return fmaf(small_int_to_float(i >> 16), 65536.0f, small_int_to_float(i & 0xffff));
-}
-__device__ __forceinline__ float round_to_int(float t) {  // nearest integer, |t| < 2^22
-    return __fsub_rn(__fadd_rn(t, 12582912.0f), 12582912.0f);
-}
-
 // X_j - X_i of double-float coordinates (hi, lo) as a double-float (dh, dl)
 __device__ __forceinline__ void df_sub(const float *h, const float *l, int i, int j, float &dh, float &dl) {
     float s, e;
@@ -163,7 +154,8 @@ __host__ __device__ inline RestF64 rest_f64(double l0, double k) {
 }
 
 __device__ __forceinline__ float spring_f32(const float *xh, const float *xl, const float *yh, const float *yl, int i,
-                                            int j, const RestF32 &r, float &ex, float &ey, float &strain) {
+                                            int j, const RestF32 &r, float &ex, float &ey, float &exl_out,
+                                            float &eyl_out, float &strain) {
     float exh, exl, eyh, eyl;
     df_sub(xh, xl, i, j, exh, exl);
     df_sub(yh, yl, i, j, eyh, eyl);
@@ -180,6 +172,8 @@ __device__ __forceinline__ float spring_f32(const float *xh, const float *xl, co
     float ell = r.l0 * (1.0f + strain);
     ex = exh;
     ey = eyh;
+    exl_out = exl;
+    eyl_out = eyl;
     return __fdividef(r.k2 * strain, ell);
 }
 
@@ -215,8 +209,9 @@ __host__ __device__ inline int pair_warps(int n_max, int threads) {
 // Per-step state in shared memory.
 // FP64: positions sx, sy [n_max] (double); sources (x, y, Fx, Fy) [2 n_max] (the point list
 //   twice in a row); tension vectors tx, ty [n_max]; six bending terms [6][n_max].
-// FP32: positions xh, xl, yh, yl [n_max]; sources per block of 32 points, each block stored
-//   twice in a row ([nbm][64] float4); tension vectors and bending terms [8][n_max], which
+// FP32: positions xh, xl, yh, yl [n_max]; sources per block of 32 points as two planes of
+//   pair records ([nbm][2][32] float4, plane_a / plane_b); tension vectors and bending terms
+//   [8][n_max], which
 //   during the pair sum hold the per-warp partial velocities [pair warps][nbm * 32] (float2)
 //   instead, the region growing when those need more room.
 template <bool F64>
@@ -239,10 +234,10 @@ __host__ __device__ size_t smem_bytes(int n_max, int P, int threads) {
 }
 
 
-// g1 and h = delta^2 g2 from the FP32 table: quadratic in G = 1 + f / 64, f in [0, 1) the
-// position of u within its panel
+// -g1 and h = delta^2 g2 from the FP32 table: quadratic in G = 1 + f / 64, f in [0, 1) the
+// position of u within its panel.  The table holds -g1, the sign g1 takes in the mobility.
 __device__ __forceinline__ void kern_f32(const float4 *__restrict__ tA, const float2 *__restrict__ tB, int pmax,
-                                         float u, float &g1, float &g2) {
+                                         float u, float &gn, float &h) {
     // u >= 1: the panel is (exponent - 127) * panels per octave + top mantissa bits; the
     // exponent bias is subtracted after the clamp, where it folds into the load offsets.  G
     // is u's mantissa with the panel bits cleared (one logic operation).
@@ -252,120 +247,104 @@ __device__ __forceinline__ void kern_f32(const float4 *__restrict__ tA, const fl
     const float G = __uint_as_float(0x3f800000u | (bits & ((1u << (23 - F32_SUB_LOG2)) - 1u)));
     const float4 a = tA[p - BIAS];
     const float2 c = tB[p - BIAS];
-    g1 = fmaf(G, fmaf(G, a.z, a.y), a.x);
-    g2 = fmaf(G, fmaf(G, c.y, c.x), a.w);
+    gn = fmaf(G, fmaf(G, a.z, a.y), a.x);
+    h = fmaf(G, fmaf(G, c.y, c.x), a.w);
 }
 
+__device__ __forceinline__ float2 dup2(float v) { return make_float2(v, v); }
 
-// One pair's 2x2 mobility M = h e e^T - g1 I (e = d / delta, h = delta^2 g2), symmetric
-// and even in e: v_i += M F_j and v_j += M F_i (Eq. BrV).  Sources and targets hold
-// positions in units of delta, so u = 1 + |e|^2 needs no scaling.
-struct Mob {
-    float m11, m12, m22;
-};
-__device__ __forceinline__ Mob pair_mob(const float4 *__restrict__ t1, const float2 *__restrict__ t2, int pmax,
-                                        float ex, float ey, float mask) {
-    const float u = fmaf(ex, ex, fmaf(ey, ey, 1.0f));
-    float g1, h;
-    kern_f32(t1, t2, pmax, u, g1, h);
-    g1 *= mask;
-    h *= mask;
-    const float hx = h * ex, hy = h * ey;
-    return Mob{fmaf(hx, ex, -g1), hx * ey, fmaf(hy, ey, -g1)};
-}
+// Sources of the FP32 pair sum, per block of 32 points, in two planes of pair records:
+// plane A entry i holds (x_i, x_{i+1}, y_i, y_{i+1}) and plane B (Fx_i, Fx_{i+1}, Fy_i,
+// Fy_{i+1}), positions in units of delta, i + 1 taken modulo 32 within the block.  One 16-byte
+// load brings the two sources a lane meets on two consecutive steps of the diagonal walk,
+// already paired for the packed FP32 instructions (two FMAs per instruction).
+__device__ __forceinline__ int plane_a(int k) { return ((k >> 5) << 6) + (k & 31); }
+__device__ __forceinline__ int plane_b(int k) { return ((k >> 5) << 6) + 32 + (k & 31); }
+__device__ __forceinline__ int plane_prev(int k) { return (k & ~31) | ((k - 1) & 31); }
 
-// One FP32 pair unit of 16 diagonal steps: lane l holds target I*32 + l and at step
-// d = d0 .. d0+15 meets source J*32 + (l + d) mod 32; the source-side sums rotate one lane
-// per step.  A diagonal block (I = J) runs d = 1 .. 16, and at d = 16 only lanes < 16 count
-// (lanes l and l + 16 meet the same pair there).  Adds the unit's sums into the warp's
-// partial array.
+// One FP32 pair unit of 16 diagonal steps: lane l holds targets I_r*32 + l, r < R (the I_r
+// and J distinct blocks, or R = 1 and I = J for a diagonal block), and at step d = d0 ..
+// d0+15 meets source J*32 + (l + d) mod 32; one source load serves R pair evaluations.  Two
+// consecutive steps run together in the two halves of the packed FP32 instructions: half 0
+// is step d, half 1 step d + 1.  Each pair's term is the symmetric 2x2 mobility
+// M = h e e^T - g1 I (e = d / delta, h = delta^2 g2), even in e (Eq. BrV): v_i += M F_j and
+// v_j += M F_i.  The source-side sums travel with their sources: after each pair of steps
+// both halves move two lanes down, so lane l always holds, in half 0, the sum (over the even
+// steps) of the source it meets next on an even step and, in half 1, the odd-step sum of the
+// source after it; at the end each source's two sums are brought to its own lane.  A
+// diagonal block runs d = 1 .. 16, and at d = 16 only lanes < 16 count (lanes l and l + 16
+// meet the same pair there).  Adds the unit's sums into the warp's partial array.
+template <int R, bool DIAG>
 __device__ __forceinline__ void pair_unit(const float4 *__restrict__ s4, const float4 *__restrict__ t1,
-                                          const float2 *__restrict__ t2, int pmax, int lane, int I, int Jb,
-                                          int d0, float2 *__restrict__ mypart) {
-    const bool diag = I == Jb;
-    const int nxt = (lane + 1) & 31;
-    const float half_mask = lane < 16 ? 1.f : 0.f;
-    const float4 me = s4[(I << 6) + lane];
-    const float4 *sp = s4 + (Jb << 6) + lane + d0;
-    float vx = 0.f, vy = 0.f, ax = 0.f, ay = 0.f;
-#pragma unroll
-    for (int s = 0; s < 16; ++s) {
-        const float4 q = sp[s];
-        const Mob M = pair_mob(t1, t2, pmax, me.x - q.x, me.y - q.y, (s == 15 && diag) ? half_mask : 1.f);
-        vx = fmaf(M.m11, q.z, fmaf(M.m12, q.w, vx));
-        vy = fmaf(M.m12, q.z, fmaf(M.m22, q.w, vy));
-        ax = fmaf(M.m11, me.z, fmaf(M.m12, me.w, ax));
-        ay = fmaf(M.m12, me.z, fmaf(M.m22, me.w, ay));
-        ax = __shfl_sync(0xffffffffu, ax, nxt);
-        ay = __shfl_sync(0xffffffffu, ay, nxt);
-    }
-    // lane l now holds the sum of source J*32 + (l + d0 + 16) mod 32
-    const int from = (lane - d0 - 16) & 31;
-    ax = __shfl_sync(0xffffffffu, ax, from);
-    ay = __shfl_sync(0xffffffffu, ay, from);
-    if (diag) {
-        vx += ax;
-        vy += ay;
-    }
-    float2 pv = mypart[(I << 5) + lane];
-    pv.x += vx;
-    pv.y += vy;
-    mypart[(I << 5) + lane] = pv;
-    if (!diag) {
-        float2 pa = mypart[(Jb << 5) + lane];
-        pa.x += ax;
-        pa.y += ay;
-        mypart[(Jb << 5) + lane] = pa;
-    }
-}
-
-// Multi-target pair unit: lane l holds targets I_r*32 + l, r < R (the I_r and J distinct
-// blocks), and at step d = d0 .. d0+15 meets source J*32 + (l + d) mod 32, so one source
-// load and one rotation of the source-side sums serve R pair evaluations.
-template <int R>
-__device__ __forceinline__ void pair_unit_multi(const float4 *__restrict__ s4, const float4 *__restrict__ t1,
-                                                const float2 *__restrict__ t2, int pmax, int lane, int I0, int I1,
-                                                int I2, int I3, int Jb, int d0, float2 *__restrict__ mypart) {
+                                          const float2 *__restrict__ t2, int pmax, int lane, int I0, int I1,
+                                          int I2, int I3, int Jb, int d0, float2 *__restrict__ mypart) {
     const int I[4] = {I0, I1, I2, I3};
-    const int nxt = (lane + 1) & 31;
-    float4 m[R];
-    float vx[R], vy[R];
+    const float2 one = dup2(1.f), neg1 = dup2(-1.f);
+    float2 mx[R], my[R], mz[R], mw[R], vx[R], vy[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) {
-        m[r] = s4[(I[r] << 6) + lane];
-        vx[r] = 0.f;
-        vy[r] = 0.f;
+        const float4 A = s4[(I[r] << 6) + lane], Bf = s4[(I[r] << 6) + 32 + lane];
+        mx[r] = dup2(A.x);
+        my[r] = dup2(A.z);
+        mz[r] = dup2(Bf.x);
+        mw[r] = dup2(Bf.z);
+        vx[r] = dup2(0.f);
+        vy[r] = dup2(0.f);
     }
-    const float4 *sp = s4 + (Jb << 6) + lane + d0;
-    float ax = 0.f, ay = 0.f;
+    const float4 *srcJ = s4 + (Jb << 6);
+    const int nxt2 = (lane + 2) & 31;
+    float2 ax = dup2(0.f), ay = dup2(0.f);
 #pragma unroll
-    for (int s = 0; s < 16; ++s) {
-        const float4 q = sp[s];
+    for (int k = 0; k < 8; ++k) {
+        const int j = (lane + d0 + 2 * k) & 31;
+        const float4 qa = srcJ[j], qb = srcJ[32 + j];
+        const float2 qx = make_float2(qa.x, qa.y), qy = make_float2(qa.z, qa.w);
+        const float2 qz = make_float2(qb.x, qb.y), qw = make_float2(qb.z, qb.w);
 #pragma unroll
         for (int r = 0; r < R; ++r) {
-            const Mob M = pair_mob(t1, t2, pmax, m[r].x - q.x, m[r].y - q.y, 1.f);
-            vx[r] = fmaf(M.m11, q.z, fmaf(M.m12, q.w, vx[r]));
-            vy[r] = fmaf(M.m12, q.z, fmaf(M.m22, q.w, vy[r]));
-            ax = fmaf(M.m11, m[r].z, fmaf(M.m12, m[r].w, ax));
-            ay = fmaf(M.m12, m[r].z, fmaf(M.m22, m[r].w, ay));
+            const float2 ex = __ffma2_rn(qx, neg1, mx[r]), ey = __ffma2_rn(qy, neg1, my[r]);
+            const float2 u = __ffma2_rn(ex, ex, __ffma2_rn(ey, ey, one));
+            float2 gn, h;
+            kern_f32(t1, t2, pmax, u.x, gn.x, h.x);
+            kern_f32(t1, t2, pmax, u.y, gn.y, h.y);
+            if (DIAG && k == 7 && lane >= 16) {  // step 16 of a diagonal block: lanes < 16 only
+                gn.y = 0.f;
+                h.y = 0.f;
+            }
+            const float2 hx = __fmul2_rn(h, ex), hy = __fmul2_rn(h, ey);
+            const float2 m11 = __ffma2_rn(hx, ex, gn), m12 = __fmul2_rn(hx, ey), m22 = __ffma2_rn(hy, ey, gn);
+            vx[r] = __ffma2_rn(m11, qz, __ffma2_rn(m12, qw, vx[r]));
+            vy[r] = __ffma2_rn(m12, qz, __ffma2_rn(m22, qw, vy[r]));
+            ax = __ffma2_rn(m11, mz[r], __ffma2_rn(m12, mw[r], ax));
+            ay = __ffma2_rn(m12, mz[r], __ffma2_rn(m22, mw[r], ay));
         }
-        ax = __shfl_sync(0xffffffffu, ax, nxt);
-        ay = __shfl_sync(0xffffffffu, ay, nxt);
+        ax.x = __shfl_sync(0xffffffffu, ax.x, nxt2);
+        ax.y = __shfl_sync(0xffffffffu, ax.y, nxt2);
+        ay.x = __shfl_sync(0xffffffffu, ay.x, nxt2);
+        ay.y = __shfl_sync(0xffffffffu, ay.y, nxt2);
     }
-    const int from = (lane - d0 - 16) & 31;
-    ax = __shfl_sync(0xffffffffu, ax, from);
-    ay = __shfl_sync(0xffffffffu, ay, from);
+    // lane l now holds the even-step sum of source (l + d0 + 16) mod 32 and the odd-step sum
+    // of source (l + d0 + 17) mod 32: bring both sums of source l to lane l
+    const int from0 = (lane - d0 - 16) & 31, from1 = (lane - d0 - 17) & 31;
+    const float sx = __shfl_sync(0xffffffffu, ax.x, from0) + __shfl_sync(0xffffffffu, ax.y, from1);
+    const float sy = __shfl_sync(0xffffffffu, ay.x, from0) + __shfl_sync(0xffffffffu, ay.y, from1);
 #pragma unroll
     for (int r = 0; r < R; ++r) {
         float2 pv = mypart[(I[r] << 5) + lane];
-        pv.x += vx[r];
-        pv.y += vy[r];
+        pv.x += vx[r].x + vx[r].y;
+        pv.y += vy[r].x + vy[r].y;
+        if (DIAG) {
+            pv.x += sx;
+            pv.y += sy;
+        }
         mypart[(I[r] << 5) + lane] = pv;
     }
-    float2 pa = mypart[(Jb << 5) + lane];
-    pa.x += ax;
-    pa.y += ay;
-    mypart[(Jb << 5) + lane] = pa;
+    if (!DIAG) {
+        float2 pa = mypart[(Jb << 5) + lane];
+        pa.x += sx;
+        pa.y += sy;
+        mypart[(Jb << 5) + lane] = pa;
+    }
 }
 
 // The sample's pair units over its n_pw pair warps, longest processing time first: the list
@@ -458,9 +437,12 @@ __global__ void __launch_bounds__(BIG ? 512 : 1024, 1) forward_kernel(FwdArgs a)
     // 2 K_HC ds_H, 2 K_NA; [23, 25) the head centre at the previous observation
     __shared__ double s_model[26];
     // FP32 kernel: the sample's single-precision constants (see below)
-    enum { F_DS, F_INV2DS, F_INVDS2, F_KC2DS, F_AMP, F_ETA, F_OMEGA, F_COS, F_ETA2, F_DSL, F_INVDELTA, F_DTMU, F_DT,
-           F_COUNT };
+    enum { F_DS, F_INV2DS, F_INVDS2, F_KC2DS, F_INVDELTA, F_DTMU, F_COUNT };
     __shared__ float s_f32[F64 ? 1 : 16];
+    // FP32 kernel: (cos, sin)(omega t) of the current step, and the FP64 rotation state
+    // (cos, sin)(omega step dt), (cos, sin)(omega dt) that thread 0 advances once per step
+    __shared__ float s_rot[2];
+    __shared__ double s_rot64[4];
     // FP32 pair sum: warp w processes units [s_wstart[w], s_wstart[w + 1]) of the sample's list
     __shared__ int s_wstart[F64 ? 1 : 33];
     static_assert(F_COUNT <= 16, "s_f32 holds 16 constants");
@@ -576,9 +558,15 @@ __global__ void __launch_bounds__(BIG ? 512 : 1024, 1) forward_kernel(FwdArgs a)
         if (!F64) {  // pad the last block with force-free sources at the origin
             const int npad = ((n + 31) >> 5) << 5;
             for (int k = n + tid; k < npad; k += T) {
-                const int ks = ((k >> 5) << 6) + (k & 31);
-                src[ks] = R4{0, 0, 0, 0};
-                src[ks + 32] = R4{0, 0, 0, 0};
+                src[plane_a(k)] = R4{0, 0, 0, 0};
+                src[plane_b(k)] = R4{0, 0, 0, 0};
+            }
+            if (n < npad && tid == 0) {  // the last point's entries pair it with the first pad
+                const int kp = plane_prev(n);
+                src[plane_a(kp)].y = 0;
+                src[plane_a(kp)].w = 0;
+                src[plane_b(kp)].y = 0;
+                src[plane_b(kp)].w = 0;
             }
         }
         // FP32 kernel: the sample's single-precision constants, made once here in FP64 and read
@@ -589,15 +577,30 @@ __global__ void __launch_bounds__(BIG ? 512 : 1024, 1) forward_kernel(FwdArgs a)
             s_f32[F_INV2DS] = (float)(0.5 / ds);
             s_f32[F_INVDS2] = (float)(1.0 / (ds * ds));
             s_f32[F_KC2DS] = (float)(2.0 * p.kc * ds);
-            s_f32[F_AMP] = (float)p.amp;
-            s_f32[F_ETA] = (float)a.eta;
-            s_f32[F_OMEGA] = (float)a.omega;
-            s_f32[F_COS] = (float)(2.0 * a.eta / L);  // preferred curvature: 2 eta / L,
-            s_f32[F_ETA2] = (float)(a.eta * a.eta);   // eta^2,
-            s_f32[F_DSL] = (float)(ds / L);           // ds / L
             s_f32[F_INVDELTA] = (float)(1.0 / p.delta);
             s_f32[F_DTMU] = (float)(a.dt / a.mu);
-            s_f32[F_DT] = (float)a.dt;
+            // (cos, sin)(omega t) at t = 0 and the rotation by omega dt per step
+            double sw, cw;
+            sincos(a.omega * a.dt, &sw, &cw);
+            s_rot64[0] = 1.0;
+            s_rot64[1] = 0.0;
+            s_rot64[2] = cw;
+            s_rot64[3] = sw;
+            s_rot[0] = 1.f;
+            s_rot[1] = 0.f;
+        }
+        if (!F64) {
+            // the preferred curvature of flagellum point k (Appendix: y^ = a (1 - s/L)
+            // sin(eta s - omega t), zeta^ = d^2 y^/ds^2) split as
+            // zeta^_k(t) = P_k cos(omega t) + Q_k sin(omega t), made in FP64 once per run
+            float2 *pq = a.pq + (size_t)b * n_max;
+            for (int k = tid; k < nf; k += T) {
+                const double sk = k * ds;
+                double sn, cs;
+                sincos(a.eta * sk, &sn, &cs);
+                const double c1 = 2.0 * a.eta / L, c2 = (1.0 - sk / L) * a.eta * a.eta;
+                pq[k] = make_float2((float)(-p.amp * (c1 * cs + c2 * sn)), (float)(-p.amp * (c1 * sn - c2 * cs)));
+            }
         }
         const double dt_mu = a.dt / a.mu;
         // FP64 pair sum: thread -> (target, source split of S lanes)
@@ -624,8 +627,7 @@ __global__ void __launch_bounds__(BIG ? 512 : 1024, 1) forward_kernel(FwdArgs a)
         const R r_ds = F64 ? (R)ds : (R)s_f32[F_DS], r_inv2ds = F64 ? (R)(0.5 / ds) : (R)s_f32[F_INV2DS];
         const R r_invds2 = F64 ? (R)(1.0 / (ds * ds)) : (R)s_f32[F_INVDS2];
         const R kc2ds = F64 ? (R)(2.0 * p.kc * ds) : (R)s_f32[F_KC2DS];
-        const R r_amp = F64 ? (R)p.amp : (R)s_f32[F_AMP], r_eta = F64 ? (R)a.eta : (R)s_f32[F_ETA];
-        const R r_omega = F64 ? (R)a.omega : (R)s_f32[F_OMEGA], r_L = (R)L;
+        const R r_amp = (R)p.amp, r_eta = (R)a.eta, r_omega = (R)a.omega, r_L = (R)L;  // (FP64 kernel)
         const R inv_d2 = (R)(1.0 / (p.delta * p.delta));
         if (vel_obs(a, nh) && tid < 32) {  // head centre at the previous observation
             double cx, cy;
@@ -635,7 +637,7 @@ __global__ void __launch_bounds__(BIG ? 512 : 1024, 1) forward_kernel(FwdArgs a)
                 s_model[M_CY] = cy;
             }
         }
-        float g10 = 0.f;  // FP32: g1 at r = 0 (self term)
+        float g10 = 0.f;  // FP32: -g1 at r = 0 (self term)
         if (!F64) {
             float g2unused;
             kern_f32((const float4 *)tabraw, (const float2 *)((const float4 *)tabraw + P), npan - 1, 1.0f, g10,
@@ -650,7 +652,7 @@ __global__ void __launch_bounds__(BIG ? 512 : 1024, 1) forward_kernel(FwdArgs a)
         const int obs_every = (int)min(a.obs_every, (long long)INT_MAX);  // > steps: no observation
         int obs_left = obs_every, obs_idx = 0;
         for (int step = 0; step < (int)last; ++step) {
-            const R tR = F64 ? (R)((double)step * a.dt) : (R)(int_to_float(step) * s_f32[F_DT]);
+            const double tR = (double)step * a.dt;  // (FP64 kernel; the FP32 kernel rotates s_rot)
             const bool obs_step = --obs_left == 0;
             int bad = 0;
             // ---- A+B: segments, tension, curvature stencils, relative positions.  Thread k
@@ -666,6 +668,7 @@ __global__ void __launch_bounds__(BIG ? 512 : 1024, 1) forward_kernel(FwdArgs a)
                 const int prev = hd ? base + nf + (m == 0 ? nh - 1 : m - 1) : k - 1;
                 const bool center = hd || (kl >= 1 && kl + 1 < nf);
                 R qx, qy, epx = 0, epy = 0, emx = 0, emy = 0, tk = 0;
+                float d2x = 0.f, d2y = 0.f;  // FP32: e_k - e_{k-1} from the double-float segments
                 if (F64) {
                     if (next >= 0) {
                         double ex, ey, strain;
@@ -681,21 +684,29 @@ __global__ void __launch_bounds__(BIG ? 512 : 1024, 1) forward_kernel(FwdArgs a)
                     qx = (R)sx[k];
                     qy = (R)sy[k];
                 } else {
+                    float epxl = 0.f, epyl = 0.f;
                     if (next >= 0) {
                         float strain, ex, ey;
-                        tk = (R)spring_f32(xh, xl, yh, yl, k, next, rest32[hd ? 1 : 0], ex, ey, strain);
+                        tk = (R)spring_f32(xh, xl, yh, yl, k, next, rest32[hd ? 1 : 0], ex, ey, epxl, epyl, strain);
                         epx = (R)ex;
                         epy = (R)ey;
                         if (!(fabsf(strain) <= (float)STRETCH_MAX)) bad = 1;
                     }
                     if (center) {
+                        // e_{k-1} as a double-float (s, lo); the second difference e_k - e_{k-1}
+                        // subtracts the high parts first (neighbouring segments are close, so
+                        // that difference is exact) and then the low parts: rounding the
+                        // segments to FP32 before subtracting would leave it an error of
+                        // about 6e-8 ds, amplified by 1/ds^2 in the curvature
                         float s, e, lo;
                         two_sum(xh[k], -xh[prev], s, e);
                         lo = e + (xl[k] - xl[prev]);
                         emx = (R)(s + lo);
+                        d2x = (epx - s) + (epxl - lo);
                         two_sum(yh[k], -yh[prev], s, e);
                         lo = e + (yl[k] - yl[prev]);
                         emy = (R)(s + lo);
+                        d2y = (epy - s) + (epyl - lo);
                     }
                     // the pair sum measures separations in units of delta
                     qx = (R)((xh[k] + xl[k]) * s_f32[F_INVDELTA]);
@@ -705,22 +716,32 @@ __global__ void __launch_bounds__(BIG ? 512 : 1024, 1) forward_kernel(FwdArgs a)
                     tvx[k] = tk * epx;
                     tvy[k] = tk * epy;
                 }
-                const int ks = F64 ? k : ((k >> 5) << 6) + (k & 31);  // first copy of point k
-                const int kd = F64 ? k + n : ks + 32;                 // second copy
-                src[ks].x = qx;
-                src[ks].y = qy;
-                src[kd].x = qx;
-                src[kd].y = qy;
+                if (F64) {  // the point list stored twice
+                    src[k].x = qx;
+                    src[k].y = qy;
+                    src[k + n].x = qx;
+                    src[k + n].y = qy;
+                } else {  // plane A: own entry, and the previous entry's second half
+                    const int ka = plane_a(k), kp = plane_a(plane_prev(k));
+                    src[ka].x = qx;
+                    src[ka].z = qy;
+                    src[kp].y = qx;
+                    src[kp].w = qy;
+                }
                 if (center) {
                     const R i2h = hd ? (R)s_model[M_I2H] : r_inv2ds, ih2 = hd ? (R)s_model[M_IH2] : r_invds2;
                     R A = (emx + epx) * i2h, Bv = (emy + epy) * i2h;
-                    R C = (epx - emx) * ih2, D = (epy - emy) * ih2;
+                    R C = (F64 ? epx - emx : (R)d2x) * ih2, D = (F64 ? epy - emy : (R)d2y) * ih2;
                     R S2 = A * A + Bv * Bv;
                     R rs;
-                    if (F64)
+                    if (F64) {
                         rs = (R)(1.0 / sqrt((double)S2));
-                    else
-                        rs = (R)rsqrtf((float)S2);
+                    } else {
+                        // the hardware estimate plus one Newton step: its ~2 ulp error would
+                        // otherwise enter zeta and the stencils, which multiply it by 1/ds^2
+                        const float r0 = rsqrtf((float)S2);
+                        rs = (R)fmaf(r0 * 0.5f, fmaf(-(float)S2 * r0, r0, 1.0f), r0);
+                    }
                     R S15 = rs * rs * rs;
                     R S25 = S15 * rs * rs;
                     R cross = A * D - Bv * C;
@@ -736,14 +757,10 @@ __global__ void __launch_bounds__(BIG ? 512 : 1024, 1) forward_kernel(FwdArgs a)
                             sincos((double)ph, &sd, &cd);
                             zhat = -r_amp * ((R)2 * r_eta / r_L * (R)cd + ((R)1 - s / r_L) * r_eta * r_eta * (R)sd);
                         } else {
-                            const float klf = small_int_to_float(kl);
-                            float ph = (float)r_eta * (klf * (float)r_ds) - (float)r_omega * (float)tR;
-                            // reduce to [-pi, pi], then the fast hardware approximation
-                            ph = fmaf(-6.28318530717958648f, round_to_int(ph * 0.159154943091895336f), ph);
-                            float sf, cf;
-                            __sincosf(ph, &sf, &cf);
-                            zhat = (R)(-(float)r_amp *
-                                       (s_f32[F_COS] * cf + (1.0f - klf * s_f32[F_DSL]) * s_f32[F_ETA2] * sf));
+                            // zeta^_k(t) = P_k cos(omega t) + Q_k sin(omega t) (made in FP64 for the
+                            // run); (cos, sin)(omega t) is advanced in FP64 once per step
+                            const float2 c = a.pq[(size_t)b * n_max + kl];
+                            zhat = (R)fmaf(c.x, s_rot[0], c.y * s_rot[1]);
                         }
                     }
                     R ck = (hd ? (R)s_model[M_KHC] : kc2ds) * (zeta - zhat);
@@ -822,8 +839,8 @@ __global__ void __launch_bounds__(BIG ? 512 : 1024, 1) forward_kernel(FwdArgs a)
                             if (!(fabs(strain) <= STRETCH_MAX)) bad = 1;
                         } else {
                             const RestF32 &r = rest32[2 + kind];
-                            float ex, ey, strain;
-                            float t = spring_f32(xh, xl, yh, yl, k, j, r, ex, ey, strain);
+                            float ex, ey, exl, eyl, strain;
+                            float t = spring_f32(xh, xl, yh, yl, k, j, r, ex, ey, exl, eyl, strain);
                             fx += (R)(t * ex);
                             fy += (R)(t * ey);
                             if (!(fabsf(strain) <= (float)STRETCH_MAX)) bad = 1;
@@ -865,22 +882,27 @@ __global__ void __launch_bounds__(BIG ? 512 : 1024, 1) forward_kernel(FwdArgs a)
                         }
                     }
                 }
-                const int ks = F64 ? k : ((k >> 5) << 6) + (k & 31);
-                const int kd = F64 ? k + n : ks + 32;
-                src[ks].z = fx;
-                src[ks].w = fy;
-                src[kd].z = fx;
-                src[kd].w = fy;
+                if (F64) {
+                    src[k].z = fx;
+                    src[k].w = fy;
+                    src[k + n].z = fx;
+                    src[k + n].w = fy;
+                } else {  // plane B
+                    const int kb = plane_b(k), kp = plane_b(plane_prev(k));
+                    src[kb].x = fx;
+                    src[kb].z = fy;
+                    src[kp].y = fx;
+                    src[kp].w = fy;
+                }
             }
             __syncthreads();
             if (step == a.steps) {  // final state: positions and the forces there
                 for (int k = tid; k < n; k += T) {
-                    const int ks = F64 ? k : ((k >> 5) << 6) + (k & 31);
                     double *o = a.final_state + ((size_t)b * n_max + k) * 4;
                     o[0] = (F64 ? sx[k] : (double)xh[k] + (double)xl[k]) + xref;
                     o[1] = F64 ? sy[k] : (double)yh[k] + (double)yl[k];
-                    o[2] = (double)src[ks].z;
-                    o[3] = (double)src[ks].w;
+                    o[2] = F64 ? (double)src[k].z : (double)src[plane_b(k)].x;
+                    o[3] = F64 ? (double)src[k].w : (double)src[plane_b(k)].z;
                 }
                 break;
             }
@@ -941,11 +963,14 @@ __global__ void __launch_bounds__(BIG ? 512 : 1024, 1) forward_kernel(FwdArgs a)
                     const int d0 = code == 2 ? 1 : code << 4;
                     const int I2 = (pk >> 10) & 31, I3 = (pk >> 15) & 31, I4 = (pk >> 20) & 31;
                     if (kind == 0) {
-                        pair_unit(s4, t1, t2, npan - 1, lane, I, Jb, d0, mypart);
+                        if (I == Jb)
+                            pair_unit<1, true>(s4, t1, t2, npan - 1, lane, I, 0, 0, 0, Jb, d0, mypart);
+                        else
+                            pair_unit<1, false>(s4, t1, t2, npan - 1, lane, I, 0, 0, 0, Jb, d0, mypart);
                     } else if (BIG && kind == 2) {
-                        pair_unit_multi<4>(s4, t1, t2, npan - 1, lane, I, I2, I3, I4, Jb, d0, mypart);
+                        pair_unit<4, false>(s4, t1, t2, npan - 1, lane, I, I2, I3, I4, Jb, d0, mypart);
                     } else {
-                        pair_unit_multi<2>(s4, t1, t2, npan - 1, lane, I, I2, 0, 0, Jb, d0, mypart);
+                        pair_unit<2, false>(s4, t1, t2, npan - 1, lane, I, I2, 0, 0, Jb, d0, mypart);
                         // the host gives four-target lists to the 128-register instantiation
                         // only; a run that meets one here ends as diverged, not with pairs missing
                         if (kind == 2) bad = 1;
@@ -962,8 +987,8 @@ __global__ void __launch_bounds__(BIG ? 512 : 1024, 1) forward_kernel(FwdArgs a)
                     sy[k] += dy;
                 } else {
                     // v_k = self term + the pair warps' partial sums, compensated
-                    const float4 me = ((const float4 *)src)[((k >> 5) << 6) + (k & 31)];
-                    float hx = -me.z * g10, lx = 0.f, hy = -me.w * g10, ly = 0.f;
+                    const float4 fk = ((const float4 *)src)[plane_b(k)];  // (Fx, ., Fy, .)
+                    float hx = fk.x * g10, lx = 0.f, hy = fk.z * g10, ly = 0.f;
                     for (int w = 0; w < n_pw; ++w) {
                         const float2 pv = part[w * (nb << 5) + k];
                         acc_two_sum(hx, lx, pv.x);
@@ -999,6 +1024,14 @@ __global__ void __launch_bounds__(BIG ? 512 : 1024, 1) forward_kernel(FwdArgs a)
                         }
                     }
                 }
+            }
+            if (!F64 && tid == 0) {  // (cos, sin)(omega t) of the next step, rotated in FP64
+                const double c = s_rot64[0], sn = s_rot64[1], wc = s_rot64[2], ws = s_rot64[3];
+                const double nc = fma(c, wc, -sn * ws), ns = fma(sn, wc, c * ws);
+                s_rot64[0] = nc;
+                s_rot64[1] = ns;
+                s_rot[0] = (float)nc;
+                s_rot[1] = (float)ns;
             }
             if (__syncthreads_or(bad)) {
                 status = SWIMMER_DIVERGED;
@@ -1302,6 +1335,7 @@ int launch_forward(swimmer_handle *h, int B, const double *obs, double sigma, do
     a.queue = h->queue;
     a.tab64 = h->tab64;
     a.tab32 = h->tab32;
+    a.pq = h->pq;
     a.mu = h->cfg.mu;
     a.dt = h->cfg.dt;
     a.kt = h->cfg.k_t;

@@ -467,7 +467,8 @@ table_build_kernel(int B, SampleParams *__restrict__ sp, const double *__restric
 
     // FP32 quadratic per eighth of an FP64 panel from the FP64 series (Chebyshev fit at 3
     // nodes, then monomial coefficients in G = 1 + f / F32_SUB, f in [0, 1) across the
-    // panel); the FP32 table holds delta^2 g2, for separations measured in units of delta
+    // panel); the FP32 table holds -g1 (the sign the pair sum's mobility -g1 I + h e e^T
+    // takes) and h = delta^2 g2, for separations measured in units of delta
     const int np32 = p.n_oct * F32_SUB;
     constexpr int SPLIT = F32_SUB / F64_SUB;  // FP32 panels per FP64 panel
     float2 *t32b = (float2 *)(t32 + F32_PANELS_MAX);
@@ -496,7 +497,7 @@ table_build_kernel(int B, SampleParams *__restrict__ sp, const double *__restric
             // reads G = 1 + f / S (S = F32_SUB) straight from the low mantissa bits of u, so
             // p = c0 + c1 G + c2 G^2 with f = S (G - 1)
             const double m0 = a[0] - a[1] + a[2], m1 = 2.0 * a[1] - 8.0 * a[2], m2 = 8.0 * a[2];  // in f
-            const double S = F32_SUB, sc = fn == 1 ? p.delta * p.delta : 1.0;  // g2 carries delta^2
+            const double S = F32_SUB, sc = fn == 1 ? p.delta * p.delta : -1.0;  // -g1; delta^2 g2
             cf[fn][0] = sc * (m0 - S * m1 + S * S * m2);
             cf[fn][1] = sc * (S * m1 - 2.0 * S * S * m2);
             cf[fn][2] = sc * (S * S * m2);
@@ -569,8 +570,8 @@ __global__ void kernel_eval_kernel(int m, const double *__restrict__ r, double *
         float G = __uint_as_float(0x3f800000u | (bits & ((1u << (23 - F32_SUB_LOG2)) - 1u)));
         float4 a = tab32[panel];
         float2 c = ((const float2 *)(tab32 + F32_PANELS_MAX))[panel];
-        g1[i] = fmaf(G, fmaf(G, a.z, a.y), a.x);
-        g2[i] = fmaf(G, fmaf(G, c.y, c.x), a.w) * inv_d2;  // the table holds delta^2 g2
+        g1[i] = -fmaf(G, fmaf(G, a.z, a.y), a.x);           // the table holds -g1
+        g2[i] = fmaf(G, fmaf(G, c.y, c.x), a.w) * inv_d2;  // and delta^2 g2
     }
 }
 
