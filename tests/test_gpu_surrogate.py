@@ -93,3 +93,67 @@ def test_delayed_acceptance_matches_plain_and_saves_forward_runs(trained):
     assert exact_da < exact_plain, (exact_da, exact_plain)
     assert exact_plain - exact_da <= rejected_plain
     assert acc_da > acc_plain, (acc_da, acc_plain)
+
+
+def test_delayed_acceptance_fp64_matches_oracle_sample_by_sample():
+    """The two-stage Metropolis-Hastings chains of delayed acceptance (stage 1 on the
+    surrogate, stage 2 on the exact model; Sec. 3.2, Algorithm 1 otherwise) on the FP64
+    kernel against the oracle's, sample by sample, over a whole TMCMC run.  The network's
+    weights are seeded inputs (not trained here), so both sides hold the same surrogate: a
+    smooth function of theta that predicts the true trajectory plus a perturbation of half
+    the noise level, whose log-likelihood varies by nats across the prior."""
+    import multiprocessing as mp
+
+    from oracle import mlp as om
+    from oracle import swimmer as sw
+    from oracle import tmcmc as tm
+
+    base = sw.SwimmerParams(n=12, dt=2e-4, steps=5000, obs_every=125, alpha=1.0, amp=0.1)
+    B, seed = 96, 44
+    obs, _, _, st = sw.run_c_batch([base.with_theta(TRUTH)])
+    xi = obs[0]
+    sigma = sw.noise_sigma(xi, 0.05)
+    D = xi + sigma * synthetic.normals(1234, synthetic.NOISE, 0, xi.size).reshape(xi.shape)
+    # seeded network (BF16-rounded weights on both sides), output normalization around xi
+    rng = np.random.default_rng(9)
+    params = [(W, rng.normal(0, 0.1, size=b.shape)) for W, b in om.init_params(rng)]
+    flat = np.concatenate([np.concatenate([W.ravel(), b]) for W, b in params]).astype(np.float32)
+    rounded, o = [], 0
+    for fi, fo in zip(om.LAYERS[:-1], om.LAYERS[1:]):
+        W = flat[o:o + fo * fi].astype(np.float64).reshape(fo, fi)
+        o += fo * fi
+        rounded.append((om.bf16_round(W), flat[o:o + fo].astype(np.float64)))
+        o += fo
+    out_mean = xi.reshape(-1)
+    out_std = np.full(80, 0.5 * sigma)
+    log10_kt, omega = math.log10(base.k_t), base.omega
+    in_lo = list(LO) + [log10_kt, omega]
+    in_hi = list(HI) + [log10_kt, omega]
+    # GPU: FP64 kernel, surrogate attached, delayed acceptance
+    cfg = g.SwimmerConfig(n_max=base.n, b_max=B, length=base.length, dt=base.dt, steps=base.steps,
+                          obs_every=base.obs_every, precision=g.FP64)
+    h = g.swimmer_init(cfg)
+    g.swimmer_surrogate_set(h, torch.tensor(flat, device=DEV), in_lo, in_hi, out_mean, out_std, 1, log10_kt, omega)
+    th0 = synthetic.prior_samples(seed, LO, HI, B)
+    log_g = []
+    stg = g.tmcmc_run(h, torch.tensor(th0, device=DEV), torch.tensor(D, device=DEV), sigma, LO, HI,
+                      lambda j: synthetic.stage_randoms(seed, j, B, 3), use_surrogate=True, log=log_g)
+    torch.cuda.synchronize()
+    th_g, ll_g = stg.theta.cpu().numpy(), stg.loglik.cpu().numpy()
+    h.close()
+    # oracle: the same chains with the oracle's surrogate and forward model
+    surr_fn = lambda th: om.surrogate_loglik(rounded, th, in_lo, in_hi, out_mean, out_std, 1, log10_kt, omega, D,
+                                             sigma)
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(min(16, mp.cpu_count())) as pool:
+        fn = lambda th: sw.batch_log_likelihood(base, th, D, sigma, pool=pool, chunk=4)
+        th_o, ll_o, log_o = tm.run(th0, fn, LO, HI, seed, surrogate_fn=surr_fn,
+                                   randoms=lambda j: synthetic.stage_randoms(seed, j, B, 3))
+    assert len(log_g) == len(log_o.q) and len(log_g) >= 2
+    assert [s["q"] for s in log_g] == pytest.approx(log_o.q, rel=1e-9)
+    assert [s["unique"] for s in log_g] == log_o.unique
+    # exact forward runs the one-step chains make, and accepted moves, stage by stage
+    assert [s["n_exact_path"] for s in log_g] == log_o.n_exact
+    assert [s["n_accept"] / B for s in log_g] == pytest.approx(log_o.accept, abs=0)
+    assert np.allclose(th_g, th_o, rtol=1e-8, atol=1e-10)
+    assert np.allclose(ll_g, ll_o, rtol=1e-8, atol=1e-8)
