@@ -338,14 +338,18 @@ int tmcmc_resample(swimmer_handle *h, int B, const double *w, const double *u, i
 size_t mlp_workspace_bytes(int n);
 
 /* Forward pass: x[n][5] (device FP32) -> y[n][80] (device FP32).  params (device FP32
- * master copy, NPARAM floats, layout W1,b1,W2,b2,W3,b3,W4,b4 with W[out][in]); every
- * weight is rounded to BF16 as it enters a product, accumulation is FP32.  workspace:
- * device buffer of mlp_workspace_bytes(n) bytes, owned by the caller. */
+ * master copy, NPARAM floats, layout W1,b1,W2,b2,W3,b3,W4,b4 with W[out][in]).  Weights are
+ * rounded to BF16 as they enter a product and every product accumulates in FP32; the three
+ * 256-wide layers run on the tensor cores, with their activations (and, in mlp_backward,
+ * the output gradients) rounded to BF16 as they enter, while the first layer keeps its 5
+ * inputs in FP32.  workspace: device buffer of mlp_workspace_bytes(n) bytes, owned by the
+ * caller. */
 int mlp_forward(int n, const float *params, const float *x, float *y, float *workspace, void *stream);
 
 /* Loss and gradient: loss_out[0] = mean over n x 80 of (y - t)^2 and grad[NPARAM] = its
- * gradient with respect to params (the BF16-rounded forward differentiated with the same
- * rounded weights), both device FP32 and overwritten.  Deterministic (no atomics). */
+ * gradient with respect to params (the forward above differentiated with its rounded
+ * factors, the rounding taken as the identity), both device FP32 and overwritten.
+ * Deterministic (no atomics). */
 int mlp_backward(int n, const float *params, const float *x, const float *t, float *grad,
                  float *loss_out, float *workspace, void *stream);
 

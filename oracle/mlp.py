@@ -8,6 +8,12 @@ normalized (alpha, log10 K_C, a, log10 K_T, omega) to 40 normalized head positio
 
 Parameters are a list of (W[out, in], b[out]).  GELU(x) = x Phi(x) = x (1 + erf(x/sqrt 2))/2.
 
+``bf16_operands=True`` gives the precision of a network whose 256-wide layers run as BF16
+products with wide accumulation: for every layer after the first, both factors of each
+product (activations or output gradients, and the weights, which the caller rounds) are
+rounded to BF16 first, and the sums are exact here.  The first layer (5 inputs) keeps its
+inputs unrounded.
+
 Pins (in tests/test_oracle_tmcmc.py, the MLP tests): gradients against central finite differences of the
 loss; GELU derivative against finite differences; an Adam step against its textbook
 formula on one scalar.
@@ -39,13 +45,14 @@ def gelu_grad(x):
     return 0.5 * (1.0 + special.erf(x / math.sqrt(2.0))) + x * np.exp(-0.5 * x * x) / math.sqrt(2.0 * math.pi)
 
 
-def forward(params, x, keep=False):
+def forward(params, x, keep=False, bf16_operands=False):
     """x[batch, 5] -> y[batch, 80]; with keep=True also the pre-activations."""
     h = np.asarray(x, dtype=np.float64)
     pre = []
     acts = [h]
     for li, (W, b) in enumerate(params):
-        z = h @ W.T + b
+        hin = bf16_round(h) if bf16_operands and li > 0 else h
+        z = hin @ W.T + b
         pre.append(z)
         h = gelu(z) if li < len(params) - 1 else z
         acts.append(h)
@@ -57,17 +64,21 @@ def loss(params, x, t):
     return float(np.mean((y - t) ** 2))
 
 
-def backward(params, x, t):
-    """Gradients of the mean squared error loss with respect to every W and b."""
-    y, pre, acts = forward(params, x, keep=True)
+def backward(params, x, t, bf16_operands=False):
+    """Gradients of the mean squared error loss with respect to every W and b (with
+    bf16_operands, those of the rounded products, differentiated as if the rounding were
+    the identity)."""
+    y, pre, acts = forward(params, x, keep=True, bf16_operands=bf16_operands)
     g = 2.0 * (y - t) / y.size
     grads = [None] * len(params)
     for li in range(len(params) - 1, -1, -1):
         W, _ = params[li]
         if li < len(params) - 1:
             g = g * gelu_grad(pre[li])
-        grads[li] = (g.T @ acts[li], g.sum(axis=0))
-        g = g @ W
+        r = bf16_operands and li > 0
+        gr = bf16_round(g) if r else g
+        grads[li] = (gr.T @ (bf16_round(acts[li]) if r else acts[li]), g.sum(axis=0))
+        g = gr @ W
     return grads
 
 
@@ -113,14 +124,15 @@ def surrogate_inputs(theta, in_lo, in_hi, log10_kt, omega):
 def surrogate_loglik(params, theta, in_lo, in_hi, out_mean, out_std, obs_stride, log10_kt, omega, D, sigma):
     """Surrogate log-likelihood used by delayed acceptance (not in the paper).
 
-    The network predicts the head position at 40 observation times, rows
+    The network (its 256-wide layers as BF16 products, ``forward(..., bf16_operands=True)``)
+    predicts the head position at 40 observation times, rows
     o * obs_stride + obs_stride - 1 of the observation record D [n_obs, 2]:
     p = out_mean + out_std * y.  The misfit over those rows is scaled to the full record,
     J = (n_obs / 40) sum |D_row - p|^2, and enters the Gaussian log-likelihood of Sec. 3.1
     (Eqs. likelihood, fitness): -(m/2) ln(2 pi sigma^2) - J / (2 sigma^2), m = 2 n_obs.
     With a fourth unknown the sample's sigma is theta[3] times sigma."""
     th = np.asarray(theta, dtype=np.float64)
-    y = forward(params, surrogate_inputs(th, in_lo, in_hi, log10_kt, omega))
+    y = forward(params, surrogate_inputs(th, in_lo, in_hi, log10_kt, omega), bf16_operands=True)
     pred = np.asarray(out_mean)[None, :] + np.asarray(out_std)[None, :] * y
     D = np.asarray(D, dtype=np.float64)
     n_obs = D.shape[0]

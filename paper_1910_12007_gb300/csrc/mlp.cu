@@ -2,10 +2,13 @@
 // activations (not in the paper).  Weights are kept as an FP32 master copy and rounded to
 // BF16 when they enter a product; every product accumulates in FP32.
 //
-// All layers run through one tiled FP32-accumulate GEMM (64 x 64 tiles, 16-deep K panels
-// staged in shared memory, 4 x 4 outputs per thread) with fused epilogues: bias + GELU
-// for the forward pass, the GELU derivative for the backward pass.  Weight gradients
-// reduce over the batch inside one tile (no atomics), so gradients are deterministic.
+// The products of the three 256-wide layers (forward, weight gradient, input gradient) run on
+// the tensor cores: BF16 operands, FP32 accumulation, warp-level m16n8k16 MMA over 64 x 64
+// output tiles.  The first layer (5 inputs, which stay FP32) runs through a tiled FP32 GEMM
+// (64 x 64 tiles, 16-deep K panels, 4 x 4 outputs per thread).  Both carry fused epilogues:
+// bias + GELU for the forward pass, the GELU derivative for the backward pass.  Weight
+// gradients reduce over the batch inside one tile (no atomics), so gradients are
+// deterministic.
 #include <cuda_bf16.h>
 #include <math.h>
 
@@ -91,6 +94,104 @@ __global__ void __launch_bounds__(256) gemm_kernel(int M, int N, int K, const fl
     }
 }
 
+// The same product on the tensor cores: BF16 operands (both rounded to nearest as they are
+// staged), FP32 accumulation, warp-level m16n8k16 MMA.  A 64 x 64 output tile per CTA of four
+// warps (2 x 2, each 32 x 32: 2 x 4 MMA tiles), K panels of 32 staged in shared memory as
+// [row][k] BF16 with rows padded to 40 elements (80 bytes: the fragment loads of a warp fall
+// in distinct banks).  Operands are read with any strides and zero-filled past M, N, K.
+constexpr int TC_TM = 64, TC_TN = 64, TC_TK = 32, TC_LD = TC_TK + 8;
+__device__ __forceinline__ unsigned pack_bf16(float lo, float hi) {
+    const unsigned a = __bfloat16_as_ushort(__float2bfloat16_rn(lo));
+    const unsigned b = __bfloat16_as_ushort(__float2bfloat16_rn(hi));
+    return a | (b << 16);
+}
+__device__ __forceinline__ void mma_bf16_16816(float (&d)[4], const unsigned (&a)[4], const unsigned (&b)[2]) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
+        "{%0, %1, %2, %3};\n"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+// stage rows [r0, r0 + 64) x k [k0, k0 + 32) of X(r, k) = X[r*sr + k*sk] into S[row][k] as BF16
+// pairs; the loop runs along whichever index has unit stride, so global reads coalesce
+__device__ __forceinline__ void tc_stage(unsigned *S, const float *__restrict__ X, int R, int K, int r0, int k0,
+                                         int sr, int sk) {
+    if (sk == 1) {
+        for (int e = threadIdx.x; e < TC_TM * TC_TK / 2; e += 128) {
+            const int rr = e / (TC_TK / 2), kk = 2 * (e % (TC_TK / 2));
+            const int r = r0 + rr, k = k0 + kk;
+            const float v0 = (r < R && k < K) ? X[(size_t)r * sr + k] : 0.f;
+            const float v1 = (r < R && k + 1 < K) ? X[(size_t)r * sr + k + 1] : 0.f;
+            S[rr * (TC_LD / 2) + kk / 2] = pack_bf16(v0, v1);
+        }
+    } else {
+        for (int e = threadIdx.x; e < TC_TM * TC_TK / 2; e += 128) {
+            const int rr = e % TC_TM, kk = 2 * (e / TC_TM);
+            const int r = r0 + rr, k = k0 + kk;
+            const float v0 = (r < R && k < K) ? X[(size_t)r * sr + (size_t)k * sk] : 0.f;
+            const float v1 = (r < R && k + 1 < K) ? X[(size_t)r * sr + (size_t)(k + 1) * sk] : 0.f;
+            S[rr * (TC_LD / 2) + kk / 2] = pack_bf16(v0, v1);
+        }
+    }
+}
+// C[m][n] = epi( sum_k A(m, k) B(k, n) ), A(m, k) = A[m*sam + k*sak], B(k, n) = B[k*sbk + n*sbn]
+__global__ void __launch_bounds__(128) gemm_tc_kernel(int M, int N, int K, const float *__restrict__ A, int sam,
+                                                     int sak, const float *__restrict__ B, int sbk, int sbn,
+                                                     float *__restrict__ C, int ldc, int epi,
+                                                     const float *__restrict__ bias, const float *__restrict__ Z,
+                                                     int ldz, float *__restrict__ C2) {
+    __shared__ unsigned As[TC_TM * TC_LD / 2];  // [m][k] BF16 pairs
+    __shared__ unsigned Bs[TC_TN * TC_LD / 2];  // [n][k] BF16 pairs
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int gid = lane >> 2, tig = lane & 3;
+    const int wm = (warp >> 1) * 32, wn = (warp & 1) * 32;
+    const int m0 = blockIdx.y * TC_TM, n0 = blockIdx.x * TC_TN;
+    float acc[2][4][4] = {};
+    for (int k0 = 0; k0 < K; k0 += TC_TK) {
+        tc_stage(As, A, M, K, m0, k0, sam, sak);
+        tc_stage(Bs, B, N, K, n0, k0, sbn, sbk);
+        __syncthreads();
+#pragma unroll
+        for (int ks = 0; ks < TC_TK; ks += 16) {
+            unsigned af[2][4], bf[4][2];
+#pragma unroll
+            for (int i = 0; i < 2; ++i) {
+                const int r = wm + 16 * i + gid, c = (ks >> 1) + tig;
+                af[i][0] = As[r * (TC_LD / 2) + c];
+                af[i][1] = As[(r + 8) * (TC_LD / 2) + c];
+                af[i][2] = As[r * (TC_LD / 2) + c + 4];
+                af[i][3] = As[(r + 8) * (TC_LD / 2) + c + 4];
+            }
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int r = wn + 8 * j + gid, c = (ks >> 1) + tig;
+                bf[j][0] = Bs[r * (TC_LD / 2) + c];
+                bf[j][1] = Bs[r * (TC_LD / 2) + c + 4];
+            }
+#pragma unroll
+            for (int i = 0; i < 2; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) mma_bf16_16816(acc[i][j], af[i], bf[j]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int m = m0 + wm + 16 * i + gid + (q >= 2 ? 8 : 0);
+                const int n = n0 + wn + 8 * j + 2 * tig + (q & 1);
+                if (m >= M || n >= N) continue;
+                float v = acc[i][j][q];
+                if (epi == EPI_BIAS || epi == EPI_BIAS_GELU) v += bias[n];
+                if (epi == EPI_DGELU) v *= gelu_grad(Z[(size_t)m * ldz + n]);
+                C[(size_t)m * ldc + n] = v;
+                if (epi == EPI_BIAS_GELU) C2[(size_t)m * ldc + n] = gelu(v);
+            }
+}
+
 // column sums (bias gradients): out[n] = sum_m X[m][n], fixed order
 __global__ void colsum_kernel(int M, int N, const float *__restrict__ X, int ldx, float *__restrict__ out) {
     int n = blockIdx.x * blockDim.x + threadIdx.x;
@@ -139,11 +240,18 @@ __global__ void adam_kernel(int n, float *__restrict__ p, const float *__restric
     p[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
 }
 
-int gemm(cudaStream_t s, int M, int N, int K, const float *A, int sam, int sak, const float *B, int sbk, int sbn,
-         int round_b, float *C, int ldc, int epi, const float *bias = nullptr, const float *Z = nullptr, int ldz = 0,
-         float *C2 = nullptr) {
-    dim3 grid((N + TN - 1) / TN, (M + TM - 1) / TM);
-    gemm_kernel<<<grid, 256, 0, s>>>(M, N, K, A, sam, sak, B, sbk, sbn, round_b, C, ldc, epi, bias, Z, ldz, C2);
+// tensor_core: BF16 operands on the tensor cores (the 256-wide layers); else the FP32 SIMT
+// product with BF16 weights (the first layer, whose 5 inputs stay unrounded)
+int gemm(cudaStream_t s, bool tensor_core, int M, int N, int K, const float *A, int sam, int sak, const float *B,
+         int sbk, int sbn, int round_b, float *C, int ldc, int epi, const float *bias = nullptr,
+         const float *Z = nullptr, int ldz = 0, float *C2 = nullptr) {
+    if (tensor_core) {
+        dim3 grid((N + TC_TN - 1) / TC_TN, (M + TC_TM - 1) / TC_TM);
+        gemm_tc_kernel<<<grid, 128, 0, s>>>(M, N, K, A, sam, sak, B, sbk, sbn, C, ldc, epi, bias, Z, ldz, C2);
+    } else {
+        dim3 grid((N + TN - 1) / TN, (M + TM - 1) / TM);
+        gemm_kernel<<<grid, 256, 0, s>>>(M, N, K, A, sam, sak, B, sbk, sbn, round_b, C, ldc, epi, bias, Z, ldz, C2);
+    }
     CUDA_TRY(cudaGetLastError());
     return 0;
 }
@@ -181,9 +289,9 @@ int forward_all(cudaStream_t s, int n, const float *P, const float *x, float *y,
         const float *W = P + w_off(l), *b = P + b_off(l);
         int rc;
         if (l < NLAYER - 1)
-            rc = gemm(s, n, fo, fi, in, fi, 1, W, 1, fi, 1, w.Z[l], fo, EPI_BIAS_GELU, b, nullptr, 0, w.H[l]);
+            rc = gemm(s, l > 0, n, fo, fi, in, fi, 1, W, 1, fi, 1, w.Z[l], fo, EPI_BIAS_GELU, b, nullptr, 0, w.H[l]);
         else
-            rc = gemm(s, n, fo, fi, in, fi, 1, W, 1, fi, 1, y, fo, EPI_BIAS, b);
+            rc = gemm(s, l > 0, n, fo, fi, in, fi, 1, W, 1, fi, 1, y, fo, EPI_BIAS, b);
         if (rc) return rc;
         in = l < NLAYER - 1 ? w.H[l] : nullptr;
     }
@@ -223,14 +331,14 @@ extern "C" int mlp_backward(int n, const float *params, const float *x, const fl
         const float *W = params + w_off(l);
         const float *hin = l > 0 ? w.H[l - 1] : x;
         // dW[o][i] = sum_s dZ[s][o] H[s][i]   (M = fo, N = fi, K = n)
-        rc = gemm(s, fo, fi, n, dz, 1, fo, hin, fi, 1, 0, grad + w_off(l), fi, EPI_PLAIN);
+        rc = gemm(s, l > 0, fo, fi, n, dz, 1, fo, hin, fi, 1, 0, grad + w_off(l), fi, EPI_PLAIN);
         if (rc) return rc;
         colsum_kernel<<<(fo + 127) / 128, 128, 0, s>>>(n, fo, dz, fo, grad + b_off(l));
         CUDA_TRY(cudaGetLastError());
         if (l > 0) {
             // dZ_{l-1}[s][i] = (sum_o dZ[s][o] W[o][i]) * gelu'(Z_{l-1}[s][i])
             float *dst = bufs[l & 1];
-            rc = gemm(s, n, fi, fo, dz, fo, 1, W, fi, 1, 1, dst, fi, EPI_DGELU, nullptr, w.Z[l - 1], HID);
+            rc = gemm(s, true, n, fi, fo, dz, fo, 1, W, fi, 1, 1, dst, fi, EPI_DGELU, nullptr, w.Z[l - 1], HID);
             if (rc) return rc;
             dz = dst;
         }

@@ -1,5 +1,10 @@
 """GPU parity of the surrogate MLP kernels (forward, backward, Adam) against the FP64
-oracle MLP evaluated with the same BF16-rounded weights."""
+oracle MLP evaluated with the same BF16-rounded weights and, in the 256-wide layers, the
+same BF16 operands (the tensor-core products round activations and output gradients to
+BF16 as they enter; the oracle rounds the same factors and sums exactly).  Tolerances: the
+GPU sums in FP32, and where an FP32 activation lies within rounding of a BF16 boundary the
+two sides may round it to neighbouring BF16 values (2^-8 apart), which moves a product by
+about 4e-3 of one term."""
 import numpy as np
 import pytest
 
@@ -48,8 +53,11 @@ def _setup(n, seed=0):
 def test_mlp_forward_matches_oracle(n):
     flat, rounded, x, t = _setup(n)
     y = g.mlp_forward(torch.tensor(flat, device=DEV), torch.tensor(x, device=DEV)).cpu().numpy()
-    ref = om.forward(rounded, x.astype(np.float64))
-    assert np.max(np.abs(y - ref)) < 2e-5 * np.max(np.abs(ref))
+    ref = om.forward(rounded, x.astype(np.float64), bf16_operands=True)
+    assert np.max(np.abs(y - ref)) < 2e-3 * np.max(np.abs(ref))
+    # and the BF16 operands are what the GPU computes: the unrounded network is farther away
+    full = om.forward(rounded, x.astype(np.float64))
+    assert np.max(np.abs(y - ref)) < 0.5 * np.max(np.abs(y - full))
 
 
 @pytest.mark.parametrize("n", [5, 300])
@@ -58,11 +66,17 @@ def test_mlp_backward_matches_oracle(n):
     grad, loss = g.mlp_backward(torch.tensor(flat, device=DEV), torch.tensor(x, device=DEV),
                                 torch.tensor(t, device=DEV))
     grad = grad.cpu().numpy().astype(np.float64)
-    ref = om.backward(rounded, x.astype(np.float64), t.astype(np.float64))
+    ref = om.backward(rounded, x.astype(np.float64), t.astype(np.float64), bf16_operands=True)
     ref_flat = _flat(ref)
-    assert abs(loss.item() - om.loss(rounded, x.astype(np.float64), t.astype(np.float64))) < 1e-5
-    scale = np.max(np.abs(ref_flat))
-    assert np.max(np.abs(grad - ref_flat)) < 1e-4 * scale
+    y_ref = om.forward(rounded, x.astype(np.float64), bf16_operands=True)
+    assert abs(loss.item() - float(np.mean((y_ref - t) ** 2))) < 1e-4 * float(np.mean((y_ref - t) ** 2))
+    # per layer, against that layer's largest gradient entry
+    o = 0
+    for W, b in ref:
+        for part in (W.ravel(), b):
+            seg = grad[o:o + part.size]
+            o += part.size
+            assert np.max(np.abs(seg - part)) < 2e-3 * np.max(np.abs(part)), (part.size,)
 
 
 def test_mlp_backward_deterministic():

@@ -226,3 +226,33 @@ def test_surrogate_loglik_reduces_to_the_gaussian_likelihood():
     # the inputs: box ends map to -1 and +1, an empty range to 0, rounded to FP32
     x = om.surrogate_inputs(np.array([[0.0, 1.0, 0.125]]), lo, hi, 3.0, 6.0)
     assert np.allclose(x, [[-1.0, 1.0, 0.0, 0.0, 0.0]], rtol=0, atol=1e-15)
+
+
+def test_bf16_operand_mode_reduces_to_the_plain_network(monkeypatch):
+    """The BF16-operand mode rounds the factors of the 256-wide layers' products and nothing
+    else: with the rounding made the identity it is the plain FP64 network and gradient, and
+    the first layer's inputs are never rounded."""
+    from oracle import mlp as om
+
+    rng = np.random.default_rng(8)
+    P = [(W, rng.normal(0, 0.1, b.shape)) for W, b in om.init_params(rng)]
+    x = rng.uniform(-1, 1, (6, 5))
+    t = rng.normal(size=(6, 80))
+    rounded_inputs = []
+    real = om.bf16_round
+
+    def spy(a):
+        rounded_inputs.append(np.asarray(a).shape)
+        return np.asarray(a, dtype=np.float64)
+
+    monkeypatch.setattr(om, "bf16_round", spy)
+    y1 = om.forward(P, x, bf16_operands=True)
+    g1 = om.backward(P, x, t, bf16_operands=True)
+    assert (6, 5) not in rounded_inputs  # the network inputs stay exact
+    monkeypatch.setattr(om, "bf16_round", real)
+    assert np.array_equal(y1, om.forward(P, x))
+    for (a, b), (c, d) in zip(g1, om.backward(P, x, t)):
+        assert np.array_equal(a, c) and np.array_equal(b, d)
+    # with the real rounding the outputs move, by about the BF16 spacing
+    y2 = om.forward(P, x, bf16_operands=True)
+    assert 0 < np.max(np.abs(y2 - y1)) < 0.05 * np.max(np.abs(y1))
