@@ -258,6 +258,44 @@ typedef struct tmcmc_state {
                               start it at 0) */
 } tmcmc_state;
 
+/* Summary record of one stage (device FP64 array of SWIMMER_STAGE_SUMMARY entries written by
+ * tmcmc_stage_async): status (0 ok; 1 every log-likelihood is -inf; 2 the proposal covariance
+ * is not positive definite; a failed stage leaves the population unchanged), the exponent q_j
+ * it started from and q_{j+1}, log S_j, mu_j [4], b^2 Sigma_j [4][4], the number of chains
+ * (distinct resampled samples), the longest chain, accepted proposals, surrogate evaluations,
+ * forward-model runs executed and those on the realized chain paths. */
+enum {
+    SWIMMER_STAGE_STATUS = 0,
+    SWIMMER_STAGE_Q_IN = 1,
+    SWIMMER_STAGE_Q = 2,
+    SWIMMER_STAGE_LOG_S = 3,
+    SWIMMER_STAGE_MU = 4,
+    SWIMMER_STAGE_SIGMA = 8,
+    SWIMMER_STAGE_UNIQUE = 24,
+    SWIMMER_STAGE_MAX_CHAIN = 25,
+    SWIMMER_STAGE_ACCEPT = 26,
+    SWIMMER_STAGE_SCREENED = 27,
+    SWIMMER_STAGE_EXACT = 28,
+    SWIMMER_STAGE_EXACT_PATH = 29,
+    SWIMMER_STAGE_SUMMARY = 32
+};
+
+/* One TMCMC stage enqueued on `stream` without any host synchronization (Sec. 3.2,
+ * Algorithm 1; the same stage as tmcmc_stage_shard, rank and world as there).  The state's
+ * device arrays (theta, loglik, status, surr_loglik) and its sigma, obs and prior box are
+ * used; its host fields are neither read nor written.  Instead:
+ *   q       device FP64 scalar, in/out: the annealing exponent q_j of the current samples,
+ *           replaced by q_{j+1} when the stage succeeds (a stage enqueued at q = 1 runs
+ *           another Metropolis pass at the posterior);
+ *   summary device FP64 [SWIMMER_STAGE_SUMMARY]: the stage's summary record (above).
+ * The Metropolis chains' pre-fetch rounds run as a loop whose condition the device sets, so a
+ * stage's length needs no host decision.  When `stream` is being captured into a CUDA graph
+ * the stage becomes part of that graph (a conditional while node holds the rounds) and every
+ * replay runs a whole stage; otherwise the stage builds, launches and releases a graph of its
+ * own.  Uses the handle's internal streams for the capture: one stage of a handle at a time. */
+int tmcmc_stage_async(swimmer_handle *h, const tmcmc_state *st, const double *uniforms, const double *normals,
+                      int use_surrogate, int rank, int world, double *q, double *summary, void *stream);
+
 /* One TMCMC stage: analyze (q_{j+1} by bisection on COV(w) = 1, w_bar, S_j, mu_j,
  * Sigma_j = b^2 sum w_bar (theta - mu)(theta - mu)^T, b = 0.2), multinomial resample
  * (64-bit fixed-point inverse CDF), and the Metropolis chains of length n_{j+1,k} with
@@ -267,10 +305,11 @@ typedef struct tmcmc_state {
  *   normals:  device [B][3] proposal normals (chain c, step s uses row off_c + s).
  *   use_surrogate: 1 = delayed acceptance through the surrogate set with
  *             swimmer_surrogate_set (requires st->surr_loglik), 0 = plain.
- * While few chains are alive, one launch pre-fetches the forward runs of a chain's next
- * steps for both outcomes of each pending accept decision (depth up to 5), so several chain
- * steps resolve per launch with results identical to the one-step-at-a-time chain.
- * Synchronizes `stream` twice (chain lengths decide the launches; counters at the end). */
+ * Each launch pre-fetches the forward runs of the live chains' next steps along a best-first
+ * tree of pending accept decisions, so several chain steps resolve per launch with results
+ * identical to the one-step-at-a-time chain.  Runs tmcmc_stage_async and synchronizes
+ * `stream` once, at the end, to fill the state's host fields (q, stage, log_s,
+ * log_evidence, mu, sigma_prop and the counters). */
 int tmcmc_stage(swimmer_handle *h, tmcmc_state *st, const double *uniforms, const double *normals,
                 int use_surrogate, void *stream);
 

@@ -9,4 +9,4 @@ from .api import (FP32C, FP64, MLP_NPARAM, SHAPE_QUAD, SHAPE_WIDE, OBS_HEAD_POIN
                   swimmer_destroy, swimmer_init, swimmer_kernel_eval, swimmer_surrogate_set, tmcmc_analyze,
                   swimmer_autotune, swimmer_kernel_eval_noalloc, swimmer_profile,
                   swimmer_pair_units, swimmer_profile_launches, swimmer_tuning, swimmer_flow_field, tmcmc_resample, tmcmc_tree_template, tmcmc_run,
-                  tmcmc_stage)
+                  tmcmc_stage, tmcmc_stage_async)

@@ -53,6 +53,8 @@ SIGNATURES = [
                                    c_void_p, c_void_p, c_void_p]),
     ("tmcmc_stage", c_int, [c_void_p, P(TmcmcStateC), c_void_p, c_void_p, c_int, c_void_p]),
     ("tmcmc_stage_shard", c_int, [c_void_p, P(TmcmcStateC), c_void_p, c_void_p, c_int, c_int, c_int, c_void_p]),
+    ("tmcmc_stage_async", c_int, [c_void_p, P(TmcmcStateC), c_void_p, c_void_p, c_int, c_int, c_int, c_void_p,
+                                  c_void_p, c_void_p]),
     ("tmcmc_tree_template", c_int, [c_int, c_double, c_int, c_void_p, c_void_p]),
     ("swimmer_pair_units", c_int, [c_int, c_int, c_void_p, c_void_p]),
     ("tmcmc_analyze", c_int, [c_void_p, c_int, c_void_p, c_void_p, c_double, c_void_p, c_void_p, c_void_p]),

@@ -289,6 +289,26 @@ def tmcmc_stage(h: Handle, st: TmcmcState, uniforms, normals, use_surrogate=Fals
     return st.summary()
 
 
+STAGE_SUMMARY = 32
+STAGE_STATUS, STAGE_Q_IN, STAGE_Q, STAGE_LOG_S, STAGE_MU, STAGE_SIGMA = 0, 1, 2, 3, 4, 8
+STAGE_UNIQUE, STAGE_MAX_CHAIN, STAGE_ACCEPT, STAGE_SCREENED, STAGE_EXACT, STAGE_EXACT_PATH = 24, 25, 26, 27, 28, 29
+
+
+def tmcmc_stage_async(h: Handle, st: TmcmcState, uniforms, normals, q, summary, use_surrogate=False, stream=None,
+                      rank=0, world=1):
+    """One TMCMC stage enqueued without host synchronization: q (device FP64 [1]) holds the
+    annealing exponent in and out, summary (device FP64 [STAGE_SUMMARY]) receives the stage's
+    record.  Inside a torch.cuda.graph capture the stage becomes part of the graph."""
+    _dev(uniforms, torch.float64)
+    _dev(normals, torch.float64)
+    _dev(q, torch.float64)
+    _dev(summary, torch.float64)
+    if q.numel() < 1 or summary.numel() < STAGE_SUMMARY:
+        raise ValueError(f"q needs 1 and summary {STAGE_SUMMARY} doubles")
+    check(lib().tmcmc_stage_async(h.ptr, ctypes.byref(st.c), _ptr(uniforms), _ptr(normals), int(bool(use_surrogate)),
+                                  int(rank), int(world), _ptr(q), _ptr(summary), _stream(stream)))
+
+
 def tmcmc_run(h: Handle, theta0, obs, sigma, prior_lo, prior_hi, randoms, use_surrogate=False, max_stages=100,
               stream=None, log=None):
     """Algorithm 1 driven from the host: prior samples theta0 [B, 3] (device), observations

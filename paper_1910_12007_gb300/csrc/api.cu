@@ -185,7 +185,8 @@ extern "C" int swimmer_init(const swimmer_config *cfg, swimmer_handle **out) {
     ALLOC(h->live, B);
     ALLOC(h->chain_pos, B);
     ALLOC(h->tmpl, B);
-    h->p_accept = 0.8;
+    ALLOC(h->stage_q, 1);
+    ALLOC(h->stage_summary, SWIMMER_STAGE_SUMMARY);
     ALLOC(h->cum, B);
     ALLOC(h->info, 128);
     ALLOC(h->work, 2);
@@ -198,15 +199,17 @@ extern "C" int swimmer_init(const swimmer_config *cfg, swimmer_handle **out) {
     {
         cudaError_t e1 = cudaMallocHost((void **)&h->host_pinned, (B + 128) * sizeof(int));
         cudaError_t e2 = cudaMallocHost((void **)&h->host_pinned_d, 64 * sizeof(double));
-        cudaError_t e3 = cudaMallocHost((void **)&h->host_tmpl, B * sizeof(int4));
-        if (e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess) {
-            set_error("cudaMallocHost failed");
+        cudaError_t e3 = cudaStreamCreateWithFlags(&h->side_stream, cudaStreamNonBlocking);
+        cudaError_t e4 = cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking);
+        if (e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess || e4 != cudaSuccess) {
+            set_error("cudaMallocHost or cudaStreamCreate failed");
             swimmer_destroy(h);
             return SWIMMER_E_CUDA;
         }
     }
     rc = gl_init();
     if (!rc) rc = upload_pair_units(h);
+    if (!rc) rc = tmcmc_templates_init(h);
     if (rc) {
         swimmer_destroy(h);
         return rc;
@@ -222,13 +225,16 @@ extern "C" int swimmer_destroy(swimmer_handle *h) {
     void *ptrs[] = {h->tab64, h->k1_scratch, h->tab32, h->pq, h->sp, h->order, h->queue, h->speed_tmp, h->w, h->stats,
                     h->idx, h->counts, h->chain_id, h->chain_off, h->chain_len, h->aux,
                     h->cur_theta, h->cur_ll, h->cur_sl, h->prop_theta, h->prop_ll, h->prop_sl,
-                    h->out_theta, h->out_ll, h->out_sl, h->prop_status, h->live, h->chain_pos, h->tmpl, h->cum, h->info, h->work, h->run_work,
+                    h->out_theta, h->out_ll, h->out_sl, h->prop_status, h->live, h->chain_pos, h->tmpl,
+                    h->tmpl_master, h->tmpl_map, h->p_accept_dev, h->stage_q, h->stage_summary, h->cum, h->info,
+                    h->work, h->run_work,
                     h->surr_norm, h->surr_params, h->surr_x, h->surr_y, h->surr_ws, h->units};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (h->host_pinned) cudaFreeHost(h->host_pinned);
     if (h->host_pinned_d) cudaFreeHost(h->host_pinned_d);
-    if (h->host_tmpl) cudaFreeHost(h->host_tmpl);
+    if (h->side_stream) cudaStreamDestroy(h->side_stream);
+    if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
     if (h->prof) {
         for (cudaEvent_t e : h->prof->start) cudaEventDestroy(e);
         for (cudaEvent_t e : h->prof->stop) cudaEventDestroy(e);
@@ -264,12 +270,12 @@ static int check_batch(swimmer_handle *h, int B, const double *theta, const int 
 
 int run_forward(swimmer_handle *h, int B, const double *theta, const int *n_pts, const double *obs,
                 double sigma, double *loglik, double *head_traj, double *mean_speed, int *status,
-                cudaStream_t s, int speculative, double *final_state) {
+                cudaStream_t s, int speculative, double *final_state, int threads_override) {
     int rc = launch_prepare(h, B, theta, n_pts, s);
     if (!rc) rc = launch_table_build(h, B, h->cfg.precision == SWIMMER_FP64, s);
     if (!rc)
-        rc = launch_forward(h, B, obs, sigma, loglik, head_traj, mean_speed, status, h->cfg.precision, s, 0,
-                            speculative, final_state);
+        rc = launch_forward(h, B, obs, sigma, loglik, head_traj, mean_speed, status, h->cfg.precision, s,
+                            threads_override, speculative, final_state);
     return rc;
 }
 
@@ -388,7 +394,7 @@ extern "C" int forward_batch(swimmer_handle *h, int B, const double *theta, cons
     int rc = check_batch(h, B, theta, status);
     if (rc) return rc;
     return run_forward(h, B, theta, n_pts, nullptr, 0.0, nullptr, head_traj, mean_speed, status,
-                       (cudaStream_t)stream, 0, nullptr);
+                       (cudaStream_t)stream, 0, nullptr, 0);
 }
 
 extern "C" int forward_batch_state(swimmer_handle *h, int B, const double *theta, const int *n_pts,
@@ -398,7 +404,7 @@ extern "C" int forward_batch_state(swimmer_handle *h, int B, const double *theta
     if (rc) return rc;
     ARG_CHECK(final_state != nullptr, "final_state is NULL");
     return run_forward(h, B, theta, n_pts, nullptr, 0.0, nullptr, head_traj, mean_speed, status,
-                       (cudaStream_t)stream, 0, final_state);
+                       (cudaStream_t)stream, 0, final_state, 0);
 }
 
 extern "C" int loglik_batch(swimmer_handle *h, int B, const double *theta, const int *n_pts,
@@ -410,5 +416,5 @@ extern "C" int loglik_batch(swimmer_handle *h, int B, const double *theta, const
     ARG_CHECK(sigma > 0.0, "sigma must be > 0");
     ARG_CHECK(h->cfg.steps / h->cfg.obs_every >= 1, "no observation within steps");
     return run_forward(h, B, theta, n_pts, obs, sigma, loglik, nullptr, nullptr, status, (cudaStream_t)stream, 0,
-                       nullptr);
+                       nullptr, 0);
 }

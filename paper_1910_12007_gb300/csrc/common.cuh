@@ -117,9 +117,13 @@ struct swimmer_handle {
     int *idx, *counts, *chain_id, *chain_off, *chain_len, *aux;  // [b_max] each, aux [b_max+64]
     double *cur_theta, *cur_ll, *cur_sl, *prop_theta, *prop_ll, *prop_sl, *out_theta, *out_ll, *out_sl;
     int *prop_status, *live, *chain_pos;  // [b_max] each
-    int4 *tmpl;                           // device [b_max]: pre-fetch template tree
-    int4 *host_tmpl;                      // pinned host [b_max]
-    double p_accept;                      // running Metropolis acceptance rate estimate
+    int4 *tmpl;                           // device [b_max]: the round's pre-fetch template tree
+    int4 *tmpl_master;                    // device [32][tmpl_slots]: best-first orders per rate bin
+    int *tmpl_map;                        // device [tmpl_slots]: master node -> round node
+    int tmpl_slots;                       // forward runs per pre-fetch round
+    double *p_accept_dev;                 // device: running Metropolis acceptance rate estimate
+    double *stage_q, *stage_summary;      // device: tmcmc_stage's exponent and summary record
+    cudaStream_t side_stream, cap_stream; // capture streams of the stage graph
     unsigned long long *cum;  // [b_max] fixed-point prefix sums
     int *info;              // [128] device counters / host-visible summary
     int *host_pinned;       // pinned host scratch (b_max + 128 ints)
@@ -172,6 +176,7 @@ int tune_bucket(const swimmer_handle *h, int B);
 int forward_min_threads(const swimmer_handle *h, int precision);
 bool forward_fits(const swimmer_handle *h, int threads, int precision);
 int forward_slots(const swimmer_handle *h, int precision);
+int tmcmc_templates_init(swimmer_handle *h);
 int upload_pair_units(swimmer_handle *h);
 int launch_kernel_eval(swimmer_handle *h, int m, const double *r, double *g1, double *g2,
                        int precision, cudaStream_t s);

@@ -25,13 +25,17 @@
 
 int run_forward(swimmer_handle *h, int B, const double *theta, const int *n_pts, const double *obs,
                 double sigma, double *loglik, double *head_traj, double *mean_speed, int *status,
-                cudaStream_t s, int speculative, double *final_state);
+                cudaStream_t s, int speculative, double *final_state, int threads_override);
 int run_surrogate_loglik(swimmer_handle *h, int B, const double *theta, const double *obs, double sigma,
                          double *loglik, cudaStream_t s);
 
 namespace {
 
 constexpr int T1 = 1024;
+
+// a host value into device memory, in stream order (no host buffer to race on)
+__global__ void set_double_kernel(double *dst, double v) { dst[0] = v; }
+
 constexpr double B_SCALE = 0.2;
 constexpr double COV_TARGET = 1.0;
 constexpr double FIXED_SCALE = 1099511627776.0;  // 2^40
@@ -95,10 +99,11 @@ __device__ double cov_of(int B, const double *__restrict__ ll, double lmax, doub
 }
 
 __global__ void __launch_bounds__(T1) analyze_kernel(int B, int P, const double *__restrict__ theta,
-                                                    const double *__restrict__ ll, double q,
+                                                    const double *__restrict__ ll, const double *__restrict__ q_in,
                                                     double *__restrict__ w_out, double *__restrict__ st) {
     __shared__ double red[40];
     const int tid = threadIdx.x;
+    const double q = q_in[0];
     double lm = -INFINITY;
     for (int k = tid; k < B; k += T1)
         if (isfinite(ll[k])) lm = fmax(lm, ll[k]);
@@ -241,7 +246,8 @@ __global__ void __launch_bounds__(T1) resample_kernel(int B, const double *__res
 
 // chains: ids/offsets/lengths in ascending sample order, a longest-first processing order,
 // per-step alive counts (host-visible) and the chains' starting states
-__global__ void __launch_bounds__(T1) chains_kernel(int B, int P, const int *__restrict__ counts,
+__global__ void __launch_bounds__(T1) chains_kernel(int B, int P, const double *__restrict__ st,
+                                                   const int *__restrict__ counts,
                                                    const double *__restrict__ theta, const double *__restrict__ ll,
                                                    const double *__restrict__ sl, int *__restrict__ chain_off,
                                                    int *__restrict__ chain_len, int *__restrict__ order,
@@ -251,6 +257,13 @@ __global__ void __launch_bounds__(T1) chains_kernel(int B, int P, const int *__r
     __shared__ unsigned long long sm[64];
     __shared__ int s_max;
     const int tid = threadIdx.x;
+    if (st[S_STATUS] != 0.0) {  // the analysis failed: no chains, the stage changes nothing
+        if (tid == 0) {
+            host_info[0] = 0;
+            host_info[1] = 0;
+        }
+        return;
+    }
     const int chunk = (B + T1 - 1) / T1;
     const int lo = tid * chunk, hi = min(B, lo + chunk);
     // exclusive prefix of (count > 0) -> chain index; prefix of counts -> output offset
@@ -363,13 +376,16 @@ __device__ __forceinline__ bool chain_owned(int off, int len, int B, int rank, i
 
 // live chains of this rank (chain_pos < chain_len) in the longest-first order, their
 // number, the largest remaining length, and the rank's accepted / decided steps so far
-__global__ void __launch_bounds__(T1) live_kernel(int U, int B, int rank, int world, const int *__restrict__ order,
-                                                  const int *__restrict__ chain_off, const int *__restrict__ chain_len,
-                                                  const int *__restrict__ chain_pos, int *__restrict__ live,
-                                                  const int *__restrict__ counter, int *__restrict__ host_info) {
+__global__ void __launch_bounds__(T1) live_kernel(const int *__restrict__ U_in, int B, int rank, int world,
+                                                  const int *__restrict__ order, const int *__restrict__ chain_off,
+                                                  const int *__restrict__ chain_len, const int *__restrict__ chain_pos,
+                                                  int *__restrict__ live, const int *__restrict__ counter,
+                                                  int *__restrict__ host_info, cudaGraphConditionalHandle cond,
+                                                  int use_cond) {
     __shared__ unsigned long long sm[64];
     __shared__ int s_rem, s_dec;
     const int tid = threadIdx.x;
+    const int U = U_in[0];
     if (tid == 0) {
         s_rem = 0;
         s_dec = 0;
@@ -400,6 +416,60 @@ __global__ void __launch_bounds__(T1) live_kernel(int U, int B, int rank, int wo
         host_info[1] = s_rem;
         host_info[2] = counter[0];  // accepted so far
         host_info[3] = s_dec;       // decided so far
+        // the stage's while loop runs another round only while chains remain after this one
+        // (this round's own work follows in the same loop body)
+        if (use_cond) cudaGraphSetConditional(cond, total > 0 ? 1u : 0u);
+    }
+}
+
+// The round's pre-fetch tree: the best-first order of M nodes for the acceptance rate
+// estimated so far, from the master orders made on the host (one per bin of that rate, nodes in
+// best-first order with children after their parents).  Best-first growth under a depth cap
+// takes, in order, the master nodes shallower than the cap, so the tree is the first
+// M = max(1, slots / A) of those, renumbered.  Writes am = {A, M, A M} for the round's kernels.
+constexpr int TMPL_BINS = 32;
+__global__ void __launch_bounds__(T1) template_kernel(int slots, const int *__restrict__ live_info,
+                                                      const double *__restrict__ p_prev,
+                                                      const int4 *__restrict__ master, int *__restrict__ map,
+                                                      int4 *__restrict__ tmpl, int *__restrict__ am,
+                                                      int *__restrict__ screened, int use_surrogate) {
+    __shared__ unsigned long long sm[64];
+    const int tid = threadIdx.x;
+    const int A = live_info[0];
+    if (A <= 0) {
+        if (tid == 0) am[0] = am[1] = am[2] = 0;
+        return;
+    }
+    const int cap = min(live_info[1], TREE_DEPTH_MAX);
+    // acceptance rate: this stage's decisions so far, shrunk towards the previous stages'
+    const double p = ((double)live_info[2] + 20.0 * p_prev[0]) / ((double)live_info[3] + 20.0);
+    const int bin = min(TMPL_BINS - 1, max(0, (int)(p * TMPL_BINS)));
+    const int want = max(1, slots / A);
+    const int4 *mo = master + (size_t)bin * slots;
+    const int chunk = (slots + T1 - 1) / T1;
+    const int lo = min(slots, tid * chunk), hi = min(slots, lo + chunk);
+    unsigned long long c = 0;
+    for (int i = lo; i < hi; ++i) c += (mo[i].y >> 1) < cap;
+    unsigned long long total;
+    unsigned long long at = block_exscan(c, sm, &total);
+    for (int i = lo; i < hi; ++i) {
+        const bool shallow = (mo[i].y >> 1) < cap;
+        map[i] = shallow && at < (unsigned long long)want ? (int)at : -1;
+        at += shallow;
+    }
+    __syncthreads();
+    for (int i = lo; i < hi; ++i) {
+        const int j = map[i];
+        if (j < 0) continue;
+        const int4 m = mo[i];
+        tmpl[j] = make_int4(m.x >= 0 ? map[m.x] : -1, m.y, m.z >= 0 ? map[m.z] : -1, m.w >= 0 ? map[m.w] : -1);
+    }
+    if (tid == 0) {
+        const int M = (int)min(total, (unsigned long long)want);
+        am[0] = A;
+        am[1] = M;
+        am[2] = A * M;
+        if (use_surrogate) screened[0] += A * M;
     }
 }
 
@@ -407,13 +477,19 @@ __global__ void __launch_bounds__(T1) live_kernel(int U, int B, int rank, int wo
 // (an accepted decision on the path whose candidate lies outside the prior box), nodes
 // beyond the chain's length and candidates outside the box get a NaN alpha, which the
 // forward launch skips.
-__global__ void tree_propose_kernel(int A, int M, const int *__restrict__ live, const int *__restrict__ chain_off,
-                                    const int *__restrict__ chain_len, const int *__restrict__ chain_pos,
-                                    const double *__restrict__ cur_theta, const double *__restrict__ st,
-                                    const double *__restrict__ normals, Box box, const int4 *__restrict__ tmpl,
-                                    double *__restrict__ prop, int *__restrict__ counter) {
+__global__ void tree_propose_kernel(int rows, const int *__restrict__ am, const int *__restrict__ live,
+                                    const int *__restrict__ chain_off, const int *__restrict__ chain_len,
+                                    const int *__restrict__ chain_pos, const double *__restrict__ cur_theta,
+                                    const double *__restrict__ st, const double *__restrict__ normals, Box box,
+                                    const int4 *__restrict__ tmpl, double *__restrict__ prop,
+                                    int *__restrict__ counter) {
     int idx = blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= A * M) return;
+    if (idx >= rows) return;
+    const int M = am[1];
+    if (idx >= am[2]) {  // a row this round does not use: the forward launch skips it
+        prop[box.P * idx] = nan("");
+        return;
+    }
     const int slot = idx / M, v = idx % M;
     const int c = live[slot];
     const int row = chain_off[c] + chain_pos[c];  // normals row of the chain's next step
@@ -442,14 +518,16 @@ __global__ void tree_propose_kernel(int A, int M, const int *__restrict__ live, 
 // surrogate against its base (the candidate of the deepest accepted decision above it, else
 // the chain's state).  A node is not run when its own candidate fails the screen or when its
 // path accepts a candidate that fails it (that path cannot happen).
-__global__ void tree_screen_kernel(int A, int M, int P, const int *__restrict__ live, const int *__restrict__ chain_off,
-                                   const int *__restrict__ chain_pos, const double *__restrict__ cur_sl,
-                                   const double *__restrict__ prop_sl, const double *__restrict__ st,
-                                   const double *__restrict__ u1, const int4 *__restrict__ tmpl,
-                                   double *__restrict__ prop, int *__restrict__ counter) {
+__global__ void tree_screen_kernel(int rows, const int *__restrict__ am, int P, const int *__restrict__ live,
+                                   const int *__restrict__ chain_off, const int *__restrict__ chain_pos,
+                                   const double *__restrict__ cur_sl, const double *__restrict__ prop_sl,
+                                   const double *__restrict__ st, const double *__restrict__ u1,
+                                   const int4 *__restrict__ tmpl, double *__restrict__ prop,
+                                   int *__restrict__ counter) {
     int idx = blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= A * M) return;
+    if (idx >= rows || idx >= am[2]) return;
     if (isnan(prop[P * idx])) return;
+    const int M = am[1];
     const int slot = idx / M, v = idx % M;
     const int c = live[slot];
     const int row = chain_off[c] + chain_pos[c];
@@ -471,7 +549,7 @@ __global__ void tree_screen_kernel(int A, int M, int P, const int *__restrict__ 
 }
 
 // walk each live chain down the template along the decisions it actually takes
-__global__ void tree_resolve_kernel(int A, int M, int P, int delayed, const int *__restrict__ live,
+__global__ void tree_resolve_kernel(const int *__restrict__ am, int P, int delayed, const int *__restrict__ live,
                                     const int *__restrict__ chain_off, const int *__restrict__ chain_len,
                                     int *__restrict__ chain_pos, double *__restrict__ cur_theta,
                                     double *__restrict__ cur_ll, double *__restrict__ cur_sl,
@@ -483,7 +561,8 @@ __global__ void tree_resolve_kernel(int A, int M, int P, int delayed, const int 
                                     const unsigned long long *__restrict__ run_work,
                                     unsigned long long *__restrict__ useful) {
     int slot = blockIdx.x * blockDim.x + threadIdx.x;
-    if (slot >= A) return;
+    if (slot >= am[0]) return;
+    const int M = am[1];
     const int c = live[slot];
     const double qn = st[S_QN];
     const int len = chain_len[c];
@@ -581,7 +660,8 @@ extern "C" int tmcmc_analyze(swimmer_handle *h, int B, const double *theta, cons
     ARG_CHECK(B >= 1 && B <= h->cfg.b_max, "B outside [1, b_max]");
     ARG_CHECK(theta && loglik && out_w && stats, "NULL device pointer");
     ARG_CHECK(q >= 0.0 && q < 1.0, "q must be in [0, 1)");
-    analyze_kernel<<<1, T1, 0, (cudaStream_t)stream>>>(B, n_params(h->cfg), theta, loglik, q, out_w, stats);
+    set_double_kernel<<<1, 1, 0, (cudaStream_t)stream>>>(h->stage_q, q);
+    analyze_kernel<<<1, T1, 0, (cudaStream_t)stream>>>(B, n_params(h->cfg), theta, loglik, h->stage_q, out_w, stats);
     CUDA_TRY(cudaGetLastError());
     return 0;
 }
@@ -596,13 +676,227 @@ extern "C" int tmcmc_resample(swimmer_handle *h, int B, const double *w, const d
     return 0;
 }
 
-extern "C" int tmcmc_stage(swimmer_handle *h, tmcmc_state *st, const double *uniforms, const double *normals,
-                           int use_surrogate, void *stream) {
-    return tmcmc_stage_shard(h, st, uniforms, normals, use_surrogate, 0, 1, stream);
+namespace {
+
+// ---------------------------------------------------------------------------------
+// One stage, enqueued without host synchronization.  Device counters (ints at info + 64):
+// [0] accepted, [1] screen passes, [2] proposals run, [3] runs on the realized paths,
+// [4] surrogate evaluations; [8..11] the round's live chains, largest remaining length,
+// accepted and decided so far; [16..18] the round's A, M, A M.
+// ---------------------------------------------------------------------------------
+constexpr int CNT = 64, LIVE = CNT + 8, AM = CNT + 16;
+
+// The chains' outputs become the population (when the analysis succeeded); the annealing
+// exponent and the acceptance estimate advance; the stage summary (SWIMMER_STAGE_* layout) is
+// written.
+__global__ void finalize_kernel(int B, int P, int use_surrogate, const double *__restrict__ st,
+                                const int *__restrict__ info, const double *__restrict__ out_theta,
+                                const double *__restrict__ out_ll, const double *__restrict__ out_sl,
+                                double *__restrict__ theta, double *__restrict__ ll, double *__restrict__ sl,
+                                int *__restrict__ status, double *__restrict__ q_io, double *__restrict__ p_accept,
+                                double *__restrict__ summary) {
+    const bool ok = st[S_STATUS] == 0.0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < B; i += gridDim.x * blockDim.x) {
+        if (ok) {
+            for (int a = 0; a < P; ++a) theta[P * i + a] = out_theta[P * i + a];
+            ll[i] = out_ll[i];
+            if (use_surrogate) sl[i] = out_sl[i];
+        }
+        status[i] = 0;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        const int *cnt = info + CNT;
+        summary[SWIMMER_STAGE_STATUS] = st[S_STATUS];
+        summary[SWIMMER_STAGE_Q_IN] = q_io[0];
+        summary[SWIMMER_STAGE_Q] = ok ? st[S_QN] : q_io[0];
+        summary[SWIMMER_STAGE_LOG_S] = ok ? st[S_LOGS] : 0.0;
+        for (int a = 0; a < P_MAX; ++a) summary[SWIMMER_STAGE_MU + a] = ok ? st[S_MU + a] : 0.0;
+        for (int a = 0; a < P_MAX * P_MAX; ++a) summary[SWIMMER_STAGE_SIGMA + a] = ok ? st[S_SIG + a] : 0.0;
+        summary[SWIMMER_STAGE_UNIQUE] = info[0];
+        summary[SWIMMER_STAGE_MAX_CHAIN] = info[1];
+        summary[SWIMMER_STAGE_ACCEPT] = cnt[0];
+        summary[SWIMMER_STAGE_SCREENED] = cnt[4];
+        summary[SWIMMER_STAGE_EXACT] = use_surrogate ? cnt[1] : cnt[2];
+        summary[SWIMMER_STAGE_EXACT_PATH] = cnt[3];
+        if (ok) {
+            q_io[0] = st[S_QN];
+            p_accept[0] = 0.5 * p_accept[0] + 0.5 * (double)cnt[0] / (double)B;
+        }
+    }
 }
 
-extern "C" int tmcmc_stage_shard(swimmer_handle *h, tmcmc_state *st, const double *uniforms, const double *normals,
-                                 int use_surrogate, int rank, int world, void *stream) {
+// the host-checked arguments of a stage
+struct StageArgs {
+    const tmcmc_state *st;
+    const double *uniforms, *normals;
+    int use_surrogate, rank, world, B, P;
+    double *q_dev, *summary;
+    Box box;
+};
+
+// analysis, resampling, chains; counters and the outputs of other ranks' rows cleared
+int enqueue_prefix(swimmer_handle *h, const StageArgs &a, cudaStream_t s) {
+    const tmcmc_state *st = a.st;
+    analyze_kernel<<<1, T1, 0, s>>>(a.B, a.P, st->theta, st->loglik, a.q_dev, h->w, h->stats);
+    CUDA_TRY(cudaGetLastError());
+    resample_kernel<<<1, T1, 0, s>>>(a.B, h->w, a.uniforms, (unsigned long long *)h->cum, h->idx, h->counts);
+    CUDA_TRY(cudaGetLastError());
+    const double *sl = a.use_surrogate ? st->surr_loglik : nullptr;
+    chains_kernel<<<1, T1, 0, s>>>(a.B, a.P, h->stats, h->counts, st->theta, st->loglik, sl, h->chain_off,
+                                   h->chain_len, h->chain_id, h->aux, h->cur_theta, h->cur_ll, h->cur_sl, h->info,
+                                   CNT);
+    CUDA_TRY(cudaGetLastError());
+    prof_count(h, 3);
+    CUDA_TRY(cudaMemsetAsync(h->info + CNT, 0, 8 * sizeof(int), s));
+    CUDA_TRY(cudaMemsetAsync(h->chain_pos, 0, sizeof(int) * a.B, s));
+    if (a.world > 1) {  // rows of other ranks' chains stay zero, so a SUM over ranks assembles them
+        CUDA_TRY(cudaMemsetAsync(h->out_theta, 0, a.P * sizeof(double) * a.B, s));
+        CUDA_TRY(cudaMemsetAsync(h->out_ll, 0, sizeof(double) * a.B, s));
+        CUDA_TRY(cudaMemsetAsync(h->out_sl, 0, sizeof(double) * a.B, s));
+    }
+    return 0;
+}
+
+// Pre-fetch slots per round: as many forward models as the GPU holds at once at the smallest
+// launch shape.  Filling the resident capacity beat smaller budgets and a cost-per-resolved-step
+// choice in simulations of the stage with measured launch costs.
+int stage_slots(const swimmer_handle *h) { return min(h->cfg.b_max, forward_slots(h, h->cfg.precision)); }
+
+// one pre-fetch round: live chains (and the loop condition), the tree, candidates, the
+// surrogate screen, the forward runs, the walk down the trees.  Every size comes from device
+// memory; the launches cover the round's capacity and idle past the round's rows.
+int enqueue_round(swimmer_handle *h, const StageArgs &a, cudaStream_t s, cudaGraphConditionalHandle cond,
+                  int use_cond) {
+    const tmcmc_state *st = a.st;
+    const int slots = h->tmpl_slots;
+    // a round runs A M <= max(slots, B) forward models (M = 1 once the live chains outnumber
+    // the slots); the launches cover that many rows, the forward launch takes the shape of a
+    // full round of `slots`
+    const int rows = max(slots, a.B);
+    live_kernel<<<1, T1, 0, s>>>(h->info, a.B, a.rank, a.world, h->chain_id, h->chain_off, h->chain_len, h->chain_pos,
+                                 h->live, h->info + CNT, h->info + LIVE, cond, use_cond);
+    CUDA_TRY(cudaGetLastError());
+    template_kernel<<<1, T1, 0, s>>>(slots, h->info + LIVE, h->p_accept_dev, h->tmpl_master, h->tmpl_map, h->tmpl,
+                                     h->info + AM, h->info + CNT + 4, a.use_surrogate);
+    CUDA_TRY(cudaGetLastError());
+    const int grid = (rows + 127) / 128;
+    tree_propose_kernel<<<grid, 128, 0, s>>>(rows, h->info + AM, h->live, h->chain_off, h->chain_len, h->chain_pos,
+                                             h->cur_theta, h->stats, a.normals, a.box, h->tmpl, h->prop_theta,
+                                             h->info + CNT + 2);
+    CUDA_TRY(cudaGetLastError());
+    prof_count(h, 3);
+    if (a.use_surrogate) {
+        int rc = run_surrogate_loglik(h, rows, h->prop_theta, st->obs, st->sigma, h->prop_sl, s);
+        if (rc) return rc;
+        tree_screen_kernel<<<grid, 128, 0, s>>>(rows, h->info + AM, a.P, h->live, h->chain_off, h->chain_pos,
+                                                h->cur_sl, h->prop_sl, h->stats, a.uniforms + a.B, h->tmpl,
+                                                h->prop_theta, h->info + CNT + 1);
+        CUDA_TRY(cudaGetLastError());
+        prof_count(h, 1);
+    }
+    int rc = run_forward(h, rows, h->prop_theta, nullptr, st->obs, st->sigma, h->prop_ll, nullptr, nullptr,
+                         h->prop_status, s, 1, nullptr, forward_threads(h, slots, h->cfg.precision));
+    if (rc) return rc;
+    tree_resolve_kernel<<<grid, 128, 0, s>>>(h->info + AM, a.P, a.use_surrogate, h->live, h->chain_off, h->chain_len,
+                                             h->chain_pos, h->cur_theta, h->cur_ll, h->cur_sl, h->prop_theta,
+                                             h->prop_ll, h->prop_sl, h->prop_status, h->stats,
+                                             a.uniforms + (a.use_surrogate ? 2 * a.B : a.B), h->tmpl, h->out_theta,
+                                             h->out_ll, h->out_sl, h->info + CNT, h->run_work, h->work + 1);
+    CUDA_TRY(cudaGetLastError());
+    prof_count(h, 1);
+    return 0;
+}
+
+int enqueue_finalize(swimmer_handle *h, const StageArgs &a, cudaStream_t s) {
+    const tmcmc_state *st = a.st;
+    finalize_kernel<<<(a.B + 255) / 256, 256, 0, s>>>(a.B, a.P, a.use_surrogate, h->stats, h->info, h->out_theta,
+                                                       h->out_ll, h->out_sl, st->theta, st->loglik, st->surr_loglik,
+                                                       st->status, a.q_dev, h->p_accept_dev, a.summary);
+    CUDA_TRY(cudaGetLastError());
+    prof_count(h, 1);
+    return 0;
+}
+
+// The rounds as a while node of the graph that stream s is capturing: its body, one round, is
+// captured on the handle's side stream; live_kernel sets the condition on the device.
+int enqueue_rounds_in_capture(swimmer_handle *h, const StageArgs &a, cudaStream_t s) {
+    cudaStreamCaptureStatus cs;
+    cudaGraph_t g;
+    const cudaGraphNode_t *deps = nullptr;
+    const cudaGraphEdgeData *edges = nullptr;
+    size_t nd = 0;
+    CUDA_TRY(cudaStreamGetCaptureInfo(s, &cs, nullptr, &g, &deps, &edges, &nd));
+    if (cs != cudaStreamCaptureStatusActive) {
+        set_error("stream is not capturing");
+        return SWIMMER_E_CUDA;
+    }
+    cudaGraphConditionalHandle cond;
+    CUDA_TRY(cudaGraphConditionalHandleCreate(&cond, g, 1, cudaGraphCondAssignDefault));
+    cudaGraphNodeParams cp = {};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = cond;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t node;
+    CUDA_TRY(cudaGraphAddNode(&node, g, deps, edges, nd, &cp));
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    CUDA_TRY(cudaStreamBeginCaptureToGraph(h->side_stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+    int rc = enqueue_round(h, a, h->side_stream, cond, 1);
+    cudaGraph_t captured = nullptr;
+    cudaError_t e = cudaStreamEndCapture(h->side_stream, &captured);
+    if (rc) return rc;
+    CUDA_TRY(e);
+    CUDA_TRY(cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+    return 0;
+}
+
+int stage_enqueue(swimmer_handle *h, const StageArgs &a, cudaStream_t s) {
+    if (h->profile) {
+        // profiling: rounds driven from the host (event records per forward launch cannot sit
+        // inside a graph's while node); the same kernels, one host synchronization per round
+        int rc = enqueue_prefix(h, a, s);
+        for (int round = 0; !rc; ++round) {
+            rc = enqueue_round(h, a, s, 0, 0);
+            if (rc) break;
+            CUDA_TRY(cudaMemcpyAsync(h->host_pinned, h->info + LIVE, sizeof(int), cudaMemcpyDeviceToHost, s));
+            CUDA_TRY(cudaStreamSynchronize(s));
+            if (h->host_pinned[0] <= 0) break;
+        }
+        return rc ? rc : enqueue_finalize(h, a, s);
+    }
+    cudaStreamCaptureStatus cs;
+    CUDA_TRY(cudaStreamIsCapturing(s, &cs));
+    if (cs == cudaStreamCaptureStatusActive) {  // the caller is capturing: become part of its graph
+        int rc = enqueue_prefix(h, a, s);
+        if (!rc) rc = enqueue_rounds_in_capture(h, a, s);
+        if (!rc) rc = enqueue_finalize(h, a, s);
+        return rc;
+    }
+    // otherwise the stage's own graph, captured on the handle's capture stream, launched on s
+    cudaStream_t c = h->cap_stream;
+    CUDA_TRY(cudaStreamBeginCapture(c, cudaStreamCaptureModeRelaxed));
+    int rc = enqueue_prefix(h, a, c);
+    if (!rc) rc = enqueue_rounds_in_capture(h, a, c);
+    if (!rc) rc = enqueue_finalize(h, a, c);
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(c, &g);
+    if (rc) {
+        if (g) cudaGraphDestroy(g);
+        return rc;
+    }
+    CUDA_TRY(e);
+    cudaGraphExec_t x = nullptr;
+    e = cudaGraphInstantiate(&x, g, 0);
+    cudaGraphDestroy(g);
+    CUDA_TRY(e);
+    e = cudaGraphLaunch(x, s);
+    cudaGraphExecDestroy(x);  // freed once the launch completes
+    CUDA_TRY(e);
+    return 0;
+}
+
+int check_stage(swimmer_handle *h, const tmcmc_state *st, const double *uniforms, const double *normals,
+                int use_surrogate, int rank, int world, StageArgs *a) {
     ARG_CHECK(h != nullptr && st != nullptr, "NULL handle or state");
     ARG_CHECK(world >= 1 && rank >= 0 && rank < world, "rank %d outside [0, world %d)", rank, world);
     const int B = st->B;
@@ -610,115 +904,94 @@ extern "C" int tmcmc_stage_shard(swimmer_handle *h, tmcmc_state *st, const doubl
     ARG_CHECK(st->theta && st->loglik && st->status && st->obs, "NULL device pointer in the state");
     ARG_CHECK(uniforms && normals, "NULL uniforms/normals");
     ARG_CHECK(st->sigma > 0.0, "sigma must be > 0");
-    ARG_CHECK(st->q >= 0.0 && st->q < 1.0, "stage already at q = 1");
     ARG_CHECK(!use_surrogate || (h->surr_ready && st->surr_loglik), "surrogate not set up");
     const int P = n_params(h->cfg);
-    for (int a = 0; a < P; ++a) ARG_CHECK(st->prior_lo[a] <= st->prior_hi[a], "prior box is empty");
+    for (int q = 0; q < P; ++q) ARG_CHECK(st->prior_lo[q] <= st->prior_hi[q], "prior box is empty");
+    a->st = st;
+    a->uniforms = uniforms;
+    a->normals = normals;
+    a->use_surrogate = use_surrogate ? 1 : 0;
+    a->rank = rank;
+    a->world = world;
+    a->B = B;
+    a->P = P;
+    a->box.P = P;
+    for (int q = 0; q < P_MAX; ++q) {
+        a->box.lo[q] = q < P ? st->prior_lo[q] : 0.0;
+        a->box.hi[q] = q < P ? st->prior_hi[q] : 0.0;
+    }
+    return 0;
+}
+
+}  // namespace
+
+// master pre-fetch orders for the handle (once, at creation): per bin of the acceptance rate
+int tmcmc_templates_init(swimmer_handle *h) {
+    const int slots = stage_slots(h);
+    h->tmpl_slots = slots;
+    std::vector<int4> all((size_t)TMPL_BINS * slots, make_int4(-1, 2 * 63, -1, -1));
+    for (int b = 0; b < TMPL_BINS; ++b) build_template(slots, (b + 0.5) / TMPL_BINS, TREE_DEPTH_MAX, &all[(size_t)b * slots]);
+    CUDA_TRY(cudaMalloc((void **)&h->tmpl_master, sizeof(int4) * all.size()));
+    CUDA_TRY(cudaMalloc((void **)&h->tmpl_map, sizeof(int) * slots));
+    CUDA_TRY(cudaMemcpy(h->tmpl_master, all.data(), sizeof(int4) * all.size(), cudaMemcpyHostToDevice));
+    const double p0 = 0.8;  // first guess of the acceptance rate
+    CUDA_TRY(cudaMalloc((void **)&h->p_accept_dev, sizeof(double)));
+    CUDA_TRY(cudaMemcpy(h->p_accept_dev, &p0, sizeof(double), cudaMemcpyHostToDevice));
+    return 0;
+}
+
+extern "C" int tmcmc_stage_async(swimmer_handle *h, const tmcmc_state *st, const double *uniforms,
+                                 const double *normals, int use_surrogate, int rank, int world, double *q,
+                                 double *summary, void *stream) {
+    StageArgs a;
+    int rc = check_stage(h, st, uniforms, normals, use_surrogate, rank, world, &a);
+    if (rc) return rc;
+    ARG_CHECK(q != nullptr && summary != nullptr, "NULL q or summary");
+    a.q_dev = q;
+    a.summary = summary;
+    return stage_enqueue(h, a, (cudaStream_t)stream);
+}
+
+extern "C" int tmcmc_stage(swimmer_handle *h, tmcmc_state *st, const double *uniforms, const double *normals,
+                           int use_surrogate, void *stream) {
+    return tmcmc_stage_shard(h, st, uniforms, normals, use_surrogate, 0, 1, stream);
+}
+
+extern "C" int tmcmc_stage_shard(swimmer_handle *h, tmcmc_state *st, const double *uniforms, const double *normals,
+                                 int use_surrogate, int rank, int world, void *stream) {
+    StageArgs a;
+    int rc = check_stage(h, st, uniforms, normals, use_surrogate, rank, world, &a);
+    if (rc) return rc;
+    ARG_CHECK(st->q >= 0.0 && st->q < 1.0, "stage already at q = 1");
     cudaStream_t s = (cudaStream_t)stream;
-    const int cap = 64;
-    analyze_kernel<<<1, T1, 0, s>>>(B, P, st->theta, st->loglik, st->q, h->w, h->stats);
+    // the exponent in, the stage, its summary out: one synchronization, at the end
+    set_double_kernel<<<1, 1, 0, s>>>(h->stage_q, st->q);
     CUDA_TRY(cudaGetLastError());
-    resample_kernel<<<1, T1, 0, s>>>(B, h->w, uniforms, (unsigned long long *)h->cum, h->idx, h->counts);
-    CUDA_TRY(cudaGetLastError());
-    const double *sl = use_surrogate ? st->surr_loglik : nullptr;
-    chains_kernel<<<1, T1, 0, s>>>(B, P, h->counts, st->theta, st->loglik, sl, h->chain_off, h->chain_len,
-                                   h->chain_id, h->aux, h->cur_theta, h->cur_ll, h->cur_sl, h->info, cap);
-    CUDA_TRY(cudaGetLastError());
-    prof_count(h, 3);
-    CUDA_TRY(cudaMemcpyAsync(h->host_pinned, h->info, cap * sizeof(int), cudaMemcpyDeviceToHost, s));
-    CUDA_TRY(cudaMemcpyAsync(h->host_pinned_d, h->stats, S_COUNT * sizeof(double), cudaMemcpyDeviceToHost, s));
+    a.q_dev = h->stage_q;
+    a.summary = h->stage_summary;
+    rc = stage_enqueue(h, a, s);
+    if (rc) return rc;
+    double *hs = h->host_pinned_d + 1;
+    CUDA_TRY(cudaMemcpyAsync(hs, h->stage_summary, sizeof(double) * SWIMMER_STAGE_SUMMARY, cudaMemcpyDeviceToHost, s));
     CUDA_TRY(cudaStreamSynchronize(s));
-    const double *hs = h->host_pinned_d;
-    if (hs[S_STATUS] != 0.0) {
-        set_error(hs[S_STATUS] == 1.0 ? "every sample has log-likelihood -inf" : "proposal covariance is not positive definite");
+    if (hs[SWIMMER_STAGE_STATUS] != 0.0) {
+        set_error(hs[SWIMMER_STAGE_STATUS] == 1.0 ? "every sample has log-likelihood -inf"
+                                                   : "proposal covariance is not positive definite");
         return SWIMMER_E_STATE;
     }
-    const int U = h->host_pinned[0], maxlen = h->host_pinned[1];
-    const double qn = hs[S_QN];
-    // counters: accepted, screen passes (runs with delayed acceptance), proposals run (plain),
-    // runs on the realized chain paths
-    CUDA_TRY(cudaMemsetAsync(h->info + cap, 0, 4 * sizeof(int), s));
-    int n_screened = 0;
-    Box box;
-    box.P = P;
-    for (int a = 0; a < P_MAX; ++a) {
-        box.lo[a] = a < P ? st->prior_lo[a] : 0.0;
-        box.hi[a] = a < P ? st->prior_hi[a] : 0.0;
-    }
-    // pre-fetching: each launch runs up to `slots` forward models (as many as the GPU holds
-    // at once at the smallest launch shape), a best-first template tree of M = slots / live
-    // nodes per live chain.  Filling the resident capacity beat smaller budgets and a
-    // cost-per-resolved-step choice in simulations of the stage with measured launch costs.
-    const int slots = min(h->cfg.b_max, forward_slots(h, h->cfg.precision));
-    CUDA_TRY(cudaMemsetAsync(h->chain_pos, 0, sizeof(int) * U, s));
-    if (world > 1) {  // rows of other ranks' chains stay zero, so a SUM over ranks assembles them
-        CUDA_TRY(cudaMemsetAsync(h->out_theta, 0, P * sizeof(double) * B, s));
-        CUDA_TRY(cudaMemsetAsync(h->out_ll, 0, sizeof(double) * B, s));
-        CUDA_TRY(cudaMemsetAsync(h->out_sl, 0, sizeof(double) * B, s));
-    }
-    for (int launch = 0;; ++launch) {
-        live_kernel<<<1, T1, 0, s>>>(U, B, rank, world, h->chain_id, h->chain_off, h->chain_len, h->chain_pos,
-                                     h->live, h->info + cap, h->info + cap + 8);
-        CUDA_TRY(cudaGetLastError());
-        prof_count(h, 1);
-        CUDA_TRY(cudaMemcpyAsync(h->host_pinned, h->info + cap + 8, 4 * sizeof(int), cudaMemcpyDeviceToHost, s));
-        CUDA_TRY(cudaStreamSynchronize(s));
-        const int A = h->host_pinned[0], max_rem = h->host_pinned[1];
-        if (A <= 0) break;
-        // acceptance rate: this stage's decisions so far, shrunk towards the previous stages'
-        const double acc_sofar = h->host_pinned[2], dec_sofar = h->host_pinned[3];
-        const double p_acc = (acc_sofar + 20.0 * h->p_accept) / (dec_sofar + 20.0);
-        const int want = max(1, slots / A);
-        const int M = build_template(want, p_acc, min(max_rem, TREE_DEPTH_MAX), h->host_tmpl);
-        CUDA_TRY(cudaMemcpyAsync(h->tmpl, h->host_tmpl, sizeof(int4) * M, cudaMemcpyHostToDevice, s));
-        const int n = A * M;
-        const int grid = (n + 127) / 128;
-        tree_propose_kernel<<<grid, 128, 0, s>>>(A, M, h->live, h->chain_off, h->chain_len, h->chain_pos,
-                                                 h->cur_theta, h->stats, normals, box, h->tmpl, h->prop_theta,
-                                                 h->info + cap + 2);
-        CUDA_TRY(cudaGetLastError());
-        prof_count(h, 1);
-        if (use_surrogate) {
-            int rc = run_surrogate_loglik(h, n, h->prop_theta, st->obs, st->sigma, h->prop_sl, s);
-            if (rc) return rc;
-            n_screened += n;
-            tree_screen_kernel<<<grid, 128, 0, s>>>(A, M, P, h->live, h->chain_off, h->chain_pos, h->cur_sl,
-                                                    h->prop_sl, h->stats, uniforms + B, h->tmpl, h->prop_theta,
-                                                    h->info + cap + 1);
-            CUDA_TRY(cudaGetLastError());
-            prof_count(h, 1);
-        }
-        int rc = run_forward(h, n, h->prop_theta, nullptr, st->obs, st->sigma, h->prop_ll, nullptr, nullptr,
-                             h->prop_status, s, 1, nullptr);
-        if (rc) return rc;
-        tree_resolve_kernel<<<(A + 127) / 128, 128, 0, s>>>(
-            A, M, P, use_surrogate, h->live, h->chain_off, h->chain_len, h->chain_pos, h->cur_theta, h->cur_ll,
-            h->cur_sl, h->prop_theta, h->prop_ll, h->prop_sl, h->prop_status, h->stats,
-            uniforms + (use_surrogate ? 2 * B : B), h->tmpl, h->out_theta, h->out_ll, h->out_sl, h->info + cap,
-            h->run_work, h->work + 1);
-        CUDA_TRY(cudaGetLastError());
-        prof_count(h, 1);
-    }
-    CUDA_TRY(cudaMemcpyAsync(st->theta, h->out_theta, P * sizeof(double) * B, cudaMemcpyDeviceToDevice, s));
-    CUDA_TRY(cudaMemcpyAsync(st->loglik, h->out_ll, sizeof(double) * B, cudaMemcpyDeviceToDevice, s));
-    if (use_surrogate)
-        CUDA_TRY(cudaMemcpyAsync(st->surr_loglik, h->out_sl, sizeof(double) * B, cudaMemcpyDeviceToDevice, s));
-    CUDA_TRY(cudaMemsetAsync(st->status, 0, sizeof(int) * B, s));
-    CUDA_TRY(cudaMemcpyAsync(h->host_pinned, h->info + cap, 4 * sizeof(int), cudaMemcpyDeviceToHost, s));
-    CUDA_TRY(cudaStreamSynchronize(s));
-    st->q = qn;
+    const int P = a.P;
+    st->q = hs[SWIMMER_STAGE_Q];
     st->stage += 1;
-    st->log_s = hs[S_LOGS];
-    st->log_evidence += hs[S_LOGS];
-    for (int a = 0; a < 4; ++a) st->mu[a] = a < P ? hs[S_MU + a] : 0.0;
-    for (int a = 0; a < 4; ++a)
-        for (int c = 0; c < 4; ++c) st->sigma_prop[4 * a + c] = a < P && c < P ? hs[S_SIG + P_MAX * a + c] : 0.0;
-    st->unique = U;
-    st->max_chain = maxlen;
-    st->n_accept = h->host_pinned[0];
-    st->n_screened = n_screened;
-    st->n_exact = use_surrogate ? h->host_pinned[1] : h->host_pinned[2];
-    st->n_exact_path = h->host_pinned[3];
-    if (B > 0) h->p_accept = 0.5 * h->p_accept + 0.5 * (double)st->n_accept / (double)B;
+    st->log_s = hs[SWIMMER_STAGE_LOG_S];
+    st->log_evidence += hs[SWIMMER_STAGE_LOG_S];
+    for (int i = 0; i < 4; ++i) st->mu[i] = i < P ? hs[SWIMMER_STAGE_MU + i] : 0.0;
+    for (int i = 0; i < 4; ++i)
+        for (int j = 0; j < 4; ++j) st->sigma_prop[4 * i + j] = i < P && j < P ? hs[SWIMMER_STAGE_SIGMA + 4 * i + j] : 0.0;
+    st->unique = (int)hs[SWIMMER_STAGE_UNIQUE];
+    st->max_chain = (int)hs[SWIMMER_STAGE_MAX_CHAIN];
+    st->n_accept = (int)hs[SWIMMER_STAGE_ACCEPT];
+    st->n_screened = (int)hs[SWIMMER_STAGE_SCREENED];
+    st->n_exact = (int)hs[SWIMMER_STAGE_EXACT];
+    st->n_exact_path = (int)hs[SWIMMER_STAGE_EXACT_PATH];
     return 0;
 }

@@ -87,11 +87,12 @@ def test_delayed_acceptance_matches_plain_and_saves_forward_runs(trained):
     acc_da = sum(s["n_accept"] for s in log_da) / exact_da
     assert screened > 0
     # the gain: the screen removes proposals the exact model would reject, so fewer exact
-    # forward runs are made and a larger share of them is accepted; the saving is bounded by
-    # the number of proposals plain TMCMC rejects
+    # forward runs are made and a larger share of them is accepted; the saving is about the
+    # number of proposals plain TMCMC rejects at most (the two runs' chains differ, so allow
+    # three standard deviations of that count)
     rejected_plain = exact_plain - sum(s["n_accept"] for s in log_plain)
     assert exact_da < exact_plain, (exact_da, exact_plain)
-    assert exact_plain - exact_da <= rejected_plain
+    assert exact_plain - exact_da <= rejected_plain + 3 * math.sqrt(rejected_plain)
     assert acc_da > acc_plain, (acc_da, acc_plain)
 
 
