@@ -146,48 +146,78 @@ def kernel_traffic():
 # -------------------------------------------------------------------------------------
 # oracle (CPU) legs
 # -------------------------------------------------------------------------------------
-def oracle_sample(samples=16, steps=10000, threads=None):
-    """Time the FP64 C oracle on `samples` forward runs of the workload's swimmer."""
-    import numpy as np
+def host_cores():
+    """Host CPUs this process may run on: (count, affinity list as ranges)."""
+    try:
+        cpus = sorted(os.sched_getaffinity(0))
+    except AttributeError:
+        cpus = list(range(os.cpu_count() or 1))
+    ranges, start = [], None
+    for i, c in enumerate(cpus):
+        if start is None:
+            start = c
+        if i + 1 == len(cpus) or cpus[i + 1] != c + 1:
+            ranges.append(f"{start}-{c}" if c > start else f"{c}")
+            start = None
+    return len(cpus), ",".join(ranges)
 
-    import synthetic
-    from oracle import swimmer as sw
 
-    threads = threads or os.cpu_count() or 1
-    base = sw.SwimmerParams(n=N_PTS, dt=DT, steps=steps, obs_every=OBS_EVERY)
-    thetas = synthetic.prior_samples(99, PRIOR_LO, PRIOR_HI, samples)
-    thetas[:, 1] = np.minimum(thetas[:, 1], 0.2)  # stay in the stable K_C range
-    ps = [base.with_theta(t) for t in thetas]
-    t0 = time.perf_counter()
-    tables = [sw.kernel_table(p) for p in ps]
-    t1 = time.perf_counter()
-    sw.run_c_batch(ps, tables, threads=threads)
-    t2 = time.perf_counter()
-    pairs = samples * N_PTS * N_PTS * steps
-    return {"pairs": pairs, "seconds": t2 - t0, "table_seconds": t1 - t0, "cores": threads,
-            "sample": f"{samples} forward runs x {steps} Euler steps of the N=128 workload swimmer "
-                      f"(FP64 C oracle, OpenMP over samples, kernel tables included)"}
+class OracleSample:
+    """The FP64 C oracle on a bounded sample of the workload: `samples` forward runs of the
+    workload's swimmer (prior draws with K_C in the stable range) of `steps` Euler steps, one
+    run per host core (OpenMP over runs).  The per-run kernel tables are built once, untimed,
+    as the GPU path builds its tables once per run outside its per-step loop; `time()` runs
+    the time loops."""
+
+    def __init__(self, samples=None, steps=5000):
+        import numpy as np
+
+        import synthetic
+        from oracle import swimmer as sw
+
+        self.sw = sw
+        self.cores, self.affinity = host_cores()
+        self.samples = samples or self.cores
+        self.steps = steps
+        base = sw.SwimmerParams(n=N_PTS, dt=DT, steps=steps, obs_every=OBS_EVERY)
+        thetas = synthetic.prior_samples(99, PRIOR_LO, PRIOR_HI, self.samples)
+        thetas[:, 1] = np.minimum(thetas[:, 1], 0.2)  # stay in the stable K_C range
+        self.ps = [base.with_theta(t) for t in thetas]
+        self.tables = [sw.kernel_table(p) for p in self.ps]
+
+    def time(self):
+        t0 = time.perf_counter()
+        self.sw.run_c_batch(self.ps, self.tables, threads=min(self.cores, self.samples))
+        return time.perf_counter() - t0
+
+    @property
+    def pairs(self):
+        return self.samples * N_PTS * N_PTS * self.steps
+
+    def describe(self):
+        return (f"{self.samples} forward runs x {self.steps} Euler steps of the N={N_PTS} workload swimmer (FP64 C "
+                f"oracle, OpenMP over runs on {min(self.cores, self.samples)} threads, host CPUs {self.affinity}; "
+                f"kernel tables built once, untimed)")
 
 
 def reference_arm(args, rank):
     if rank != 0:
         return 0
     W, K = args.warmup, args.steps
-    times, pairs = [], 0
-    r = None
+    o = OracleSample()
+    times = []
     for i in range(W + K):
-        r = oracle_sample(samples=8, steps=1000)
+        t = o.time()
         if i >= W:
-            times.append(r["seconds"])
-            pairs += r["pairs"]
+            times.append(t)
     tot = sum(times)
-    value = pairs / tot
+    value = o.pairs * K / tot
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "pair-evals/s", "n_gpus": args.gpus,
         "steps": K, "warmup": W, "ms_per_step": 1e3 * tot / K, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": workload_config("fp64-oracle"),
-        "cpu_baseline": {"value": value, "unit": "pair-evals/s", "cores": r["cores"], "kind": "oracle",
-                         "sample": "per step: " + r["sample"]},
+        "cpu_baseline": {"value": value, "unit": "pair-evals/s", "cores": min(o.cores, o.samples),
+                         "affinity": o.affinity, "kind": "oracle", "sample": "per step: " + o.describe()},
         "e2e": {"value": value, "unit": "pair-evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -205,6 +235,12 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="fp32c", choices=["fp32c", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-forms", action="store_true",
+                    help="leave out the side-by-side leg of the plain FP64, batched FP32 and surrogate forms")
+    ap.add_argument("--horizon", default="short", choices=["short", "full"],
+                    help="--workload posterior: the benchmark's 2e4-step horizon, or the configured two beats "
+                         "(1.28e6 steps at the stable dt)")
+    ap.add_argument("--seeds", type=int, default=4, help="--workload posterior: TMCMC runs per precision")
     ap.add_argument("--shard-stage", action="store_true",
                     help="N > 1: one TMCMC population sharded over the ranks (strong scaling, one SUM "
                          "all-reduce per stage) instead of an independent TMCMC per rank (weak scaling)")
@@ -451,15 +487,101 @@ def main():
                          "launches": int(k2_launches), "avg_launch_ms": k2_avg_ms,
                          "peak_note": f"FP32 {sm_count} SMs x 128 lanes x 2 x {max_mhz:.0f} MHz ({peak_src} max clock)"},
         }
+        if world == 1 and not args.no_forms:
+            line["forms"] = forms_leg(dev)
         if world == 1 and not args.no_cpu_baseline:
-            r = oracle_sample()
-            line["cpu_baseline"] = {"value": r["pairs"] / r["seconds"], "unit": "pair-evals/s", "cores": r["cores"],
-                                    "kind": "oracle", "sample": r["sample"]}
+            o = OracleSample()
+            secs = o.time()
+            line["cpu_baseline"] = {"value": o.pairs / secs, "unit": "pair-evals/s",
+                                    "cores": min(o.cores, o.samples), "affinity": o.affinity, "kind": "oracle",
+                                    "sample": o.describe()}
         print(json.dumps(line), flush=True)
     h.close()
     if dist is not None:
         dist.destroy_process_group()
     return 0
+
+
+def forms_leg(dev, seed=700):
+    """The three forms side by side on one inference problem: whole TMCMC runs to q = 1 with the
+    plain FP64 kernel, the batched FP32 kernel and the FP32 kernel behind the learned surrogate
+    (delayed acceptance), sharing every random number.  The TMCMC workload's swimmer (1024
+    samples per stage, N = 128, dt = 1e-4/64) over a 2000-step horizon, head x, y every 50
+    steps (the 40 times the surrogate predicts), noise 5 % of the head's mean displacement
+    (several stages).  The surrogate is trained
+    on 50k forward runs of the prior sampler by the library's MLP kernels first (timed apart).
+    Samples/s count every stage's population; the posterior gaps are against the FP64 run."""
+    import numpy as np
+    import torch
+
+    import paper_1910_12007_gb300 as g
+    import synthetic
+    from paper_1910_12007_gb300 import surrogate as sg
+
+    steps, obs_every = 2000, 50
+    cfgs = {name: g.SwimmerConfig(n_max=N_PTS, b_max=B_STAGE, length=1.0, dt=DT, steps=steps, obs_every=obs_every,
+                                  precision=prec) for name, prec in (("fp64", g.FP64), ("fp32c", g.FP32C))}
+    hs = {name: g.swimmer_init(c) for name, c in cfgs.items()}
+    th_tune = torch.tensor(synthetic.prior_samples(4242, PRIOR_LO, PRIOR_HI, B_STAGE), device=dev)
+    for h in hs.values():
+        g.swimmer_autotune(h, steps=200, theta=th_tune)
+    xi = g.forward_batch(hs["fp64"], torch.tensor([THETA_TRUE], dtype=torch.float64, device=dev))[0][0].cpu().numpy()
+    sigma = 0.05 * float(np.mean(np.abs(xi - [1.0, 0.0])))
+    obs = torch.tensor(xi + sigma * synthetic.normals(1236, synthetic.NOISE, 0, xi.size).reshape(xi.shape),
+                       device=dev)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    th_train = torch.tensor(synthetic.prior_samples(seed + 77, PRIOR_LO, PRIOR_HI, 50000), device=dev)
+    traj, status = sg.generate_training_set(hs["fp32c"], th_train)
+    torch.cuda.synchronize()
+    t_gen = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    sur = sg.train(hs["fp32c"], th_train, PRIOR_LO, PRIOR_HI, epochs=40, batch=2048, lr=2e-3, seed=1, traj=traj,
+                   status=status)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    th_val = torch.tensor(synthetic.prior_samples(seed + 78, PRIOR_LO, PRIOR_HI, 2048), device=dev)
+    tv, sv = sg.generate_training_set(hs["fp32c"], th_val)
+    val_err = sg.validation_error(sur, tv, th_val, sv)
+    out = {}
+    for form, name, da in (("plain_fp64", "fp64", False), ("batched_fp32", "fp32c", False),
+                           ("surrogate_fp32", "fp32c", True)):
+        h = hs[name]
+        if da:
+            sur.attach(h)
+        th0 = torch.tensor(synthetic.prior_samples(seed, PRIOR_LO, PRIOR_HI, B_STAGE), device=dev)
+        log = []
+        g.swimmer_profile(h, 1)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        st = g.tmcmc_run(h, th0, obs, sigma, PRIOR_LO, PRIOR_HI, lambda j: synthetic.stage_randoms(seed, j, B_STAGE, 3),
+                         use_surrogate=da, log=log)
+        torch.cuda.synchronize()
+        el = time.perf_counter() - t0
+        _, _, _, pairs_exec, pairs = g.swimmer_profile(h, 2)
+        g.swimmer_profile(h, 0)
+        th = st.theta.cpu().numpy()
+        out[form] = {"tmcmc_samples_per_s": B_STAGE * (len(log) + 1) / el, "seconds": el, "stages": len(log),
+                     "pair_evals_per_s": pairs / el, "executed_pair_evals_per_s": pairs_exec / el,
+                     "exact_forward_runs": int(sum(s["n_exact_path"] for s in log) + B_STAGE),
+                     "posterior_mean": th.mean(0).tolist(), "posterior_sd": th.std(0).tolist(),
+                     "accepts": [s["n_accept"] for s in log]}
+        if da:
+            out[form]["screened"] = int(sum(s["n_screened"] for s in log))
+    for h in hs.values():
+        h.close()
+    m64, s64 = np.array(out["plain_fp64"]["posterior_mean"]), np.array(out["plain_fp64"]["posterior_sd"])
+    for form in ("batched_fp32", "surrogate_fp32"):
+        m, sd = np.array(out[form]["posterior_mean"]), np.array(out[form]["posterior_sd"])
+        out[form]["mean_gap_rel_vs_fp64"] = (np.abs(m - m64) / np.maximum(np.abs(m64), s64)).tolist()
+        out[form]["sd_gap_rel_vs_fp64"] = (np.abs(sd - s64) / s64).tolist()
+        out[form]["same_decisions_as_fp64"] = out[form]["accepts"] == out["plain_fp64"]["accepts"]
+    out["surrogate_fp32"]["training"] = {"runs": 50000, "generate_s": t_gen, "train_s": t_train,
+                                         "val_rel_rmse": val_err}
+    out["workload"] = ("TMCMC to q = 1, 1024 samples/stage, N=128, dt=1e-4/64, 2000 steps per run, head x,y every "
+                       "50 steps, noise 5% of the head's mean displacement; shared random streams")
+    out["gap_scale"] = "mean gaps relative to max(|mean|, sd) of the FP64 posterior; sd gaps relative to its sd"
+    return out
 
 
 def shape_arg(g, s):
@@ -588,12 +710,12 @@ def forward_workload(args, rank, world, local_rank):
         dist.barrier()
     clk = clocks.stop()
     ms = e0.elapsed_time(e1)
-    k2_ms, k2_launches, launches, _, pairs = g.swimmer_profile(h, 2)
-    # graph replays bypass the host-side profiling hooks: count from the workload instead
+    k2_ms, k2_launches, launches, pairs, _ = g.swimmer_profile(h, 2)
+    # the forward kernel counts the pair evaluations each run executed (n^2 x the steps it
+    # ran, so a run that stopped early counts only its steps), graph replays included
+    if pairs <= 0:
+        raise RuntimeError("the forward kernel's work counters read zero")
     n_tot = cfg.n_max
-    if pairs == 0:
-        n2 = (ns.astype(np.float64) ** 2).sum() if ns is not None else B * float(n_tot) ** 2
-        pairs = n2 * steps * args.steps
     status = graph.out[2].cpu().numpy()
     (pairs, ok_all, samples_all), (ms,) = ranks.totals(dist, [pairs, float(np.sum(status == 0)), B], [ms], device=dev)
     peaks, _ = load_peaks()
@@ -780,6 +902,21 @@ def sperm_tmcmc_workload(args, rank, local_rank):
 # whole TMCMC runs to q = 1 at the TMCMC workload's full size, FP32 kernel vs FP64 kernel
 # -------------------------------------------------------------------------------------
 def posterior_workload(args, rank, local_rank):
+    """Posterior moments of the FP32 kernel against the FP64 kernel (which equals the FP64
+    oracle to 1e-8 sample by sample in the tests), on the TMCMC workload: 1024 samples per
+    stage, N = 128, dt = 1e-4/64, head x, y observed, 5 % noise.
+
+    --horizon short: 2e4 Euler steps, observations every 100 (the benchmark's horizon).  Per
+    seed, one FP64 and one FP32 TMCMC run sharing every random number; then the FP64
+    log-likelihood at the FP32 run's final samples.
+    --horizon full: the configured two beats, 1.28e6 steps, the same 200 observation times
+    (every 6400 steps).  FP32 TMCMC runs; the FP64 log-likelihood at a subsample of 152 of
+    their final samples (a whole FP64 TMCMC run at this horizon takes hours).
+
+    A target posterior whose log-likelihood differs by at most eps has every moment within a
+    factor exp(2 eps) of the other's; the FP64 moments follow from the FP32 samples by
+    reweighting with exp(l64 - l32).  The Monte-Carlo standard error of one run's moments is the
+    spread over the seeds."""
     import numpy as np
     import torch
 
@@ -790,59 +927,111 @@ def posterior_workload(args, rank, local_rank):
         return 0  # a comparison of two precisions on one GPU: rank 0 alone runs it
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
-    seed = 600
-    results = {}
-    obs = sigma = None
+    full = args.horizon == "full"
+    steps, obs_every = (1280000, 6400) if full else (STEPS, OBS_EVERY)
+    seeds = [600 + i for i in range(args.seeds)]
+    hs = {}
     for name, prec in (("fp64", g.FP64), ("fp32c", g.FP32C)):
-        cfg = g.SwimmerConfig(n_max=N_PTS, b_max=B_STAGE, length=1.0, dt=DT, steps=STEPS, obs_every=OBS_EVERY,
+        cfg = g.SwimmerConfig(n_max=N_PTS, b_max=B_STAGE, length=1.0, dt=DT, steps=steps, obs_every=obs_every,
                               precision=prec)
-        h = g.swimmer_init(cfg)
-        th_tune = torch.tensor(synthetic.prior_samples(4242, PRIOR_LO, PRIOR_HI, B_STAGE), device=dev)
-        g.swimmer_autotune(h, steps=200, theta=th_tune)
-        if obs is None:  # one data set (the FP64 model at theta* plus 5 % noise) for both
-            xi = g.forward_batch(h, torch.tensor([THETA_TRUE], dtype=torch.float64, device=dev))[0][0].cpu().numpy()
-            sigma = NOISE * float(np.mean(np.abs(xi)))
-            D = xi + sigma * synthetic.normals(1234, synthetic.NOISE, 0, xi.size).reshape(xi.shape)
-            obs = torch.tensor(D, dtype=torch.float64, device=dev)
+        hs[name] = g.swimmer_init(cfg)
+    th_tune = torch.tensor(synthetic.prior_samples(4242, PRIOR_LO, PRIOR_HI, B_STAGE), device=dev)
+    g.swimmer_autotune(hs["fp32c"], steps=200, theta=th_tune)
+    if not full:
+        g.swimmer_autotune(hs["fp64"], steps=200, theta=th_tune)
+    # one data set for all runs: the FP64 model at theta* plus 5 % noise
+    xi = g.forward_batch(hs["fp64"], torch.tensor([THETA_TRUE], dtype=torch.float64, device=dev))[0][0].cpu().numpy()
+    sigma = NOISE * float(np.mean(np.abs(xi)))
+    D = xi + sigma * synthetic.normals(1234, synthetic.NOISE, 0, xi.size).reshape(xi.shape)
+    obs = torch.tensor(D, dtype=torch.float64, device=dev)
+
+    def run(name, seed):
         th0 = torch.tensor(synthetic.prior_samples(seed, PRIOR_LO, PRIOR_HI, B_STAGE), device=dev)
         log = []
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        st = g.tmcmc_run(h, th0, obs, sigma, PRIOR_LO, PRIOR_HI,
+        st = g.tmcmc_run(hs[name], th0, obs, sigma, PRIOR_LO, PRIOR_HI,
                          lambda j: synthetic.stage_randoms(seed, j, B_STAGE, 3), log=log)
         torch.cuda.synchronize()
         el = time.perf_counter() - t0
         th = st.theta.cpu().numpy()
-        results[name] = {"seconds": el, "stages": len(log), "samples_per_s": B_STAGE * len(log) / el,
-                         "q": [s["q"] for s in log], "log_evidence": log[-1]["log_evidence"],
-                         "posterior_mean": th.mean(0).tolist(), "posterior_sd": th.std(0).tolist()}
+        return th, st.loglik.cpu().numpy(), log, el
+
+    per_seed = []
+    m32s, s32s = [], []
+    for seed in seeds:
+        th32, ll32, log32, t32 = run("fp32c", seed)
+        rec = {"seed": seed, "fp32c": {"seconds": t32, "stages": len(log32),
+                                       "samples_per_s": B_STAGE * len(log32) / t32,
+                                       "q": [s["q"] for s in log32], "mean": th32.mean(0).tolist(),
+                                       "sd": th32.std(0).tolist(), "log_evidence": log32[-1]["log_evidence"]}}
+        m32s.append(th32.mean(0))
+        s32s.append(th32.std(0))
+        # the FP64 log-likelihood at the FP32 run's final samples (all, or 152 of them)
+        rows = np.arange(B_STAGE) if not full else np.sort(
+            np.argsort(synthetic.uniforms(seed, synthetic.PRIOR, 9, B_STAGE))[:152])
+        sub = torch.tensor(th32[rows], device=dev)
+        ll64_at, st64 = g.loglik_batch(hs["fp64"], sub.contiguous(), obs, sigma)
+        torch.cuda.synchronize()
+        a, b = ll32[rows], ll64_at.cpu().numpy()
+        ok = st64.cpu().numpy() == 0
+        eps = float(np.max(np.abs(a - b)[ok]))
+        w = np.exp(b[ok] - a[ok])
+        w /= w.sum()
+        t = th32[rows][ok]
+        m_plain, s_plain = t.mean(0), t.std(0)
+        m_rw = w @ t
+        s_rw = np.sqrt(w @ (t - m_rw) ** 2)
+        rec["reweighted"] = {"samples": int(ok.sum()), "max_abs_dloglik": eps,
+                             "moment_bound_rel": float(np.expm1(2 * eps)),
+                             "mean_gap_rel_sd": (np.abs(m_rw - m_plain) / s_plain).tolist(),
+                             "sd_gap_rel": (np.abs(s_rw - s_plain) / s_plain).tolist()}
+        if not full:
+            th64, _, log64, t64 = run("fp64", seed)
+            m64, s64 = th64.mean(0), th64.std(0)
+            rec["fp64"] = {"seconds": t64, "stages": len(log64), "samples_per_s": B_STAGE * len(log64) / t64,
+                           "q": [s["q"] for s in log64], "mean": m64.tolist(), "sd": s64.tolist()}
+            rec["coupled"] = {"same_decisions": [s["n_accept"] for s in log32] == [s["n_accept"] for s in log64],
+                              "mean_gap_rel": (np.abs(m32s[-1] - m64) / np.maximum(np.abs(m64), s64)).tolist(),
+                              "sd_gap_rel": (np.abs(s32s[-1] - s64) / s64).tolist()}
+        per_seed.append(rec)
+        print(json.dumps({"progress": rec}), flush=True)
+    for h in hs.values():
         h.close()
-    r64, r32 = results["fp64"], results["fp32c"]
-    m64, s64 = np.array(r64["posterior_mean"]), np.array(r64["posterior_sd"])
-    m32, s32 = np.array(r32["posterior_mean"]), np.array(r32["posterior_sd"])
-    # Monte Carlo standard error of the difference of two runs' means and sds: TMCMC keeps
-    # the weights' COV at 1, an effective sample size of B / 2 per population
-    ess = B_STAGE / 2.0
-    se_mean = np.sqrt(2.0) * s64 / np.sqrt(ess)
-    se_sd = np.sqrt(2.0) * s64 / np.sqrt(2.0 * ess)
-    line = {"metric": METRIC, "value": r32["samples_per_s"], "unit": "TMCMC samples/s", "n_gpus": 1, "steps": 1,
-            "warmup": 0, "ms_per_step": 1e3 * r32["seconds"], "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": "whole TMCMC runs to q = 1 on the TMCMC workload (1024 samples/stage, N=128, 2e4 "
-                                   "steps per run, head x,y every 100 steps, 5% noise), FP32 kernel vs FP64 kernel "
-                                   "(the FP64 kernel equals the FP64 oracle to 1e-8 sample by sample in the tests)"},
-            "fp32c": r32, "fp64": r64,
-            "mean_rel_diff": (np.abs(m32 - m64) / np.abs(m64)).tolist(),
-            "sd_rel_diff": (np.abs(s32 - s64) / s64).tolist(),
-            "within_2pct": bool(np.all(np.abs(m32 - m64) <= 0.02 * np.abs(m64)) and
-                                np.all(np.abs(s32 - s64) <= 0.02 * s64)),
-            "mean_diff_in_mc_se": (np.abs(m32 - m64) / se_mean).tolist(),
-            "sd_diff_in_mc_se": (np.abs(s32 - s64) / se_sd).tolist(),
-            "within_2_mc_se": bool(np.all(np.abs(m32 - m64) <= 2 * se_mean) and np.all(np.abs(s32 - s64) <= 2 * se_sd)),
-            "note": "the runs share random streams; once one Metropolis decision differs (FP32 and FP64 "
-                    "log-likelihoods differ by rounding) the chains decorrelate and the moments differ by Monte "
-                    "Carlo error, ~4.4 % of a posterior sd for the mean at 1024 samples",
-            "speedup_fp32_over_fp64": r32["samples_per_s"] / r64["samples_per_s"]}
+    m32s, s32s = np.array(m32s), np.array(s32s)
+    mc_se_mean = (m32s.std(0, ddof=1) if len(seeds) > 1 else np.full(3, np.nan)).tolist()
+    mc_se_sd = (s32s.std(0, ddof=1) if len(seeds) > 1 else np.full(3, np.nan)).tolist()
+    worst_bound = max(r["reweighted"]["moment_bound_rel"] for r in per_seed)
+    rw_mean = max(max(r["reweighted"]["mean_gap_rel_sd"]) for r in per_seed)
+    rw_sd = max(max(r["reweighted"]["sd_gap_rel"]) for r in per_seed)
+    secs = sum(r["fp32c"]["seconds"] for r in per_seed)
+    stages = sum(r["fp32c"]["stages"] for r in per_seed)
+    line = {"metric": METRIC, "value": B_STAGE * stages / secs, "unit": "TMCMC samples/s", "n_gpus": 1,
+            "steps": len(seeds), "warmup": 0, "ms_per_step": 1e3 * secs / len(seeds), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"whole TMCMC runs to q = 1 on the TMCMC workload (1024 samples/stage, N=128, "
+                                   f"dt=1e-4/64, {steps} steps per run, head x,y every {obs_every} steps, 5% noise), "
+                                   f"FP32 kernel against the FP64 kernel, {len(seeds)} seeds",
+                       "horizon": args.horizon},
+            "posterior_mean_fp32": m32s.mean(0).tolist(), "posterior_sd_fp32": s32s.mean(0).tolist(),
+            "mc_standard_error_of_one_run": {"mean": mc_se_mean, "sd": mc_se_sd},
+            "fp32_vs_fp64_target": {"max_abs_dloglik": max(r["reweighted"]["max_abs_dloglik"] for r in per_seed),
+                                    "moment_bound_rel": worst_bound, "reweighted_mean_gap_rel_sd": rw_mean,
+                                    "reweighted_sd_gap_rel": rw_sd,
+                                    "within_2pct": bool(rw_mean < 0.02 and rw_sd < 0.02),
+                                    "note": "the FP64 posterior's moments estimated from the FP32 samples by "
+                                            "weights exp(l64 - l32) (the Monte-Carlo error of the two estimates is "
+                                            "shared); moment_bound_rel = exp(2 max|dl|) - 1 bounds every moment "
+                                            "gap but is loose when few samples carry the largest |dl|"},
+            "per_seed": per_seed}
+    if not full:
+        line["coupled_runs"] = {
+            "same_decisions": [r["coupled"]["same_decisions"] for r in per_seed],
+            "max_mean_gap_rel": max(max(r["coupled"]["mean_gap_rel"]) for r in per_seed),
+            "max_sd_gap_rel": max(max(r["coupled"]["sd_gap_rel"]) for r in per_seed),
+            "speedup_fp32_over_fp64": (sum(B_STAGE * r["fp32c"]["stages"] for r in per_seed) / secs) /
+                                      (sum(B_STAGE * r["fp64"]["stages"] for r in per_seed) /
+                                       sum(r["fp64"]["seconds"] for r in per_seed))}
     print(json.dumps(line), flush=True)
     return 0
 
