@@ -502,6 +502,9 @@ def main():
     return 0
 
 
+FORMS_SEEDS = 8
+
+
 def forms_leg(dev, seed=700):
     """The three forms side by side on one inference problem: whole TMCMC runs to q = 1 with the
     plain FP64 kernel, the batched FP32 kernel and the FP32 kernel behind the learned surrogate
@@ -510,7 +513,9 @@ def forms_leg(dev, seed=700):
     steps (the 40 times the surrogate predicts), noise 5 % of the head's mean displacement
     (several stages).  The surrogate is trained
     on 50k forward runs of the prior sampler by the library's MLP kernels first (timed apart).
-    Samples/s count every stage's population; the posterior gaps are against the FP64 run."""
+    Samples/s count every stage's population; the posterior gaps are against the FP64 run.  The
+    two FP32 forms then run again over FORMS_SEEDS further seeds, for the surrogate's posterior
+    against the plain one in units of their Monte Carlo standard errors."""
     import numpy as np
     import torch
 
@@ -568,6 +573,30 @@ def forms_leg(dev, seed=700):
                      "accepts": [s["n_accept"] for s in log]}
         if da:
             out[form]["screened"] = int(sum(s["n_screened"] for s in log))
+            out[form]["stages_screened"] = [int(s["surrogate_used"]) for s in log]
+            out[form]["surrogate_error_nats"] = [s["surrogate_error"] for s in log]
+    # the two FP32 forms over more seeds: across-seed averages of the posterior moments with their
+    # standard errors, so that the surrogate's gap reads against the Monte Carlo error of a run
+    per = {"batched_fp32": [], "surrogate_fp32": []}
+    for k in range(FORMS_SEEDS):
+        sk = seed + 1 + k
+        th0 = torch.tensor(synthetic.prior_samples(sk, PRIOR_LO, PRIOR_HI, B_STAGE), device=dev)
+        for form, da in (("batched_fp32", False), ("surrogate_fp32", True)):
+            st = g.tmcmc_run(hs["fp32c"], th0, obs, sigma, PRIOR_LO, PRIOR_HI,
+                             lambda j, sk=sk: synthetic.stage_randoms(sk, j, B_STAGE, 3), use_surrogate=da)
+            th = st.theta.cpu().numpy()
+            per[form].append((th.mean(0), th.std(0)))
+    seeds = {"seeds": FORMS_SEEDS, "first_seed": seed + 1}
+    for form, runs in per.items():
+        mu, sd = np.array([r[0] for r in runs]), np.array([r[1] for r in runs])
+        seeds[form] = {"mean": mu.mean(0).tolist(), "mean_se": (mu.std(0, ddof=1) / np.sqrt(len(runs))).tolist(),
+                       "sd": sd.mean(0).tolist(), "sd_se": (sd.std(0, ddof=1) / np.sqrt(len(runs))).tolist()}
+    a, b = seeds["batched_fp32"], seeds["surrogate_fp32"]
+    for key in ("mean", "sd"):
+        se = np.hypot(a[key + "_se"], b[key + "_se"])
+        seeds[key + "_gap_in_se"] = ((np.array(b[key]) - np.array(a[key])) / se).tolist()
+    seeds["sd_gap_rel"] = ((np.array(b["sd"]) - np.array(a["sd"])) / np.array(a["sd"])).tolist()
+    out["surrogate_vs_plain_over_seeds"] = seeds
     for h in hs.values():
         h.close()
     m64, s64 = np.array(out["plain_fp64"]["posterior_mean"]), np.array(out["plain_fp64"]["posterior_sd"])

@@ -256,6 +256,10 @@ typedef struct tmcmc_state {
     double log_evidence;   /* host: sum of log S_j over the stages run with this state, the
                               estimate of log p(D | M) once q = 1 (Sec. 3.2, model evidence;
                               start it at 0) */
+    int surrogate_used;    /* host: 1 when the last stage screened proposals with the surrogate */
+    double surrogate_error; /* host: the plain model's judgement of the surrogate in the last stage,
+                               q_{j+1} sd(l - l~) in nats over the proposals both evaluated (NaN
+                               without one); above 1 the next stage runs plain Metropolis */
 } tmcmc_state;
 
 /* Summary record of one stage (device FP64 array of SWIMMER_STAGE_SUMMARY entries written by
@@ -263,7 +267,10 @@ typedef struct tmcmc_state {
  * is not positive definite; a failed stage leaves the population unchanged), the exponent q_j
  * it started from and q_{j+1}, log S_j, mu_j [4], b^2 Sigma_j [4][4], the number of chains
  * (distinct resampled samples), the longest chain, accepted proposals, surrogate evaluations,
- * forward-model runs executed and those on the realized chain paths. */
+ * forward-model runs executed and those on the realized chain paths; with delayed acceptance,
+ * whether this stage screened with the surrogate (1) and the plain model's judgement of the
+ * surrogate: q_{j+1} times the spread (standard deviation) of l - l~ over the proposals both
+ * evaluated, in nats (NaN without a judgement). */
 enum {
     SWIMMER_STAGE_STATUS = 0,
     SWIMMER_STAGE_Q_IN = 1,
@@ -277,6 +284,8 @@ enum {
     SWIMMER_STAGE_SCREENED = 27,
     SWIMMER_STAGE_EXACT = 28,
     SWIMMER_STAGE_EXACT_PATH = 29,
+    SWIMMER_STAGE_SURR_USED = 30,
+    SWIMMER_STAGE_SURR_ERR = 31,
     SWIMMER_STAGE_SUMMARY = 32
 };
 
@@ -304,7 +313,11 @@ int tmcmc_stage_async(swimmer_handle *h, const tmcmc_state *st, const double *un
  *             acceptance (delayed acceptance only);
  *   normals:  device [B][3] proposal normals (chain c, step s uses row off_c + s).
  *   use_surrogate: 1 = delayed acceptance through the surrogate set with
- *             swimmer_surrogate_set (requires st->surr_loglik), 0 = plain.
+ *             swimmer_surrogate_set (requires st->surr_loglik), 0 = plain.  The plain model
+ *             judges the surrogate on every proposal both evaluate: a stage screens only while
+ *             the previous one found q_{j+1} sd(l - l~) <= 1 nat (the first stage, from
+ *             q_j = 0, and a surrogate set anew are trusted); otherwise it runs plain Metropolis with row 1's uniforms, still
+ *             evaluating the surrogate so that it can be trusted again.
  * Each launch pre-fetches the forward runs of the live chains' next steps along a best-first
  * tree of pending accept decisions, so several chain steps resolve per launch with results
  * identical to the one-step-at-a-time chain.  Runs tmcmc_stage_async and synchronizes

@@ -30,7 +30,11 @@ Readings where the paper is loose (the same readings the CUDA path takes):
 Delayed acceptance (not in the paper): a cheap surrogate l~ screens each proposal first;
 step 1 accepts with min(1, exp(q (l~' - l~))), step 2 with
 min(1, exp(q (l' - l) - q (l~' - l~))), the two-stage Metropolis-Hastings rule that keeps
-the exact target for a symmetric proposal.
+the exact target for a symmetric proposal.  The plain model judges the surrogate: over the
+proposals a stage evaluates with both (at least 10, finite l), err = q_{j+1} times the
+population standard deviation of l - l~ (a constant offset cancels in the screen's ratio);
+the next stage screens only if err <= 1 nat, else it runs plain Metropolis (row 0 of the
+acceptance uniforms), still evaluating the surrogate.  A run starts trusting the surrogate.
 
 Pins (tests/test_oracle_tmcmc.py): Gaussian toy posterior mean/variance (closed form);
 the COV at the chosen q equals 1; the resample against brute-force inverse-CDF search;
@@ -46,6 +50,8 @@ import numpy as np
 FIXED_BITS = 40
 COV_TARGET = 1.0
 B_SCALE = 0.2
+SURROGATE_ERR_MAX = 1.0    # nats
+SURROGATE_MIN_JUDGED = 10
 
 
 def _weights(loglik, dq):
@@ -118,12 +124,14 @@ def in_support(theta, lo, hi):
 
 
 def metropolis(theta, loglik, idx, chol, q_next, z, u_acc, lo, hi, loglik_fn,
-               surrogate_fn=None, surr=None):
+               surrogate_fn=None, surr=None, trust=True):
     """Run the Metropolis chains of one stage.
 
     loglik_fn(thetas[m, P]) -> logliks[m] evaluates the exact model on a batch.
     With ``surrogate_fn`` (delayed acceptance) ``surr`` holds the surrogate logliks of the
-    current samples.  Returns new theta, loglik (and surrogate logliks), plus counters."""
+    current samples; ``trust`` False runs plain Metropolis while still evaluating it.  Returns
+    new theta, loglik (and surrogate logliks), counters and the values l - l~ of the proposals
+    evaluated with both."""
     B, P = theta.shape
     uniq, n_c, off = chains(idx, B)
     out_t = np.zeros_like(theta)
@@ -135,6 +143,7 @@ def metropolis(theta, loglik, idx, chol, q_next, z, u_acc, lo, hi, loglik_fn,
     n_exact = 0
     n_accept = 0
     n_pass1 = 0
+    judged = []
     for s in range(int(n_c.max())):
         act = np.nonzero(n_c > s)[0]
         pos = off[act] + s
@@ -152,6 +161,17 @@ def metropolis(theta, loglik, idx, chol, q_next, z, u_acc, lo, hi, loglik_fn,
                 sel = cand[a]
                 cur_t[sel] = cprop[a]
                 cur_l[sel] = lp[a]
+            elif not trust:  # plain Metropolis, the surrogate still evaluated and judged
+                sp = surrogate_fn(cprop)
+                lp = loglik_fn(cprop)
+                n_exact += len(cand)
+                fin = np.isfinite(lp)
+                judged.extend((lp - sp)[fin])
+                a = np.log(u_acc[0, cpos]) < q_next * (lp - cur_l[cand])
+                sel = cand[a]
+                cur_t[sel] = cprop[a]
+                cur_l[sel] = lp[a]
+                cur_s[sel] = sp[a]
             else:
                 sp = surrogate_fn(cprop)
                 a1 = np.log(u_acc[0, cpos]) < q_next * (sp - cur_s[cand])
@@ -160,6 +180,7 @@ def metropolis(theta, loglik, idx, chol, q_next, z, u_acc, lo, hi, loglik_fn,
                 if len(c2):
                     lp = loglik_fn(cprop[a1])
                     n_exact += len(c2)
+                    judged.extend((lp - sp[a1])[np.isfinite(lp)])
                     a2 = np.log(u_acc[1, cpos[a1]]) < q_next * (lp - cur_l[c2]) - q_next * (sp[a1] - cur_s[c2])
                     sel = c2[a2]
                     cur_t[sel] = cprop[a1][a2]
@@ -176,7 +197,7 @@ def metropolis(theta, loglik, idx, chol, q_next, z, u_acc, lo, hi, loglik_fn,
         if out_s is not None:
             out_s[pos] = cur_s[act]
     return dict(theta=out_t, loglik=out_l, surr=out_s, n_exact=n_exact, n_accept=n_accept,
-                n_pass1=n_pass1, unique=len(uniq), max_chain=int(n_c.max()))
+                n_pass1=n_pass1, unique=len(uniq), max_chain=int(n_c.max()), judged=np.array(judged))
 
 
 @dataclass
@@ -186,6 +207,8 @@ class StageLog:
     accept: list = field(default_factory=list)
     unique: list = field(default_factory=list)
     n_exact: list = field(default_factory=list)
+    surrogate_used: list = field(default_factory=list)
+    surrogate_error: list = field(default_factory=list)
 
 
 def run(theta0, loglik_fn, lo, hi, seed, surrogate_fn=None, max_stages=100, randoms=None):
@@ -196,14 +219,22 @@ def run(theta0, loglik_fn, lo, hi, seed, surrogate_fn=None, max_stages=100, rand
     surr = surrogate_fn(theta) if surrogate_fn is not None else None
     q = 0.0
     log = StageLog()
+    trust = True
     for j in range(max_stages):
         a = analyze(theta, loglik, q)
         u_res, u_acc, z = randoms(j)
         idx = resample(a["w"], u_res)
         m = metropolis(theta, loglik, idx, a["chol"], a["q_next"], z, u_acc, lo, hi, loglik_fn,
-                       surrogate_fn, surr)
+                       surrogate_fn, surr, trust)
         theta, loglik, surr = m["theta"], m["loglik"], m["surr"]
         q = a["q_next"]
+        if surrogate_fn is not None:
+            log.surrogate_used.append(trust)
+            d = m["judged"]
+            err = q * float(np.std(d)) if len(d) >= SURROGATE_MIN_JUDGED else float("nan")
+            log.surrogate_error.append(err)
+            if len(d) >= SURROGATE_MIN_JUDGED:
+                trust = err <= SURROGATE_ERR_MAX
         log.q.append(q)
         log.log_s.append(a["log_s"])
         log.accept.append(m["n_accept"] / B)

@@ -31,6 +31,7 @@ class TmcmcStateC(ctypes.Structure):
         ("log_s", c_double), ("mu", c_double * 4), ("sigma_prop", c_double * 16),
         ("unique", c_int), ("max_chain", c_int), ("n_exact", c_int), ("n_screened", c_int),
         ("n_accept", c_int), ("n_exact_path", c_int), ("surr_loglik", c_void_p), ("log_evidence", c_double),
+        ("surrogate_used", c_int), ("surrogate_error", c_double),
     ]
 
 

@@ -245,7 +245,7 @@ class TmcmcState:
         return dict(stage=c.stage, q=c.q, log_s=c.log_s, log_evidence=c.log_evidence, mu=list(c.mu)[:self.P],
                     unique=c.unique,
                     max_chain=c.max_chain, n_exact=c.n_exact, n_screened=c.n_screened, n_accept=c.n_accept,
-                    n_exact_path=c.n_exact_path)
+                    n_exact_path=c.n_exact_path, surrogate_used=c.surrogate_used, surrogate_error=c.surrogate_error)
 
 
 def tmcmc_tree_template(M, p_accept, depth_cap):
@@ -292,6 +292,7 @@ def tmcmc_stage(h: Handle, st: TmcmcState, uniforms, normals, use_surrogate=Fals
 STAGE_SUMMARY = 32
 STAGE_STATUS, STAGE_Q_IN, STAGE_Q, STAGE_LOG_S, STAGE_MU, STAGE_SIGMA = 0, 1, 2, 3, 4, 8
 STAGE_UNIQUE, STAGE_MAX_CHAIN, STAGE_ACCEPT, STAGE_SCREENED, STAGE_EXACT, STAGE_EXACT_PATH = 24, 25, 26, 27, 28, 29
+STAGE_SURR_USED, STAGE_SURR_ERR = 30, 31
 
 
 def tmcmc_stage_async(h: Handle, st: TmcmcState, uniforms, normals, q, summary, use_surrogate=False, stream=None,

@@ -187,6 +187,8 @@ extern "C" int swimmer_init(const swimmer_config *cfg, swimmer_handle **out) {
     ALLOC(h->tmpl, B);
     ALLOC(h->stage_q, 1);
     ALLOC(h->stage_summary, SWIMMER_STAGE_SUMMARY);
+    ALLOC(h->surr_dstat, 3);
+    ALLOC(h->surr_trust, 1);
     ALLOC(h->cum, B);
     ALLOC(h->info, 128);
     ALLOC(h->work, 2);
@@ -201,7 +203,8 @@ extern "C" int swimmer_init(const swimmer_config *cfg, swimmer_handle **out) {
         cudaError_t e2 = cudaMallocHost((void **)&h->host_pinned_d, 64 * sizeof(double));
         cudaError_t e3 = cudaStreamCreateWithFlags(&h->side_stream, cudaStreamNonBlocking);
         cudaError_t e4 = cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking);
-        if (e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess || e4 != cudaSuccess) {
+        cudaError_t e5 = cudaStreamCreateWithFlags(&h->shape_stream, cudaStreamNonBlocking);
+        if (e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess || e4 != cudaSuccess || e5 != cudaSuccess) {
             set_error("cudaMallocHost or cudaStreamCreate failed");
             swimmer_destroy(h);
             return SWIMMER_E_CUDA;
@@ -226,7 +229,8 @@ extern "C" int swimmer_destroy(swimmer_handle *h) {
                     h->idx, h->counts, h->chain_id, h->chain_off, h->chain_len, h->aux,
                     h->cur_theta, h->cur_ll, h->cur_sl, h->prop_theta, h->prop_ll, h->prop_sl,
                     h->out_theta, h->out_ll, h->out_sl, h->prop_status, h->live, h->chain_pos, h->tmpl,
-                    h->tmpl_master, h->tmpl_map, h->p_accept_dev, h->stage_q, h->stage_summary, h->cum, h->info,
+                    h->tmpl_master, h->tmpl_map, h->p_accept_dev, h->stage_q, h->stage_summary, h->surr_dstat,
+                    h->surr_trust, h->cum, h->info,
                     h->work, h->run_work,
                     h->surr_norm, h->surr_params, h->surr_x, h->surr_y, h->surr_ws, h->units};
     for (void *p : ptrs)
@@ -235,6 +239,7 @@ extern "C" int swimmer_destroy(swimmer_handle *h) {
     if (h->host_pinned_d) cudaFreeHost(h->host_pinned_d);
     if (h->side_stream) cudaStreamDestroy(h->side_stream);
     if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+    if (h->shape_stream) cudaStreamDestroy(h->shape_stream);
     if (h->prof) {
         for (cudaEvent_t e : h->prof->start) cudaEventDestroy(e);
         for (cudaEvent_t e : h->prof->stop) cudaEventDestroy(e);

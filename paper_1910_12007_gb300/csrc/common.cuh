@@ -123,7 +123,9 @@ struct swimmer_handle {
     int tmpl_slots;                       // forward runs per pre-fetch round
     double *p_accept_dev;                 // device: running Metropolis acceptance rate estimate
     double *stage_q, *stage_summary;      // device: tmcmc_stage's exponent and summary record
-    cudaStream_t side_stream, cap_stream; // capture streams of the stage graph
+    double *surr_dstat;                   // device [3]: sum, sum of squares, count of l - l~
+    int *surr_trust;                      // device: 1 while the surrogate may screen proposals
+    cudaStream_t side_stream, cap_stream, shape_stream;  // capture streams of the stage graph
     unsigned long long *cum;  // [b_max] fixed-point prefix sums
     int *info;              // [128] device counters / host-visible summary
     int *host_pinned;       // pinned host scratch (b_max + 128 ints)

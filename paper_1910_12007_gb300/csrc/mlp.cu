@@ -436,6 +436,8 @@ extern "C" int swimmer_surrogate_set(swimmer_handle *h, const float *params, con
     CUDA_TRY(cudaMemcpy(h->surr_params, params, sizeof(float) * SWIMMER_MLP_NPARAM, cudaMemcpyDeviceToDevice));
     CUDA_TRY(cudaMemcpy(h->surr_norm, out_mean, sizeof(double) * OUT, cudaMemcpyHostToDevice));
     CUDA_TRY(cudaMemcpy(h->surr_norm + OUT, out_std, sizeof(double) * OUT, cudaMemcpyHostToDevice));
+    const int trusted = 1;  // a surrogate set anew may screen until the plain model judges it
+    CUDA_TRY(cudaMemcpy(h->surr_trust, &trusted, sizeof(int), cudaMemcpyHostToDevice));
     h->surr_obs_stride = obs_stride;
     h->surr_log10_kt = log10_kt;
     h->surr_omega = omega;

@@ -100,10 +100,13 @@ __device__ double cov_of(int B, const double *__restrict__ ll, double lmax, doub
 
 __global__ void __launch_bounds__(T1) analyze_kernel(int B, int P, const double *__restrict__ theta,
                                                     const double *__restrict__ ll, const double *__restrict__ q_in,
-                                                    double *__restrict__ w_out, double *__restrict__ st) {
+                                                    double *__restrict__ w_out, double *__restrict__ st,
+                                                    int *__restrict__ trust) {
     __shared__ double red[40];
     const int tid = threadIdx.x;
     const double q = q_in[0];
+    // a run from the prior (q = 0) trusts the surrogate anew: no earlier stage has judged it
+    if (trust && tid == 0 && q == 0.0) trust[0] = 1;
     double lm = -INFINITY;
     for (int k = tid; k < B; k += T1)
         if (isfinite(ll[k])) lm = fmax(lm, ll[k]);
@@ -426,18 +429,35 @@ __global__ void __launch_bounds__(T1) live_kernel(const int *__restrict__ U_in, 
 // estimated so far, from the master orders made on the host (one per bin of that rate, nodes in
 // best-first order with children after their parents).  Best-first growth under a depth cap
 // takes, in order, the master nodes shallower than the cap, so the tree is the first
-// M = max(1, slots / A) of those, renumbered.  Writes am = {A, M, A M} for the round's kernels.
+// M = max(1, slots / A) of those, renumbered.  Writes am = {A, M, A M} for the round's kernels
+// and, inside a graph, selects the forward launch shape of A M runs (the switch node's branch of
+// their bucket of samples per SM; none when no chain is live).
 constexpr int TMPL_BINS = 32;
+struct ShapeSwitch {
+    int sms;          // SMs of the device
+    int buckets;      // buckets the table covers: those of 1 .. rows runs
+    int branch[17];   // switch branch of each bucket
+};
+__device__ void select_shape(const ShapeSwitch &sw, cudaGraphConditionalHandle h, int n) {
+    int b = sw.buckets;  // past the last branch: no forward launch
+    if (n > 0) b = min(sw.buckets - 1, (n + sw.sms - 1) / sw.sms - 1);
+    cudaGraphSetConditional(h, b < sw.buckets ? sw.branch[b] : 17);
+}
 __global__ void __launch_bounds__(T1) template_kernel(int slots, const int *__restrict__ live_info,
                                                       const double *__restrict__ p_prev,
                                                       const int4 *__restrict__ master, int *__restrict__ map,
                                                       int4 *__restrict__ tmpl, int *__restrict__ am,
-                                                      int *__restrict__ screened, int use_surrogate) {
+                                                      int *__restrict__ screened, int use_surrogate,
+                                                      ShapeSwitch sw, cudaGraphConditionalHandle sw_handle,
+                                                      int use_switch) {
     __shared__ unsigned long long sm[64];
     const int tid = threadIdx.x;
     const int A = live_info[0];
     if (A <= 0) {
-        if (tid == 0) am[0] = am[1] = am[2] = 0;
+        if (tid == 0) {
+            am[0] = am[1] = am[2] = 0;
+            if (use_switch) select_shape(sw, sw_handle, 0);
+        }
         return;
     }
     const int cap = min(live_info[1], TREE_DEPTH_MAX);
@@ -470,6 +490,7 @@ __global__ void __launch_bounds__(T1) template_kernel(int slots, const int *__re
         am[1] = M;
         am[2] = A * M;
         if (use_surrogate) screened[0] += A * M;
+        if (use_switch) select_shape(sw, sw_handle, A * M);
     }
 }
 
@@ -523,9 +544,9 @@ __global__ void tree_screen_kernel(int rows, const int *__restrict__ am, int P, 
                                    const double *__restrict__ cur_sl, const double *__restrict__ prop_sl,
                                    const double *__restrict__ st, const double *__restrict__ u1,
                                    const int4 *__restrict__ tmpl, double *__restrict__ prop,
-                                   int *__restrict__ counter) {
+                                   int *__restrict__ counter, const int *__restrict__ trust) {
     int idx = blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= rows || idx >= am[2]) return;
+    if (idx >= rows || idx >= am[2] || !trust[0]) return;  // no screen while the surrogate is not trusted
     if (isnan(prop[P * idx])) return;
     const int M = am[1];
     const int slot = idx / M, v = idx % M;
@@ -549,14 +570,17 @@ __global__ void tree_screen_kernel(int rows, const int *__restrict__ am, int P, 
 }
 
 // walk each live chain down the template along the decisions it actually takes
-__global__ void tree_resolve_kernel(const int *__restrict__ am, int P, int delayed, const int *__restrict__ live,
+__global__ void tree_resolve_kernel(const int *__restrict__ am, int P, int use_surrogate,
+                                    const int *__restrict__ trust, double *__restrict__ dstat,
+                                    const int *__restrict__ live,
                                     const int *__restrict__ chain_off, const int *__restrict__ chain_len,
                                     int *__restrict__ chain_pos, double *__restrict__ cur_theta,
                                     double *__restrict__ cur_ll, double *__restrict__ cur_sl,
                                     const double *__restrict__ prop, const double *__restrict__ prop_ll,
                                     const double *__restrict__ prop_sl, const int *__restrict__ prop_status,
-                                    const double *__restrict__ st, const double *__restrict__ u_acc,
-                                    const int4 *__restrict__ tmpl, double *__restrict__ out_theta,
+                                    const double *__restrict__ st, const double *__restrict__ u_plain,
+                                    const double *__restrict__ u_second, const int4 *__restrict__ tmpl,
+                                    double *__restrict__ out_theta,
                                     double *__restrict__ out_ll, double *__restrict__ out_sl, int *__restrict__ counter,
                                     const unsigned long long *__restrict__ run_work,
                                     unsigned long long *__restrict__ useful) {
@@ -566,8 +590,11 @@ __global__ void tree_resolve_kernel(const int *__restrict__ am, int P, int delay
     const int c = live[slot];
     const double qn = st[S_QN];
     const int len = chain_len[c];
+    const bool delayed = use_surrogate && trust[0];
+    const double *u_acc = delayed ? u_second : u_plain;  // the second step's row, or plain Metropolis
     int p = chain_pos[c];
     int v = 0, acc = 0, ran = 0;
+    double d1 = 0.0, d2 = 0.0, dn = 0.0;  // the plain model's judgement of the surrogate
     unsigned long long work = 0;
     while (v >= 0 && p < len) {
         const int idx = slot * M + v;
@@ -576,13 +603,19 @@ __global__ void tree_resolve_kernel(const int *__restrict__ am, int P, int delay
         ran += run;
         if (run) work += run_work[idx];
         const bool valid = run && prop_status[idx] == SWIMMER_OK;
+        if (use_surrogate && valid) {
+            const double d = prop_ll[idx] - prop_sl[idx];
+            d1 += d;
+            d2 += d * d;
+            dn += 1.0;
+        }
         double thr = qn * (prop_ll[idx] - cur_ll[c]);
         if (delayed) thr -= qn * (prop_sl[idx] - cur_sl[c]);
         const bool accept = valid && log(u_acc[pos]) < thr;
         if (accept) {
             for (int q = 0; q < P; ++q) cur_theta[P * c + q] = prop[P * idx + q];
             cur_ll[c] = prop_ll[idx];
-            if (delayed) cur_sl[c] = prop_sl[idx];
+            if (use_surrogate) cur_sl[c] = prop_sl[idx];
             ++acc;
         }
         for (int q = 0; q < P; ++q) out_theta[P * pos + q] = cur_theta[P * c + q];
@@ -595,6 +628,11 @@ __global__ void tree_resolve_kernel(const int *__restrict__ am, int P, int delay
     if (acc) atomicAdd(counter, acc);
     if (ran) atomicAdd(counter + 3, ran);
     if (work) atomicAdd(useful, work);
+    if (dn > 0.0) {
+        atomicAdd(dstat, d1);
+        atomicAdd(dstat + 1, d2);
+        atomicAdd(dstat + 2, dn);
+    }
 }
 
 // Best-first decision tree of M nodes (host): the root, then repeatedly the candidate child
@@ -661,7 +699,8 @@ extern "C" int tmcmc_analyze(swimmer_handle *h, int B, const double *theta, cons
     ARG_CHECK(theta && loglik && out_w && stats, "NULL device pointer");
     ARG_CHECK(q >= 0.0 && q < 1.0, "q must be in [0, 1)");
     set_double_kernel<<<1, 1, 0, (cudaStream_t)stream>>>(h->stage_q, q);
-    analyze_kernel<<<1, T1, 0, (cudaStream_t)stream>>>(B, n_params(h->cfg), theta, loglik, h->stage_q, out_w, stats);
+    analyze_kernel<<<1, T1, 0, (cudaStream_t)stream>>>(B, n_params(h->cfg), theta, loglik, h->stage_q, out_w, stats,
+                                                       nullptr);
     CUDA_TRY(cudaGetLastError());
     return 0;
 }
@@ -685,6 +724,8 @@ namespace {
 // accepted and decided so far; [16..18] the round's A, M, A M.
 // ---------------------------------------------------------------------------------
 constexpr int CNT = 64, LIVE = CNT + 8, AM = CNT + 16;
+constexpr double SURR_ERR_MAX = 1.0;    // nats: spread of l - l~ allowed for screening
+constexpr double SURR_MIN_JUDGED = 10;  // proposals both models evaluated, for a judgement
 
 // The chains' outputs become the population (when the analysis succeeded); the annealing
 // exponent and the acceptance estimate advance; the stage summary (SWIMMER_STAGE_* layout) is
@@ -694,7 +735,8 @@ __global__ void finalize_kernel(int B, int P, int use_surrogate, const double *_
                                 const double *__restrict__ out_ll, const double *__restrict__ out_sl,
                                 double *__restrict__ theta, double *__restrict__ ll, double *__restrict__ sl,
                                 int *__restrict__ status, double *__restrict__ q_io, double *__restrict__ p_accept,
-                                double *__restrict__ summary) {
+                                double *__restrict__ summary, const double *__restrict__ dstat,
+                                int *__restrict__ trust) {
     const bool ok = st[S_STATUS] == 0.0;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < B; i += gridDim.x * blockDim.x) {
         if (ok) {
@@ -716,11 +758,25 @@ __global__ void finalize_kernel(int B, int P, int use_surrogate, const double *_
         summary[SWIMMER_STAGE_MAX_CHAIN] = info[1];
         summary[SWIMMER_STAGE_ACCEPT] = cnt[0];
         summary[SWIMMER_STAGE_SCREENED] = cnt[4];
-        summary[SWIMMER_STAGE_EXACT] = use_surrogate ? cnt[1] : cnt[2];
+        const bool screened = use_surrogate && trust[0];
+        summary[SWIMMER_STAGE_EXACT] = screened ? cnt[1] : cnt[2];
         summary[SWIMMER_STAGE_EXACT_PATH] = cnt[3];
+        summary[SWIMMER_STAGE_SURR_USED] = screened ? 1.0 : 0.0;
+        summary[SWIMMER_STAGE_SURR_ERR] = nan("");
         if (ok) {
             q_io[0] = st[S_QN];
             p_accept[0] = 0.5 * p_accept[0] + 0.5 * (double)cnt[0] / (double)B;
+        }
+        // delayed acceptance (not in the paper): the plain model judges the surrogate on the
+        // proposals both evaluated.  A constant offset of l - l~ cancels in the screen's ratio;
+        // its spread, in nats at this stage's exponent, must stay within SURR_ERR_MAX for the
+        // next stage to screen, else that stage runs plain Metropolis (the surrogate is still
+        // evaluated, so it can be trusted again)
+        if (use_surrogate && ok && dstat[2] >= SURR_MIN_JUDGED) {
+            const double m = dstat[0] / dstat[2];
+            const double err = st[S_QN] * sqrt(fmax(dstat[1] / dstat[2] - m * m, 0.0));
+            summary[SWIMMER_STAGE_SURR_ERR] = err;
+            trust[0] = err <= SURR_ERR_MAX ? 1 : 0;
         }
     }
 }
@@ -737,7 +793,7 @@ struct StageArgs {
 // analysis, resampling, chains; counters and the outputs of other ranks' rows cleared
 int enqueue_prefix(swimmer_handle *h, const StageArgs &a, cudaStream_t s) {
     const tmcmc_state *st = a.st;
-    analyze_kernel<<<1, T1, 0, s>>>(a.B, a.P, st->theta, st->loglik, a.q_dev, h->w, h->stats);
+    analyze_kernel<<<1, T1, 0, s>>>(a.B, a.P, st->theta, st->loglik, a.q_dev, h->w, h->stats, h->surr_trust);
     CUDA_TRY(cudaGetLastError());
     resample_kernel<<<1, T1, 0, s>>>(a.B, h->w, a.uniforms, (unsigned long long *)h->cum, h->idx, h->counts);
     CUDA_TRY(cudaGetLastError());
@@ -748,6 +804,7 @@ int enqueue_prefix(swimmer_handle *h, const StageArgs &a, cudaStream_t s) {
     CUDA_TRY(cudaGetLastError());
     prof_count(h, 3);
     CUDA_TRY(cudaMemsetAsync(h->info + CNT, 0, 8 * sizeof(int), s));
+    CUDA_TRY(cudaMemsetAsync(h->surr_dstat, 0, 3 * sizeof(double), s));
     CUDA_TRY(cudaMemsetAsync(h->chain_pos, 0, sizeof(int) * a.B, s));
     if (a.world > 1) {  // rows of other ranks' chains stay zero, so a SUM over ranks assembles them
         CUDA_TRY(cudaMemsetAsync(h->out_theta, 0, a.P * sizeof(double) * a.B, s));
@@ -762,23 +819,63 @@ int enqueue_prefix(swimmer_handle *h, const StageArgs &a, cudaStream_t s) {
 // choice in simulations of the stage with measured launch costs.
 int stage_slots(const swimmer_handle *h) { return min(h->cfg.b_max, forward_slots(h, h->cfg.precision)); }
 
+// Launch shape of a round of forward runs in bucket b of samples per SM: the autotuned shape
+// of that bucket, else the heuristic's at the bucket's largest batch (at most the round's rows).
+// Both the graph's switch node and the host-driven rounds take it, so they run alike.
+int round_shape(const swimmer_handle *h, int b, int rows) {
+    return forward_threads(h, min(rows, (b + 1) * h->num_sms), h->cfg.precision);
+}
+
+// The distinct round shapes over the buckets of 1 .. rows runs, and the branch of each bucket.
+ShapeSwitch round_shapes(const swimmer_handle *h, int rows, std::vector<int> &shapes) {
+    ShapeSwitch sw = {};
+    sw.sms = h->num_sms;
+    sw.buckets = tune_bucket(h, rows) + 1;
+    shapes.clear();
+    for (int b = 0; b < sw.buckets; ++b) {
+        const int t = round_shape(h, b, rows);
+        int k = 0;
+        while (k < (int)shapes.size() && shapes[k] != t) ++k;
+        if (k == (int)shapes.size()) shapes.push_back(t);
+        sw.branch[b] = k;
+    }
+    return sw;
+}
+
 // one pre-fetch round: live chains (and the loop condition), the tree, candidates, the
 // surrogate screen, the forward runs, the walk down the trees.  Every size comes from device
-// memory; the launches cover the round's capacity and idle past the round's rows.
-int enqueue_round(swimmer_handle *h, const StageArgs &a, cudaStream_t s, cudaGraphConditionalHandle cond,
-                  int use_cond) {
+// memory; the launches cover the round's capacity and idle past the round's rows.  Inside a
+// graph (body != nullptr: the while node's body) the forward launch is a switch node with one
+// branch per launch shape, set by the template kernel from the round's A M.  Driven from the
+// host, the round reads A M back (its one synchronization) and stops when no chain is live.
+int enqueue_round(swimmer_handle *h, const StageArgs &a, cudaStream_t s, cudaGraph_t body,
+                  cudaGraphConditionalHandle cond, bool *done) {
     const tmcmc_state *st = a.st;
     const int slots = h->tmpl_slots;
     // a round runs A M <= max(slots, B) forward models (M = 1 once the live chains outnumber
-    // the slots); the launches cover that many rows, the forward launch takes the shape of a
-    // full round of `slots`
+    // the slots); the launches cover that many rows
     const int rows = max(slots, a.B);
+    std::vector<int> shapes;
+    const ShapeSwitch sw = round_shapes(h, rows, shapes);
+    cudaGraphConditionalHandle sw_handle = 0;
+    if (body) CUDA_TRY(cudaGraphConditionalHandleCreate(&sw_handle, body, 0, cudaGraphCondAssignDefault));
     live_kernel<<<1, T1, 0, s>>>(h->info, a.B, a.rank, a.world, h->chain_id, h->chain_off, h->chain_len, h->chain_pos,
-                                 h->live, h->info + CNT, h->info + LIVE, cond, use_cond);
+                                 h->live, h->info + CNT, h->info + LIVE, cond, body != nullptr);
     CUDA_TRY(cudaGetLastError());
     template_kernel<<<1, T1, 0, s>>>(slots, h->info + LIVE, h->p_accept_dev, h->tmpl_master, h->tmpl_map, h->tmpl,
-                                     h->info + AM, h->info + CNT + 4, a.use_surrogate);
+                                     h->info + AM, h->info + CNT + 4, a.use_surrogate, sw, sw_handle,
+                                     body != nullptr);
     CUDA_TRY(cudaGetLastError());
+    int shape = 0;
+    if (!body) {
+        CUDA_TRY(cudaMemcpyAsync(h->host_pinned, h->info + AM, 3 * sizeof(int), cudaMemcpyDeviceToHost, s));
+        CUDA_TRY(cudaStreamSynchronize(s));
+        if (h->host_pinned[0] <= 0) {
+            *done = true;
+            return 0;
+        }
+        shape = round_shape(h, tune_bucket(h, h->host_pinned[2]), rows);
+    }
     const int grid = (rows + 127) / 128;
     tree_propose_kernel<<<grid, 128, 0, s>>>(rows, h->info + AM, h->live, h->chain_off, h->chain_len, h->chain_pos,
                                              h->cur_theta, h->stats, a.normals, a.box, h->tmpl, h->prop_theta,
@@ -790,17 +887,48 @@ int enqueue_round(swimmer_handle *h, const StageArgs &a, cudaStream_t s, cudaGra
         if (rc) return rc;
         tree_screen_kernel<<<grid, 128, 0, s>>>(rows, h->info + AM, a.P, h->live, h->chain_off, h->chain_pos,
                                                 h->cur_sl, h->prop_sl, h->stats, a.uniforms + a.B, h->tmpl,
-                                                h->prop_theta, h->info + CNT + 1);
+                                                h->prop_theta, h->info + CNT + 1, h->surr_trust);
         CUDA_TRY(cudaGetLastError());
         prof_count(h, 1);
     }
-    int rc = run_forward(h, rows, h->prop_theta, nullptr, st->obs, st->sigma, h->prop_ll, nullptr, nullptr,
-                         h->prop_status, s, 1, nullptr, forward_threads(h, slots, h->cfg.precision));
+    int rc = launch_prepare(h, rows, h->prop_theta, nullptr, s);
+    if (!rc) rc = launch_table_build(h, rows, h->cfg.precision == SWIMMER_FP64, s);
     if (rc) return rc;
-    tree_resolve_kernel<<<grid, 128, 0, s>>>(h->info + AM, a.P, a.use_surrogate, h->live, h->chain_off, h->chain_len,
+    if (body) {
+        cudaStreamCaptureStatus cs;
+        cudaGraph_t g;
+        const cudaGraphNode_t *deps = nullptr;
+        const cudaGraphEdgeData *edges = nullptr;
+        size_t nd = 0;
+        CUDA_TRY(cudaStreamGetCaptureInfo(s, &cs, nullptr, &g, &deps, &edges, &nd));
+        cudaGraphNodeParams cp = {};
+        cp.type = cudaGraphNodeTypeConditional;
+        cp.conditional.handle = sw_handle;
+        cp.conditional.type = cudaGraphCondTypeSwitch;
+        cp.conditional.size = (unsigned)shapes.size();
+        cudaGraphNode_t node;
+        CUDA_TRY(cudaGraphAddNode(&node, g, deps, edges, nd, &cp));
+        for (size_t k = 0; k < shapes.size(); ++k) {
+            CUDA_TRY(cudaStreamBeginCaptureToGraph(h->shape_stream, cp.conditional.phGraph_out[k], nullptr, nullptr,
+                                                   0, cudaStreamCaptureModeRelaxed));
+            rc = launch_forward(h, rows, st->obs, st->sigma, h->prop_ll, nullptr, nullptr, h->prop_status,
+                                h->cfg.precision, h->shape_stream, shapes[k], 1, nullptr);
+            cudaGraph_t captured = nullptr;
+            cudaError_t e = cudaStreamEndCapture(h->shape_stream, &captured);
+            if (rc) return rc;
+            CUDA_TRY(e);
+        }
+        CUDA_TRY(cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+    } else {
+        rc = launch_forward(h, rows, st->obs, st->sigma, h->prop_ll, nullptr, nullptr, h->prop_status,
+                            h->cfg.precision, s, shape, 1, nullptr);
+        if (rc) return rc;
+    }
+    tree_resolve_kernel<<<grid, 128, 0, s>>>(h->info + AM, a.P, a.use_surrogate, h->surr_trust, h->surr_dstat,
+                                             h->live, h->chain_off, h->chain_len,
                                              h->chain_pos, h->cur_theta, h->cur_ll, h->cur_sl, h->prop_theta,
                                              h->prop_ll, h->prop_sl, h->prop_status, h->stats,
-                                             a.uniforms + (a.use_surrogate ? 2 * a.B : a.B), h->tmpl, h->out_theta,
+                                             a.uniforms + a.B, a.uniforms + 2 * a.B, h->tmpl, h->out_theta,
                                              h->out_ll, h->out_sl, h->info + CNT, h->run_work, h->work + 1);
     CUDA_TRY(cudaGetLastError());
     prof_count(h, 1);
@@ -811,7 +939,8 @@ int enqueue_finalize(swimmer_handle *h, const StageArgs &a, cudaStream_t s) {
     const tmcmc_state *st = a.st;
     finalize_kernel<<<(a.B + 255) / 256, 256, 0, s>>>(a.B, a.P, a.use_surrogate, h->stats, h->info, h->out_theta,
                                                        h->out_ll, h->out_sl, st->theta, st->loglik, st->surr_loglik,
-                                                       st->status, a.q_dev, h->p_accept_dev, a.summary);
+                                                       st->status, a.q_dev, h->p_accept_dev, a.summary, h->surr_dstat,
+                                                       h->surr_trust);
     CUDA_TRY(cudaGetLastError());
     prof_count(h, 1);
     return 0;
@@ -841,7 +970,8 @@ int enqueue_rounds_in_capture(swimmer_handle *h, const StageArgs &a, cudaStream_
     CUDA_TRY(cudaGraphAddNode(&node, g, deps, edges, nd, &cp));
     cudaGraph_t body = cp.conditional.phGraph_out[0];
     CUDA_TRY(cudaStreamBeginCaptureToGraph(h->side_stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
-    int rc = enqueue_round(h, a, h->side_stream, cond, 1);
+    bool done = false;
+    int rc = enqueue_round(h, a, h->side_stream, body, cond, &done);
     cudaGraph_t captured = nullptr;
     cudaError_t e = cudaStreamEndCapture(h->side_stream, &captured);
     if (rc) return rc;
@@ -855,13 +985,7 @@ int stage_enqueue(swimmer_handle *h, const StageArgs &a, cudaStream_t s) {
         // profiling: rounds driven from the host (event records per forward launch cannot sit
         // inside a graph's while node); the same kernels, one host synchronization per round
         int rc = enqueue_prefix(h, a, s);
-        for (int round = 0; !rc; ++round) {
-            rc = enqueue_round(h, a, s, 0, 0);
-            if (rc) break;
-            CUDA_TRY(cudaMemcpyAsync(h->host_pinned, h->info + LIVE, sizeof(int), cudaMemcpyDeviceToHost, s));
-            CUDA_TRY(cudaStreamSynchronize(s));
-            if (h->host_pinned[0] <= 0) break;
-        }
+        for (bool done = false; !rc && !done;) rc = enqueue_round(h, a, s, nullptr, 0, &done);
         return rc ? rc : enqueue_finalize(h, a, s);
     }
     cudaStreamCaptureStatus cs;
@@ -993,5 +1117,7 @@ extern "C" int tmcmc_stage_shard(swimmer_handle *h, tmcmc_state *st, const doubl
     st->n_screened = (int)hs[SWIMMER_STAGE_SCREENED];
     st->n_exact = (int)hs[SWIMMER_STAGE_EXACT];
     st->n_exact_path = (int)hs[SWIMMER_STAGE_EXACT_PATH];
+    st->surrogate_used = (int)hs[SWIMMER_STAGE_SURR_USED];
+    st->surrogate_error = hs[SWIMMER_STAGE_SURR_ERR];
     return 0;
 }

@@ -96,6 +96,41 @@ def test_delayed_acceptance_matches_plain_and_saves_forward_runs(trained):
     assert acc_da > acc_plain, (acc_da, acc_plain)
 
 
+def test_a_run_from_the_prior_trusts_the_surrogate_anew(trained):
+    """The plain model's judgement is state of the handle that carries over from stage to
+    stage; a second run on the same handle starts from the prior and must not inherit the end
+    of the first.  The trained surrogate's predictions are shifted by ten noise levels, which
+    moves its log-likelihood by amounts that vary with theta by far more than 1 nat, so the
+    first run ends with the surrogate distrusted."""
+    import dataclasses
+
+    sur, _ = trained
+    B, seed = 256, 12
+    h = g.swimmer_init(_cfg(B))
+    truth_traj, _, _ = g.forward_batch(h, torch.tensor([TRUTH], dtype=torch.float64, device=DEV))
+    xi = truth_traj[0].cpu().numpy()
+    sigma = 0.01 * float(np.mean(np.abs(xi)))
+    obs = torch.tensor(xi + sigma * synthetic.normals(1234, synthetic.NOISE, 0, xi.size).reshape(xi.shape),
+                       device=DEV)
+    dataclasses.replace(sur, out_mean=sur.out_mean + 10.0 * sigma).attach(h)
+    th0 = torch.tensor(synthetic.prior_samples(seed, LO, HI, B), device=DEV)
+    logs, thetas = [], []
+    for _ in range(2):
+        log = []
+        st = g.tmcmc_run(h, th0, obs, sigma, LO, HI, lambda j: synthetic.stage_randoms(seed, j, B, 3),
+                         use_surrogate=True, log=log)
+        thetas.append(st.theta.cpu().numpy())
+        logs.append(log)
+    h.close()
+    used = [s["surrogate_used"] for s in logs[0]]
+    assert used[0] == 1 and not used[-1], used
+    # the judged error sums over proposals in atomic order: equal to rounding
+    err = [[s.pop("surrogate_error") for s in log] for log in logs]
+    assert np.allclose(err[0], err[1], rtol=1e-9, equal_nan=True)
+    assert logs[0] == logs[1]
+    assert np.array_equal(thetas[0], thetas[1])
+
+
 def test_delayed_acceptance_fp64_matches_oracle_sample_by_sample():
     """The two-stage Metropolis-Hastings chains of delayed acceptance (stage 1 on the
     surrogate, stage 2 on the exact model; Sec. 3.2, Algorithm 1 otherwise) on the FP64
@@ -155,6 +190,13 @@ def test_delayed_acceptance_fp64_matches_oracle_sample_by_sample():
     assert [s["unique"] for s in log_g] == log_o.unique
     # exact forward runs the one-step chains make, and accepted moves, stage by stage
     assert [s["n_exact_path"] for s in log_g] == log_o.n_exact
+    # the plain model's judgement of the surrogate, and the screening it allows, stage by stage
+    assert [bool(s["surrogate_used"]) for s in log_g] == log_o.surrogate_used
+    err_g = np.array([s["surrogate_error"] for s in log_g])
+    # the judged error is a standard deviation of l - l~ over the stage's proposals; the GPU's
+    # l~ is FP32 MLP arithmetic on values of a few hundred nats (rounding near 1e-5 nats), and a
+    # standard deviation moves by at most the largest change of its terms
+    assert np.allclose(err_g, log_o.surrogate_error, rtol=0, atol=1e-4, equal_nan=True)
     assert [s["n_accept"] / B for s in log_g] == pytest.approx(log_o.accept, abs=0)
     assert np.allclose(th_g, th_o, rtol=1e-8, atol=1e-10)
     assert np.allclose(ll_g, ll_o, rtol=1e-8, atol=1e-8)

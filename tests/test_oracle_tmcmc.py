@@ -256,3 +256,27 @@ def test_bf16_operand_mode_reduces_to_the_plain_network(monkeypatch):
     # with the real rounding the outputs move, by about the BF16 spacing
     y2 = om.forward(P, x, bf16_operands=True)
     assert 0 < np.max(np.abs(y2 - y1)) < 0.05 * np.max(np.abs(y1))
+
+
+def test_plain_model_judges_the_surrogate():
+    """The fallback rule of delayed acceptance: a surrogate that differs from the exact
+    log-likelihood by a constant (the offset cancels in the screen's ratio) keeps screening at
+    every stage; one whose error spreads over many nats is dropped as soon as a stage judges it
+    above 1 nat at that stage's exponent, the stages after it run plain Metropolis, and the
+    posterior is still the exact one (closed form)."""
+    mean = np.array([0.3, 0.1])
+    sd = np.array([0.2, 0.4])
+    lo, hi = np.full(2, -5.0), np.full(2, 5.0)
+    B = 2048
+    exact = _toy(mean, sd)
+    rnd = lambda j: synthetic.stage_randoms(6, j, B, 2)
+    th0 = synthetic.prior_samples(6, lo, hi, B)
+    _, _, good = tm.run(th0, exact, lo, hi, 6, surrogate_fn=lambda th: exact(th) - 3.0, randoms=rnd)
+    assert all(good.surrogate_used) and max(good.surrogate_error) < 1e-9
+    noisy = lambda th: exact(th) + 40.0 * np.sin(37.0 * np.atleast_2d(th)[:, 0])
+    theta, _, bad = tm.run(th0, exact, lo, hi, 6, surrogate_fn=noisy, randoms=rnd)
+    used, err = bad.surrogate_used, bad.surrogate_error
+    assert used[0] and not all(used)
+    assert all(used[j] == (err[j - 1] <= 1.0) for j in range(1, len(used)))
+    assert np.all(np.abs(theta.mean(0) - mean) < 0.3 * sd)
+    assert np.all(np.abs(theta.std(0) / sd - 1) < 0.12)
