@@ -247,6 +247,9 @@ def main():
     ap.add_argument("--profile-case", action="store_true",
                     help="run one forward batch of the workload (1024 samples, 200 steps; with --workload large: "
                          "256 samples x N=1024, 50 steps) twice, for ncu, and exit")
+    ap.add_argument("--batch", type=int, default=0,
+                    help="--profile-case (TMCMC workload): samples in the launch (default 1024; 152 puts one on "
+                         "each SM, as in a stage's last pre-fetch round)")
     ap.add_argument("--shape", default=None,
                     help="--profile-case launch shape: threads per sample, suffix w (q) for two- (four-) target "
                          "pair units (e.g. 128w); default: the untuned heuristic")
@@ -311,16 +314,18 @@ def main():
         h = g.swimmer_init(cfg)
         if args.shape:
             g.swimmer_tuning(h, prec, [shape_arg(g, args.shape)] * 17)
-        th = torch.tensor(synthetic.prior_samples(5, PRIOR_LO, (10.0, 0.2, 0.2), B_STAGE), device=dev)
+        nb = args.batch if args.batch > 0 else B_STAGE
+        th = torch.tensor(synthetic.prior_samples(5, PRIOR_LO, (10.0, 0.2, 0.2), nb), device=dev)
         for rep in range(2):
             g.swimmer_profile(h, 1)
             g.forward_batch(h, th, want_traj=False)
             k2_ms, _, _, pairs, _ = g.swimmer_profile(h, 2)
         g.swimmer_profile(h, 0)
         torch.cuda.synchronize()
-        print(json.dumps({"profile_case": f"{B_STAGE} samples x N={N_PTS} x {cfg.steps} steps",
+        print(json.dumps({"profile_case": f"{nb} samples x N={N_PTS} x {cfg.steps} steps",
                           "shape": args.shape or "heuristic",
-                          "k2_ms": k2_ms, "pair_evals_per_s": pairs / (k2_ms * 1e-3),
+                          "k2_ms": k2_ms, "us_per_step": 1e3 * k2_ms / cfg.steps,
+                          "pair_evals_per_s": pairs / (k2_ms * 1e-3),
                           "tflops": pair_sum_flops(pairs, (N_PTS - 1) / (2.0 * N_PTS)) / (k2_ms * 1e-3) / 1e12}))
         h.close()
         return 0
@@ -799,7 +804,8 @@ def shapes_workload(args, rank, local_rank):
         B = 1 if per == 0 else min(per * sms, B_STAGE)
         th = torch.tensor(synthetic.prior_samples(77, lo, hi, B), device=dev)
         row = {}
-        for T in (128, 256, 512, 1024, 128 | g.SHAPE_WIDE, 256 | g.SHAPE_WIDE, 512 | g.SHAPE_WIDE, 512 | g.SHAPE_QUAD):
+        for T in (128, 256, 512, 1024, 128 | g.SHAPE_WIDE, 256 | g.SHAPE_WIDE, 512 | g.SHAPE_WIDE, 128 | g.SHAPE_QUAD,
+                  256 | g.SHAPE_QUAD, 512 | g.SHAPE_QUAD):
             try:
                 g.swimmer_tuning(h, g.FP32C, [T] * 17)
             except RuntimeError:

@@ -31,7 +31,7 @@ void prof_k2_begin(swimmer_handle *h, cudaStream_t s, int samples) {
         p->stop.push_back(b);
         p->samples.push_back(0);
     }
-    p->samples[p->used] = samples;
+    p->samples[p->used] = h->prof_rows > 0 ? h->prof_rows : samples;
     cudaEventRecord(p->start[p->used], s);
 }
 

@@ -92,6 +92,7 @@ struct swimmer_handle {
     int profile;
     long long n_launch;
     ProfileEvents *prof;
+    int prof_rows;          // rows a speculative launch actually runs (profiling record), 0 = all
     unsigned long long *work;  // device counters: [0] pair evaluations executed by the forward
                                // kernel, [1] those a one-step-at-a-time TMCMC would also run
     unsigned long long *run_work;  // [b_max] pair evaluations of each run of the last launch
@@ -172,7 +173,8 @@ int launch_prepare(swimmer_handle *h, int B, const double *theta, const int *n_p
 int launch_table_build(swimmer_handle *h, int B, int need64, cudaStream_t s);
 int launch_forward(swimmer_handle *h, int B, const double *obs, double sigma, double *loglik,
                    double *head_traj, double *mean_speed, int *status, int precision,
-                   cudaStream_t s, int threads_override = 0, int speculative = 0, double *final_state = nullptr);
+                   cudaStream_t s, int threads_override = 0, int speculative = 0, double *final_state = nullptr,
+                   int max_runs = 0);
 int forward_threads(const swimmer_handle *h, int B, int precision);
 int tune_bucket(const swimmer_handle *h, int B);
 int forward_min_threads(const swimmer_handle *h, int precision);

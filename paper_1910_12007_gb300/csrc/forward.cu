@@ -1327,7 +1327,7 @@ int forward_threads(const swimmer_handle *h, int B, int precision) {
 
 int launch_forward(swimmer_handle *h, int B, const double *obs, double sigma, double *loglik,
                    double *head_traj, double *mean_speed, int *status, int precision, cudaStream_t s,
-                   int threads_override, int speculative, double *final_state) {
+                   int threads_override, int speculative, double *final_state, int max_runs) {
     FwdArgs a;
     a.B = B;
     a.sp = h->sp;
@@ -1377,6 +1377,12 @@ int launch_forward(swimmer_handle *h, int B, const double *obs, double sigma, do
                                   cudaSharedmemCarveoutMaxShared));
     int per_sm = 0;
     CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, T, smem));
+    // CTAs per SM: no more than the launch has runs per SM.  A speculative launch over B rows of
+    // which at most max_runs are real (the others skip as bad samples, queued last) counts
+    // those: the real runs, queued first, are then taken one per CTA as the CTAs start, spread
+    // over the SMs, instead of landing two or three on some SMs
+    const int runs = max_runs > 0 && max_runs < B ? max_runs : B;
+    if (per_sm > 1) per_sm = min(per_sm, (runs + h->num_sms - 1) / h->num_sms);
     // FP32 with shared memory for so few threads per SM that each could hold 128 registers:
     // the instantiation compiled for that register budget (same CTAs per SM)
     if (!f64 && T <= 512 && per_sm >= 1 && (long long)per_sm * T * 128 <= h->regs_per_sm) {

@@ -434,14 +434,12 @@ __global__ void __launch_bounds__(T1) live_kernel(const int *__restrict__ U_in, 
 // their bucket of samples per SM; none when no chain is live).
 constexpr int TMPL_BINS = 32;
 struct ShapeSwitch {
-    int sms;          // SMs of the device
-    int buckets;      // buckets the table covers: those of 1 .. rows runs
-    int branch[17];   // switch branch of each bucket
+    int sms;      // SMs of the device
+    int buckets;  // branches: buckets of 1 .. rows runs by runs per SM, ceil(n / SMs) - 1
 };
 __device__ void select_shape(const ShapeSwitch &sw, cudaGraphConditionalHandle h, int n) {
-    int b = sw.buckets;  // past the last branch: no forward launch
-    if (n > 0) b = min(sw.buckets - 1, (n + sw.sms - 1) / sw.sms - 1);
-    cudaGraphSetConditional(h, b < sw.buckets ? sw.branch[b] : 17);
+    // n = 0: past the last branch, so no forward launch runs
+    cudaGraphSetConditional(h, n > 0 ? min(sw.buckets - 1, (n + sw.sms - 1) / sw.sms - 1) : sw.buckets);
 }
 __global__ void __launch_bounds__(T1) template_kernel(int slots, const int *__restrict__ live_info,
                                                       const double *__restrict__ p_prev,
@@ -826,21 +824,9 @@ int round_shape(const swimmer_handle *h, int b, int rows) {
     return forward_threads(h, min(rows, (b + 1) * h->num_sms), h->cfg.precision);
 }
 
-// The distinct round shapes over the buckets of 1 .. rows runs, and the branch of each bucket.
-ShapeSwitch round_shapes(const swimmer_handle *h, int rows, std::vector<int> &shapes) {
-    ShapeSwitch sw = {};
-    sw.sms = h->num_sms;
-    sw.buckets = tune_bucket(h, rows) + 1;
-    shapes.clear();
-    for (int b = 0; b < sw.buckets; ++b) {
-        const int t = round_shape(h, b, rows);
-        int k = 0;
-        while (k < (int)shapes.size() && shapes[k] != t) ++k;
-        if (k == (int)shapes.size()) shapes.push_back(t);
-        sw.branch[b] = k;
-    }
-    return sw;
-}
+// The switch over the buckets of 1 .. rows runs: one branch per bucket (its launch shape, and
+// as many CTAs per SM as the bucket has runs per SM).
+ShapeSwitch round_shapes(const swimmer_handle *h, int rows) { return ShapeSwitch{h->num_sms, tune_bucket(h, rows) + 1}; }
 
 // one pre-fetch round: live chains (and the loop condition), the tree, candidates, the
 // surrogate screen, the forward runs, the walk down the trees.  Every size comes from device
@@ -855,8 +841,7 @@ int enqueue_round(swimmer_handle *h, const StageArgs &a, cudaStream_t s, cudaGra
     // a round runs A M <= max(slots, B) forward models (M = 1 once the live chains outnumber
     // the slots); the launches cover that many rows
     const int rows = max(slots, a.B);
-    std::vector<int> shapes;
-    const ShapeSwitch sw = round_shapes(h, rows, shapes);
+    const ShapeSwitch sw = round_shapes(h, rows);
     cudaGraphConditionalHandle sw_handle = 0;
     if (body) CUDA_TRY(cudaGraphConditionalHandleCreate(&sw_handle, body, 0, cudaGraphCondAssignDefault));
     live_kernel<<<1, T1, 0, s>>>(h->info, a.B, a.rank, a.world, h->chain_id, h->chain_off, h->chain_len, h->chain_pos,
@@ -866,7 +851,7 @@ int enqueue_round(swimmer_handle *h, const StageArgs &a, cudaStream_t s, cudaGra
                                      h->info + AM, h->info + CNT + 4, a.use_surrogate, sw, sw_handle,
                                      body != nullptr);
     CUDA_TRY(cudaGetLastError());
-    int shape = 0;
+    int bucket = 0;
     if (!body) {
         CUDA_TRY(cudaMemcpyAsync(h->host_pinned, h->info + AM, 3 * sizeof(int), cudaMemcpyDeviceToHost, s));
         CUDA_TRY(cudaStreamSynchronize(s));
@@ -874,7 +859,7 @@ int enqueue_round(swimmer_handle *h, const StageArgs &a, cudaStream_t s, cudaGra
             *done = true;
             return 0;
         }
-        shape = round_shape(h, tune_bucket(h, h->host_pinned[2]), rows);
+        bucket = tune_bucket(h, h->host_pinned[2]);
     }
     const int grid = (rows + 127) / 128;
     tree_propose_kernel<<<grid, 128, 0, s>>>(rows, h->info + AM, h->live, h->chain_off, h->chain_len, h->chain_pos,
@@ -905,14 +890,15 @@ int enqueue_round(swimmer_handle *h, const StageArgs &a, cudaStream_t s, cudaGra
         cp.type = cudaGraphNodeTypeConditional;
         cp.conditional.handle = sw_handle;
         cp.conditional.type = cudaGraphCondTypeSwitch;
-        cp.conditional.size = (unsigned)shapes.size();
+        cp.conditional.size = (unsigned)sw.buckets;
         cudaGraphNode_t node;
         CUDA_TRY(cudaGraphAddNode(&node, g, deps, edges, nd, &cp));
-        for (size_t k = 0; k < shapes.size(); ++k) {
+        for (int k = 0; k < sw.buckets; ++k) {
             CUDA_TRY(cudaStreamBeginCaptureToGraph(h->shape_stream, cp.conditional.phGraph_out[k], nullptr, nullptr,
                                                    0, cudaStreamCaptureModeRelaxed));
             rc = launch_forward(h, rows, st->obs, st->sigma, h->prop_ll, nullptr, nullptr, h->prop_status,
-                                h->cfg.precision, h->shape_stream, shapes[k], 1, nullptr);
+                                h->cfg.precision, h->shape_stream, round_shape(h, k, rows), 1, nullptr,
+                                (k + 1) * h->num_sms);
             cudaGraph_t captured = nullptr;
             cudaError_t e = cudaStreamEndCapture(h->shape_stream, &captured);
             if (rc) return rc;
@@ -920,8 +906,10 @@ int enqueue_round(swimmer_handle *h, const StageArgs &a, cudaStream_t s, cudaGra
         }
         CUDA_TRY(cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
     } else {
+        h->prof_rows = h->host_pinned[2];  // the profile records the round's A M runs
         rc = launch_forward(h, rows, st->obs, st->sigma, h->prop_ll, nullptr, nullptr, h->prop_status,
-                            h->cfg.precision, s, shape, 1, nullptr);
+                            h->cfg.precision, s, round_shape(h, bucket, rows), 1, nullptr, (bucket + 1) * h->num_sms);
+        h->prof_rows = 0;
         if (rc) return rc;
     }
     tree_resolve_kernel<<<grid, 128, 0, s>>>(h->info + AM, a.P, a.use_surrogate, h->surr_trust, h->surr_dstat,
