@@ -776,6 +776,16 @@ __global__ void __launch_bounds__(BIG ? 512 : 1024, 1) forward_kernel(FwdArgs a)
                 }
             }
             __syncthreads();
+            // (cos, sin)(omega t) of the next step, rotated in FP64 by the last thread, which
+            // has the fewest points here (this step's values were read before the barrier)
+            if (!F64 && tid == T - 1) {
+                const double c = s_rot64[0], sn = s_rot64[1], wc = s_rot64[2], ws = s_rot64[3];
+                const double nc = fma(c, wc, -sn * ws), ns = fma(sn, wc, c * ws);
+                s_rot64[0] = nc;
+                s_rot64[1] = ns;
+                s_rot[0] = (float)nc;
+                s_rot[1] = (float)ns;
+            }
             // ---- C: point forces, gathered per point (no atomics): segment tensions, the
             //      bending stencils of the centres k-1, k, k+1, and for the head model the
             //      diametral and neck springs and the neck angle (Appendix)
@@ -1024,14 +1034,6 @@ __global__ void __launch_bounds__(BIG ? 512 : 1024, 1) forward_kernel(FwdArgs a)
                         }
                     }
                 }
-            }
-            if (!F64 && tid == 0) {  // (cos, sin)(omega t) of the next step, rotated in FP64
-                const double c = s_rot64[0], sn = s_rot64[1], wc = s_rot64[2], ws = s_rot64[3];
-                const double nc = fma(c, wc, -sn * ws), ns = fma(sn, wc, c * ws);
-                s_rot64[0] = nc;
-                s_rot64[1] = ns;
-                s_rot[0] = (float)nc;
-                s_rot[1] = (float)ns;
             }
             if (__syncthreads_or(bad)) {
                 status = SWIMMER_DIVERGED;

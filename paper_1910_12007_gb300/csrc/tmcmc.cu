@@ -429,33 +429,19 @@ __global__ void __launch_bounds__(T1) live_kernel(const int *__restrict__ U_in, 
 // estimated so far, from the master orders made on the host (one per bin of that rate, nodes in
 // best-first order with children after their parents).  Best-first growth under a depth cap
 // takes, in order, the master nodes shallower than the cap, so the tree is the first
-// M = max(1, slots / A) of those, renumbered.  Writes am = {A, M, A M} for the round's kernels
-// and, inside a graph, selects the forward launch shape of A M runs (the switch node's branch of
-// their bucket of samples per SM; none when no chain is live).
+// M = max(1, slots / A) of those, renumbered.  Writes am = {A, M, A M, 0} for the round's
+// kernels; am[3] then counts the rows that will run (candidates and screen below).
 constexpr int TMPL_BINS = 32;
-struct ShapeSwitch {
-    int sms;      // SMs of the device
-    int buckets;  // branches: buckets of 1 .. rows runs by runs per SM, ceil(n / SMs) - 1
-};
-__device__ void select_shape(const ShapeSwitch &sw, cudaGraphConditionalHandle h, int n) {
-    // n = 0: past the last branch, so no forward launch runs
-    cudaGraphSetConditional(h, n > 0 ? min(sw.buckets - 1, (n + sw.sms - 1) / sw.sms - 1) : sw.buckets);
-}
 __global__ void __launch_bounds__(T1) template_kernel(int slots, const int *__restrict__ live_info,
                                                       const double *__restrict__ p_prev,
                                                       const int4 *__restrict__ master, int *__restrict__ map,
                                                       int4 *__restrict__ tmpl, int *__restrict__ am,
-                                                      int *__restrict__ screened, int use_surrogate,
-                                                      ShapeSwitch sw, cudaGraphConditionalHandle sw_handle,
-                                                      int use_switch) {
+                                                      int *__restrict__ screened, int use_surrogate) {
     __shared__ unsigned long long sm[64];
     const int tid = threadIdx.x;
     const int A = live_info[0];
     if (A <= 0) {
-        if (tid == 0) {
-            am[0] = am[1] = am[2] = 0;
-            if (use_switch) select_shape(sw, sw_handle, 0);
-        }
+        if (tid == 0) am[0] = am[1] = am[2] = am[3] = 0;
         return;
     }
     const int cap = min(live_info[1], TREE_DEPTH_MAX);
@@ -487,9 +473,20 @@ __global__ void __launch_bounds__(T1) template_kernel(int slots, const int *__re
         am[0] = A;
         am[1] = M;
         am[2] = A * M;
+        am[3] = 0;
         if (use_surrogate) screened[0] += A * M;
-        if (use_switch) select_shape(sw, sw_handle, A * M);
     }
+}
+
+// The forward launch of a round inside a graph: a switch node with one branch per bucket of
+// runs per SM, ceil(n / SMs) - 1 for the n rows that run (none when n = 0).
+struct ShapeSwitch {
+    int sms;      // SMs of the device
+    int buckets;  // branches: the buckets of 1 .. rows runs
+};
+__global__ void select_kernel(const int *__restrict__ runs, ShapeSwitch sw, cudaGraphConditionalHandle h) {
+    const int n = runs[0];
+    cudaGraphSetConditional(h, n > 0 ? min(sw.buckets - 1, (n + sw.sms - 1) / sw.sms - 1) : sw.buckets);
 }
 
 // candidates of every (live chain, template node): prop[(slot*M + v)*3].  Unreachable nodes
@@ -501,7 +498,7 @@ __global__ void tree_propose_kernel(int rows, const int *__restrict__ am, const 
                                     const int *__restrict__ chain_pos, const double *__restrict__ cur_theta,
                                     const double *__restrict__ st, const double *__restrict__ normals, Box box,
                                     const int4 *__restrict__ tmpl, double *__restrict__ prop,
-                                    int *__restrict__ counter) {
+                                    int *__restrict__ counter, int *__restrict__ runs) {
     int idx = blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= rows) return;
     const int M = am[1];
@@ -530,7 +527,10 @@ __global__ void tree_propose_kernel(int rows, const int *__restrict__ am, const 
     ok = ok && box.in(cand);
     prop[P * idx] = ok ? cand[0] : nan("");
     for (int a = 1; a < P; ++a) prop[P * idx + a] = cand[a];
-    if (ok) atomicAdd(counter, 1);
+    if (ok) {
+        atomicAdd(counter, 1);
+        atomicAdd(runs, 1);
+    }
 }
 
 // delayed acceptance step 1: along the path of each node, every decision is screened by the
@@ -542,7 +542,8 @@ __global__ void tree_screen_kernel(int rows, const int *__restrict__ am, int P, 
                                    const double *__restrict__ cur_sl, const double *__restrict__ prop_sl,
                                    const double *__restrict__ st, const double *__restrict__ u1,
                                    const int4 *__restrict__ tmpl, double *__restrict__ prop,
-                                   int *__restrict__ counter, const int *__restrict__ trust) {
+                                   int *__restrict__ counter, const int *__restrict__ trust,
+                                   int *__restrict__ runs) {
     int idx = blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= rows || idx >= am[2] || !trust[0]) return;  // no screen while the surrogate is not trusted
     if (isnan(prop[P * idx])) return;
@@ -563,8 +564,12 @@ __global__ void tree_screen_kernel(int rows, const int *__restrict__ am, int P, 
         }
     }
     const bool pass = reach && log(u1[row + depth]) < qn * (prop_sl[idx] - bsl);
-    if (!pass) prop[P * idx] = nan("");
-    else atomicAdd(counter, 1);
+    if (!pass) {
+        prop[P * idx] = nan("");
+        atomicSub(runs, 1);
+    } else {
+        atomicAdd(counter, 1);
+    }
 }
 
 // walk each live chain down the template along the decisions it actually takes
@@ -825,15 +830,17 @@ int round_shape(const swimmer_handle *h, int b, int rows) {
 }
 
 // The switch over the buckets of 1 .. rows runs: one branch per bucket (its launch shape, and
-// as many CTAs per SM as the bucket has runs per SM).
+// as many CTAs per SM as the bucket has runs per SM: the running rows, dealt first by the
+// queue, then go one per CTA and spread over the SMs).
 ShapeSwitch round_shapes(const swimmer_handle *h, int rows) { return ShapeSwitch{h->num_sms, tune_bucket(h, rows) + 1}; }
 
 // one pre-fetch round: live chains (and the loop condition), the tree, candidates, the
 // surrogate screen, the forward runs, the walk down the trees.  Every size comes from device
-// memory; the launches cover the round's capacity and idle past the round's rows.  Inside a
-// graph (body != nullptr: the while node's body) the forward launch is a switch node with one
-// branch per launch shape, set by the template kernel from the round's A M.  Driven from the
-// host, the round reads A M back (its one synchronization) and stops when no chain is live.
+// memory; the launches cover the round's capacity and idle past the round's rows.  The
+// candidate and screen kernels count the rows that will run; inside a graph (body != nullptr:
+// the while node's body) the forward launch is a switch node with one branch per bucket of that
+// count, selected on the device.  Driven from the host, the round reads the count back (its one
+// synchronization) and stops when no chain is live.
 int enqueue_round(swimmer_handle *h, const StageArgs &a, cudaStream_t s, cudaGraph_t body,
                   cudaGraphConditionalHandle cond, bool *done) {
     const tmcmc_state *st = a.st;
@@ -841,30 +848,17 @@ int enqueue_round(swimmer_handle *h, const StageArgs &a, cudaStream_t s, cudaGra
     // a round runs A M <= max(slots, B) forward models (M = 1 once the live chains outnumber
     // the slots); the launches cover that many rows
     const int rows = max(slots, a.B);
-    const ShapeSwitch sw = round_shapes(h, rows);
-    cudaGraphConditionalHandle sw_handle = 0;
-    if (body) CUDA_TRY(cudaGraphConditionalHandleCreate(&sw_handle, body, 0, cudaGraphCondAssignDefault));
+    int *runs = h->info + AM + 3;
     live_kernel<<<1, T1, 0, s>>>(h->info, a.B, a.rank, a.world, h->chain_id, h->chain_off, h->chain_len, h->chain_pos,
                                  h->live, h->info + CNT, h->info + LIVE, cond, body != nullptr);
     CUDA_TRY(cudaGetLastError());
     template_kernel<<<1, T1, 0, s>>>(slots, h->info + LIVE, h->p_accept_dev, h->tmpl_master, h->tmpl_map, h->tmpl,
-                                     h->info + AM, h->info + CNT + 4, a.use_surrogate, sw, sw_handle,
-                                     body != nullptr);
+                                     h->info + AM, h->info + CNT + 4, a.use_surrogate);
     CUDA_TRY(cudaGetLastError());
-    int bucket = 0;
-    if (!body) {
-        CUDA_TRY(cudaMemcpyAsync(h->host_pinned, h->info + AM, 3 * sizeof(int), cudaMemcpyDeviceToHost, s));
-        CUDA_TRY(cudaStreamSynchronize(s));
-        if (h->host_pinned[0] <= 0) {
-            *done = true;
-            return 0;
-        }
-        bucket = tune_bucket(h, h->host_pinned[2]);
-    }
     const int grid = (rows + 127) / 128;
     tree_propose_kernel<<<grid, 128, 0, s>>>(rows, h->info + AM, h->live, h->chain_off, h->chain_len, h->chain_pos,
                                              h->cur_theta, h->stats, a.normals, a.box, h->tmpl, h->prop_theta,
-                                             h->info + CNT + 2);
+                                             h->info + CNT + 2, runs);
     CUDA_TRY(cudaGetLastError());
     prof_count(h, 3);
     if (a.use_surrogate) {
@@ -872,9 +866,26 @@ int enqueue_round(swimmer_handle *h, const StageArgs &a, cudaStream_t s, cudaGra
         if (rc) return rc;
         tree_screen_kernel<<<grid, 128, 0, s>>>(rows, h->info + AM, a.P, h->live, h->chain_off, h->chain_pos,
                                                 h->cur_sl, h->prop_sl, h->stats, a.uniforms + a.B, h->tmpl,
-                                                h->prop_theta, h->info + CNT + 1, h->surr_trust);
+                                                h->prop_theta, h->info + CNT + 1, h->surr_trust, runs);
         CUDA_TRY(cudaGetLastError());
         prof_count(h, 1);
+    }
+    const ShapeSwitch sw = round_shapes(h, rows);
+    cudaGraphConditionalHandle sw_handle = 0;
+    int n_run = 0;
+    if (body) {
+        CUDA_TRY(cudaGraphConditionalHandleCreate(&sw_handle, body, 0, cudaGraphCondAssignDefault));
+        select_kernel<<<1, 1, 0, s>>>(runs, sw, sw_handle);
+        CUDA_TRY(cudaGetLastError());
+        prof_count(h, 1);
+    } else {
+        CUDA_TRY(cudaMemcpyAsync(h->host_pinned, h->info + AM, 4 * sizeof(int), cudaMemcpyDeviceToHost, s));
+        CUDA_TRY(cudaStreamSynchronize(s));
+        if (h->host_pinned[0] <= 0) {
+            *done = true;
+            return 0;
+        }
+        n_run = h->host_pinned[3];
     }
     int rc = launch_prepare(h, rows, h->prop_theta, nullptr, s);
     if (!rc) rc = launch_table_build(h, rows, h->cfg.precision == SWIMMER_FP64, s);
@@ -905,8 +916,9 @@ int enqueue_round(swimmer_handle *h, const StageArgs &a, cudaStream_t s, cudaGra
             CUDA_TRY(e);
         }
         CUDA_TRY(cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
-    } else {
-        h->prof_rows = h->host_pinned[2];  // the profile records the round's A M runs
+    } else if (n_run > 0) {
+        const int bucket = tune_bucket(h, n_run);
+        h->prof_rows = n_run;  // the profile records the runs, not the rows the launch covers
         rc = launch_forward(h, rows, st->obs, st->sigma, h->prop_ll, nullptr, nullptr, h->prop_status,
                             h->cfg.precision, s, round_shape(h, bucket, rows), 1, nullptr, (bucket + 1) * h->num_sms);
         h->prof_rows = 0;
