@@ -187,11 +187,14 @@ __device__ __forceinline__ double spring_f64(const double *sx, const double *sy,
     return r.k2 * strain / ell;
 }
 
-// table region in shared memory: FP32: float4 part A [P] then float2 part B [P];
+// table region in shared memory: FP32: float4 part A [P] then float2 part B [P] (24 bytes a
+// panel), or with MERGED one 32-byte record per panel [P][2] float4, so that one address serves
+// both loads of a lookup (the 128-register instantiation, whose launches are held to one or two
+// CTAs per SM by other limits, so the larger table costs no occupancy there);
 // FP64: Chebyshev coefficients of g1 [P][10] then of g2 [P][10]
-template <bool F64>
+template <bool F64, bool MERGED = false>
 __host__ __device__ size_t table_bytes(int P) {
-    return F64 ? sizeof(double) * 2 * P * F64_NODES : (sizeof(float4) + sizeof(float2)) * P;
+    return F64 ? sizeof(double) * 2 * P * F64_NODES : (MERGED ? 2 * sizeof(float4) : sizeof(float4) + sizeof(float2)) * P;
 }
 
 __host__ __device__ inline size_t align32(size_t b) { return (b + 31) & ~size_t(31); }
@@ -227,16 +230,18 @@ __host__ __device__ size_t state_bytes(int n_max, int threads) {
 }
 
 // FP32: the sample's pair units (unit_pack), at most ceil(n_max/32)^2 ints after the table
-template <bool F64>
+template <bool F64, bool MERGED = false>
 __host__ __device__ size_t smem_bytes(int n_max, int P, int threads) {
     const size_t nbm = (n_max + 31) / 32;
-    return state_bytes<F64>(n_max, threads) + table_bytes<F64>(P) + (F64 ? 0 : 4 * nbm * nbm);
+    return state_bytes<F64>(n_max, threads) + table_bytes<F64, MERGED>(P) + (F64 ? 0 : 4 * nbm * nbm);
 }
 
 
 // -g1 and h = delta^2 g2 from the FP32 table: quadratic in G = 1 + f / 64, f in [0, 1) the
 // position of u within its panel.  The table holds -g1, the sign g1 takes in the mobility.
-__device__ __forceinline__ void kern_f32(const float4 *__restrict__ tA, const float2 *__restrict__ tB, int pmax,
+// tab: part A (or the merged records), tB: part B (unused with MERGED).
+template <bool MERGED>
+__device__ __forceinline__ void kern_f32(const float4 *__restrict__ tab, const float2 *__restrict__ tB, int pmax,
                                          float u, float &gn, float &h) {
     // u >= 1: the panel is (exponent - 127) * panels per octave + top mantissa bits; the
     // exponent bias is subtracted after the clamp, where it folds into the load offsets.  G
@@ -245,8 +250,16 @@ __device__ __forceinline__ void kern_f32(const float4 *__restrict__ tA, const fl
     const unsigned bits = __float_as_uint(u);
     const int p = (int)min(bits >> (23 - F32_SUB_LOG2), (unsigned)(pmax + BIAS));
     const float G = __uint_as_float(0x3f800000u | (bits & ((1u << (23 - F32_SUB_LOG2)) - 1u)));
-    const float4 a = tA[p - BIAS];
-    const float2 c = tB[p - BIAS];
+    float4 a;
+    float2 c;
+    if (MERGED) {
+        const float4 *rec = tab + 2 * (p - BIAS);  // (-g1 c0, c1, c2, h c0), (h c1, h c2, ., .)
+        a = rec[0];
+        c = *(const float2 *)(rec + 1);
+    } else {
+        a = tab[p - BIAS];
+        c = tB[p - BIAS];
+    }
     gn = fmaf(G, fmaf(G, a.z, a.y), a.x);
     h = fmaf(G, fmaf(G, c.y, c.x), a.w);
 }
@@ -274,10 +287,10 @@ __device__ __forceinline__ int plane_prev(int k) { return (k & ~31) | ((k - 1) &
 // source after it; at the end each source's two sums are brought to its own lane.  A
 // diagonal block runs d = 1 .. 16, and at d = 16 only lanes < 16 count (lanes l and l + 16
 // meet the same pair there).  Adds the unit's sums into the warp's partial array.
-template <int R, bool DIAG>
-__device__ __forceinline__ void pair_unit(const float4 *__restrict__ s4, const float4 *__restrict__ t1,
-                                          const float2 *__restrict__ t2, int pmax, int lane, int I0, int I1,
-                                          int I2, int I3, int Jb, int d0, float2 *__restrict__ mypart) {
+template <int R, bool DIAG, bool MERGED>
+__device__ __forceinline__ void pair_unit(const float4 *__restrict__ s4, const float4 *__restrict__ tab,
+                                          const float2 *__restrict__ tB, int pmax, int lane, int I0, int I1, int I2,
+                                          int I3, int Jb, int d0, float2 *__restrict__ mypart) {
     const int I[4] = {I0, I1, I2, I3};
     const float2 one = dup2(1.f), neg1 = dup2(-1.f);
     float2 mx[R], my[R], mz[R], mw[R], vx[R], vy[R];
@@ -305,8 +318,8 @@ __device__ __forceinline__ void pair_unit(const float4 *__restrict__ s4, const f
             const float2 ex = __ffma2_rn(qx, neg1, mx[r]), ey = __ffma2_rn(qy, neg1, my[r]);
             const float2 u = __ffma2_rn(ex, ex, __ffma2_rn(ey, ey, one));
             float2 gn, h;
-            kern_f32(t1, t2, pmax, u.x, gn.x, h.x);
-            kern_f32(t1, t2, pmax, u.y, gn.y, h.y);
+            kern_f32<MERGED>(tab, tB, pmax, u.x, gn.x, h.x);
+            kern_f32<MERGED>(tab, tB, pmax, u.y, gn.y, h.y);
             if (DIAG && k == 7 && lane >= 16) {  // step 16 of a diagonal block: lanes < 16 only
                 gn.y = 0.f;
                 h.y = 0.f;
@@ -415,6 +428,7 @@ __device__ __forceinline__ void head_centre(const double *sx, const double *sy, 
 template <bool F64, int MODEL, bool BIG = false>
 __global__ void __launch_bounds__(BIG ? 512 : 1024, 1) forward_kernel(FwdArgs a) {
     constexpr bool HEAD = MODEL >= 1, TWO = MODEL == 2;
+    constexpr bool MERGED = !F64 && BIG;  // the FP32 table as 32-byte records (see table_bytes)
     typedef typename Types<F64>::R R;
     typedef typename Types<F64>::R4 R4;
     extern __shared__ __align__(32) unsigned char smraw[];
@@ -492,14 +506,19 @@ __global__ void __launch_bounds__(BIG ? 512 : 1024, 1) forward_kernel(FwdArgs a)
             float4 *t = (float4 *)tabraw;
             float2 *tb = (float2 *)(t + P);
             for (int i = tid; i < npan; i += T) {
-                t[i] = g[i];
-                tb[i] = gb[i];
+                if (MERGED) {
+                    t[2 * i] = g[i];
+                    t[2 * i + 1] = make_float4(gb[i].x, gb[i].y, 0.f, 0.f);
+                } else {
+                    t[i] = g[i];
+                    tb[i] = gb[i];
+                }
             }
             // the sample's pair units, from the handle's list for its block count
             const int nbs = (n + 31) >> 5;
             const unsigned *hdr = a.units + a.mode * (UNIT_NB_MAX + 1);
             const unsigned *ul = a.units + UNIT_HDR + hdr[nbs - 1];
-            unsigned *units = (unsigned *)(tabraw + table_bytes<F64>(P));
+            unsigned *units = (unsigned *)(tabraw + table_bytes<F64, MERGED>(P));
             for (int un = tid; un < (int)(hdr[nbs] - hdr[nbs - 1]); un += T) units[un] = ul[un];
         }
         // ---- initial straight filament X_k = (k ds, 0), stored relative to (L/2, 0); the
@@ -622,7 +641,7 @@ __global__ void __launch_bounds__(BIG ? 512 : 1024, 1) forward_kernel(FwdArgs a)
         long long steps_done = a.steps;
         __syncthreads();
         if (!F64 && tid == 0)
-            assign_units((unsigned *)(tabraw + table_bytes<F64>(P)), n_units, n_pw, (unsigned *)part, s_wstart);
+            assign_units((unsigned *)(tabraw + table_bytes<F64, MERGED>(P)), n_units, n_pw, (unsigned *)part, s_wstart);
         __syncthreads();
         const R r_ds = F64 ? (R)ds : (R)s_f32[F_DS], r_inv2ds = F64 ? (R)(0.5 / ds) : (R)s_f32[F_INV2DS];
         const R r_invds2 = F64 ? (R)(1.0 / (ds * ds)) : (R)s_f32[F_INVDS2];
@@ -640,8 +659,8 @@ __global__ void __launch_bounds__(BIG ? 512 : 1024, 1) forward_kernel(FwdArgs a)
         float g10 = 0.f;  // FP32: -g1 at r = 0 (self term)
         if (!F64) {
             float g2unused;
-            kern_f32((const float4 *)tabraw, (const float2 *)((const float4 *)tabraw + P), npan - 1, 1.0f, g10,
-                     g2unused);
+            kern_f32<MERGED>((const float4 *)tabraw, (const float2 *)((const float4 *)tabraw + P), npan - 1, 1.0f,
+                             g10, g2unused);
         }
 
         // with a final state requested, one more pass of the force phases at t = steps dt
@@ -961,12 +980,12 @@ __global__ void __launch_bounds__(BIG ? 512 : 1024, 1) forward_kernel(FwdArgs a)
                 // warp adds its units' sums into its own partial array, in a fixed order, so
                 // the result does not depend on scheduling.
                 const float4 *s4 = (const float4 *)src;
-                const float4 *t1 = (const float4 *)tabraw;
-                const float2 *t2 = (const float2 *)(t1 + P);
+                const float4 *tab = (const float4 *)tabraw;
+                const float2 *tB = (const float2 *)(tab + P);
                 const int warp = tid >> 5;
                 float2 *mypart = part + warp * (nb << 5);
                 for (int k = lane; k < (nb << 5); k += 32) mypart[k] = make_float2(0.f, 0.f);
-                const unsigned *units = (const unsigned *)(tabraw + table_bytes<F64>(P));
+                const unsigned *units = (const unsigned *)(tabraw + table_bytes<F64, MERGED>(P));
                 for (int un = s_wstart[warp]; un < s_wstart[warp + 1]; ++un) {
                     const unsigned pk = units[un];
                     const int I = pk & 31, Jb = (pk >> 5) & 31, code = (pk >> 25) & 3, kind = (pk >> 27) & 3;
@@ -974,13 +993,13 @@ __global__ void __launch_bounds__(BIG ? 512 : 1024, 1) forward_kernel(FwdArgs a)
                     const int I2 = (pk >> 10) & 31, I3 = (pk >> 15) & 31, I4 = (pk >> 20) & 31;
                     if (kind == 0) {
                         if (I == Jb)
-                            pair_unit<1, true>(s4, t1, t2, npan - 1, lane, I, 0, 0, 0, Jb, d0, mypart);
+                            pair_unit<1, true, MERGED>(s4, tab, tB, npan - 1, lane, I, 0, 0, 0, Jb, d0, mypart);
                         else
-                            pair_unit<1, false>(s4, t1, t2, npan - 1, lane, I, 0, 0, 0, Jb, d0, mypart);
+                            pair_unit<1, false, MERGED>(s4, tab, tB, npan - 1, lane, I, 0, 0, 0, Jb, d0, mypart);
                     } else if (BIG && kind == 2) {
-                        pair_unit<4, false>(s4, t1, t2, npan - 1, lane, I, I2, I3, I4, Jb, d0, mypart);
+                        pair_unit<4, false, MERGED>(s4, tab, tB, npan - 1, lane, I, I2, I3, I4, Jb, d0, mypart);
                     } else {
-                        pair_unit<2, false>(s4, t1, t2, npan - 1, lane, I, I2, 0, 0, Jb, d0, mypart);
+                        pair_unit<2, false, MERGED>(s4, tab, tB, npan - 1, lane, I, I2, 0, 0, Jb, d0, mypart);
                         // the host gives four-target lists to the 128-register instantiation
                         // only; a run that meets one here ends as diverged, not with pairs missing
                         if (kind == 2) bad = 1;
@@ -1387,14 +1406,20 @@ int launch_forward(swimmer_handle *h, int B, const double *obs, double sigma, do
     if (per_sm > 1) per_sm = min(per_sm, (runs + h->num_sms - 1) / h->num_sms);
     // FP32 with shared memory for so few threads per SM that each could hold 128 registers:
     // the instantiation compiled for that register budget (same CTAs per SM)
-    if (!f64 && T <= 512 && per_sm >= 1 && (long long)per_sm * T * 128 <= h->regs_per_sm) {
+    // (with the table as 32-byte records, if that still fits)
+    const size_t smem_big = smem_bytes<false, true>(a.n_max, a.tab_panels, T);
+    if (!f64 && T <= 512 && per_sm >= 1 && (long long)per_sm * T * 128 <= h->regs_per_sm &&
+        smem_big + 1024 <= (size_t)h->max_smem) {
         auto big = forward_kernel_for(f64, h->cfg, true);
         int per_big = 0;
-        CUDA_TRY(cudaFuncSetAttribute(big, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        CUDA_TRY(cudaFuncSetAttribute(big, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_big));
         CUDA_TRY(cudaFuncSetAttribute(big, cudaFuncAttributePreferredSharedMemoryCarveout,
                                       cudaSharedmemCarveoutMaxShared));
-        CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_big, big, T, smem));
-        if (per_big >= per_sm) kern = big;
+        CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_big, big, T, smem_big));
+        if (per_big >= per_sm) {
+            kern = big;
+            smem = smem_big;
+        }
     }
     // four-target units need the 128-register budget; elsewhere the launch runs two-target ones
     if (a.mode == 2 && kern == forward_kernel_for(f64, h->cfg)) a.mode = 1;
