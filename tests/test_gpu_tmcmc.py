@@ -385,3 +385,47 @@ def test_stage_async_captured_in_a_graph_replays_the_eager_stage(precision):
         check_summary()
     del graph
     h.close()
+
+
+def test_stage_rounds_at_the_workload_size_same_in_graph_and_host_loop():
+    """At the TMCMC workload's size (1024 samples, N = 128, FP32, autotuned launch shapes) the
+    pre-fetch rounds launch their forward runs with the shape and grid of the rows that run:
+    a switch node selects the branch on the device inside the stage graph, and the
+    host-driven loop (profiling) reads the same count.  Both must give the same stage bit for
+    bit, every round's recorded rows must be positive and no more than the rows a round can
+    hold, and together they cover every chain step (Algorithm 1: one exact run per step)."""
+    p = sw.SwimmerParams(n=128, dt=1e-4 / 64, steps=400, obs_every=10, k_t=1e3)
+    B, seed, P = 1024, 47, 3
+    obs, _, _, _ = sw.run_c_batch([p.with_theta(TRUTH)])
+    xi = obs[0]
+    sigma = 0.05 * float(np.mean(np.abs(xi - [p.length, 0.0])))
+    D = xi + sigma * synthetic.normals(1236, synthetic.NOISE, 0, xi.size).reshape(xi.shape)
+    cfg = g.SwimmerConfig(n_max=p.n, b_max=B, length=p.length, dt=p.dt, k_t=p.k_t, steps=p.steps,
+                          obs_every=p.obs_every, precision=g.FP32C)
+    h = g.swimmer_init(cfg)
+    th0 = torch.tensor(synthetic.prior_samples(seed, LO, HI, B), device=DEV)
+    g.swimmer_autotune(h, steps=200, theta=th0)
+    obs_d = torch.tensor(D, device=DEV)
+    ll0, _ = g.loglik_batch(h, th0, obs_d, sigma)
+    states = {}
+    for mode in ("graph", "host"):
+        st = g.TmcmcState(th0.clone(), ll0.clone(), obs_d, sigma, LO, HI)
+        for j in range(3):
+            u_res, u_acc, z = synthetic.stage_randoms(seed, j, B, P)
+            U = torch.tensor(np.concatenate([u_res[None], u_acc]), device=DEV)
+            if mode == "host":
+                g.swimmer_profile(h, 1)
+            s = g.tmcmc_stage(h, st, U, torch.tensor(z, device=DEV))
+            if mode == "host":
+                rounds = g.swimmer_profile_launches(h)
+                g.swimmer_profile(h, 0)
+                runs = [n for _, n in rounds]
+                assert len(runs) >= 2 and all(0 < n <= B for n in runs), runs
+                # every chain step ran once on its realized path; speculative runs add to that
+                assert sum(runs) >= s["n_exact_path"]
+        torch.cuda.synchronize()
+        states[mode] = (st.theta.clone(), st.loglik.clone(), st.q)
+    h.close()
+    assert torch.equal(states["graph"][0], states["host"][0])
+    assert torch.equal(states["graph"][1], states["host"][1])
+    assert states["graph"][2] == states["host"][2]
