@@ -298,7 +298,9 @@ enum {
  *           another Metropolis pass at the posterior);
  *   summary device FP64 [SWIMMER_STAGE_SUMMARY]: the stage's summary record (above).
  * The Metropolis chains' pre-fetch rounds run as a loop whose condition the device sets, so a
- * stage's length needs no host decision.  When `stream` is being captured into a CUDA graph
+ * stage's length needs no host decision; each round's forward launch takes the launch shape
+ * and CTAs per SM of the rows that run in it (a conditional switch node, set on the device,
+ * with one branch per bucket of runs per SM).  When `stream` is being captured into a CUDA graph
  * the stage becomes part of that graph (a conditional while node holds the rounds) and every
  * replay runs a whole stage; otherwise the stage builds, launches and releases a graph of its
  * own.  Uses the handle's internal streams for the capture: one stage of a handle at a time. */

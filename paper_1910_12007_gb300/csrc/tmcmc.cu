@@ -724,7 +724,7 @@ namespace {
 // One stage, enqueued without host synchronization.  Device counters (ints at info + 64):
 // [0] accepted, [1] screen passes, [2] proposals run, [3] runs on the realized paths,
 // [4] surrogate evaluations; [8..11] the round's live chains, largest remaining length,
-// accepted and decided so far; [16..18] the round's A, M, A M.
+// accepted and decided so far; [16..19] the round's A, M, A M and rows that run.
 // ---------------------------------------------------------------------------------
 constexpr int CNT = 64, LIVE = CNT + 8, AM = CNT + 16;
 constexpr double SURR_ERR_MAX = 1.0;    // nats: spread of l - l~ allowed for screening
@@ -845,8 +845,8 @@ int enqueue_round(swimmer_handle *h, const StageArgs &a, cudaStream_t s, cudaGra
                   cudaGraphConditionalHandle cond, bool *done) {
     const tmcmc_state *st = a.st;
     const int slots = h->tmpl_slots;
-    // a round runs A M <= max(slots, B) forward models (M = 1 once the live chains outnumber
-    // the slots); the launches cover that many rows
+    // a round has A M <= max(slots, B) tree nodes (M = 1 once the live chains outnumber the
+    // slots); the launches cover that many rows, of which the counted ones run
     const int rows = max(slots, a.B);
     int *runs = h->info + AM + 3;
     live_kernel<<<1, T1, 0, s>>>(h->info, a.B, a.rank, a.world, h->chain_id, h->chain_off, h->chain_len, h->chain_pos,
