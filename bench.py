@@ -279,6 +279,8 @@ def main():
     import paper_1910_12007_gb300 as g
     import synthetic
 
+    if args.profile_case and args.workload == "surrogate":
+        return profile_case_mlp(args, local_rank)
     if args.profile_case and args.workload == "large":
         return profile_case_large(args, local_rank)
     if args.workload in ("uneven", "large", "sperm", "two-sperm"):
@@ -621,6 +623,41 @@ def forms_leg(dev, seed=700):
 def shape_arg(g, s):
     """--shape value: threads per sample, suffix w (q) for two- (four-) target pair units."""
     return int(s.rstrip("wq")) | {"w": g.SHAPE_WIDE, "q": g.SHAPE_QUAD}.get(s[-1], 0)
+
+
+def profile_case_mlp(args, local_rank):
+    """The surrogate MLP's forward and backward passes on 4096 samples (the delayed-acceptance
+    workload's stage size), twice each: the second launches are the ones to capture."""
+    import numpy as np
+    import torch
+
+    import paper_1910_12007_gb300 as g
+    from paper_1910_12007_gb300 import api
+    from paper_1910_12007_gb300 import surrogate as sg
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    n = 4096
+    params = sg.init_params(1, dev)
+    rng = np.random.default_rng(5)
+    x = torch.tensor(rng.uniform(-1, 1, (n, api.MLP_IN)), dtype=torch.float32, device=dev)
+    t = torch.tensor(rng.normal(0, 1, (n, api.MLP_OUT)), dtype=torch.float32, device=dev)
+    ws = g.mlp_workspace(n, dev)
+    times = []
+    for _ in range(2):
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        e0.record()
+        y = g.mlp_forward(params, x, workspace=ws)
+        e1.record()
+        grad, loss = g.mlp_backward(params, x, t, workspace=ws)
+        e2.record()
+        torch.cuda.synchronize()
+        times.append((e0.elapsed_time(e1), e1.elapsed_time(e2)))
+    flops_fwd = 2.0 * n * (5 * 256 + 256 * 256 * 2 + 256 * 80)
+    print(json.dumps({"profile_case": f"MLP 5-256-256-256-80, {n} samples", "forward_ms": times[-1][0],
+                      "backward_ms": times[-1][1], "forward_tflops": flops_fwd / (times[-1][0] * 1e-3) / 1e12,
+                      "finite": bool(torch.isfinite(y).all() and torch.isfinite(grad).all())}))
+    return 0
 
 
 def profile_case_large(args, local_rank):

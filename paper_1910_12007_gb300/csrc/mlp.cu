@@ -7,8 +7,9 @@
 // output tiles.  The first layer (5 inputs, which stay FP32) runs through a tiled FP32 GEMM
 // (64 x 64 tiles, 16-deep K panels, 4 x 4 outputs per thread).  Both carry fused epilogues:
 // bias + GELU for the forward pass, the GELU derivative for the backward pass.  Weight
-// gradients reduce over the batch inside one tile (no atomics), so gradients are
-// deterministic.
+// gradients reduce over the batch in up to 16 slices of the batch (split K, so that the 16
+// output tiles of a 256 x 256 gradient fill the GPU), whose partial products are then summed
+// in a fixed order (no atomics), so gradients are deterministic.
 #include <cuda_bf16.h>
 #include <math.h>
 
@@ -38,10 +39,11 @@ __device__ __forceinline__ float gelu_grad(float z) {
 __device__ __forceinline__ float bf16r(float w) { return __bfloat162float(__float2bfloat16_rn(w)); }
 
 // C[m][n] = epi( sum_k A(m, k) B(k, n) ),  A(m, k) = A[m*sam + k*sak], B(k, n) = B[k*sbk + n*sbn]
-// round_b: B holds weights, rounded to BF16 on load.
+// round_b: B holds weights, rounded to BF16 on load.  Split K (gridDim.z > 1, EPI_PLAIN):
+// CTA z sums k in [z kc, (z + 1) kc) into the partial plane C + z M ldc.
 constexpr int TM = 64, TN = 64, TK = 16;
-__global__ void __launch_bounds__(256) gemm_kernel(int M, int N, int K, const float *__restrict__ A, int sam, int sak,
-                                                  const float *__restrict__ B, int sbk, int sbn, int round_b,
+__global__ void __launch_bounds__(256) gemm_kernel(int M, int N, int K, int kc, const float *__restrict__ A, int sam,
+                                                  int sak, const float *__restrict__ B, int sbk, int sbn, int round_b,
                                                   float *__restrict__ C, int ldc, int epi,
                                                   const float *__restrict__ bias, const float *__restrict__ Z,
                                                   int ldz, float *__restrict__ C2) {
@@ -49,17 +51,19 @@ __global__ void __launch_bounds__(256) gemm_kernel(int M, int N, int K, const fl
     __shared__ float Bs[TK][TN + 1];
     const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
     const int m0 = blockIdx.y * TM, n0 = blockIdx.x * TN;
+    const int kb = blockIdx.z * kc, ke = min(K, kb + kc);
+    C += (size_t)blockIdx.z * M * ldc;
     float acc[4][4] = {};
-    for (int k0 = 0; k0 < K; k0 += TK) {
+    for (int k0 = kb; k0 < ke; k0 += TK) {
         for (int e = threadIdx.x; e < TM * TK; e += 256) {
             int mm = e / TK, kk = e % TK;
             int m = m0 + mm, k = k0 + kk;
-            As[kk][mm] = (m < M && k < K) ? A[(size_t)m * sam + (size_t)k * sak] : 0.f;
+            As[kk][mm] = (m < M && k < ke) ? A[(size_t)m * sam + (size_t)k * sak] : 0.f;
         }
         for (int e = threadIdx.x; e < TK * TN; e += 256) {
             int kk = e / TN, nn = e % TN;
             int k = k0 + kk, n = n0 + nn;
-            float v = (k < K && n < N) ? B[(size_t)k * sbk + (size_t)n * sbn] : 0.f;
+            float v = (k < ke && n < N) ? B[(size_t)k * sbk + (size_t)n * sbn] : 0.f;
             Bs[kk][nn] = round_b ? bf16r(v) : v;
         }
         __syncthreads();
@@ -134,9 +138,10 @@ __device__ __forceinline__ void tc_stage(unsigned *S, const float *__restrict__ 
         }
     }
 }
-// C[m][n] = epi( sum_k A(m, k) B(k, n) ), A(m, k) = A[m*sam + k*sak], B(k, n) = B[k*sbk + n*sbn]
-__global__ void __launch_bounds__(128) gemm_tc_kernel(int M, int N, int K, const float *__restrict__ A, int sam,
-                                                     int sak, const float *__restrict__ B, int sbk, int sbn,
+// C[m][n] = epi( sum_k A(m, k) B(k, n) ), A(m, k) = A[m*sam + k*sak], B(k, n) = B[k*sbk + n*sbn];
+// split K as in gemm_kernel (kc a multiple of the 32-deep panel)
+__global__ void __launch_bounds__(128) gemm_tc_kernel(int M, int N, int K, int kc, const float *__restrict__ A,
+                                                     int sam, int sak, const float *__restrict__ B, int sbk, int sbn,
                                                      float *__restrict__ C, int ldc, int epi,
                                                      const float *__restrict__ bias, const float *__restrict__ Z,
                                                      int ldz, float *__restrict__ C2) {
@@ -146,10 +151,12 @@ __global__ void __launch_bounds__(128) gemm_tc_kernel(int M, int N, int K, const
     const int gid = lane >> 2, tig = lane & 3;
     const int wm = (warp >> 1) * 32, wn = (warp & 1) * 32;
     const int m0 = blockIdx.y * TC_TM, n0 = blockIdx.x * TC_TN;
+    const int kb = blockIdx.z * kc, ke = min(K, kb + kc);
+    C += (size_t)blockIdx.z * M * ldc;
     float acc[2][4][4] = {};
-    for (int k0 = 0; k0 < K; k0 += TC_TK) {
-        tc_stage(As, A, M, K, m0, k0, sam, sak);
-        tc_stage(Bs, B, N, K, n0, k0, sbn, sbk);
+    for (int k0 = kb; k0 < ke; k0 += TC_TK) {
+        tc_stage(As, A, M, ke, m0, k0, sam, sak);
+        tc_stage(Bs, B, N, ke, n0, k0, sbn, sbk);
         __syncthreads();
 #pragma unroll
         for (int ks = 0; ks < TC_TK; ks += 16) {
@@ -192,13 +199,32 @@ __global__ void __launch_bounds__(128) gemm_tc_kernel(int M, int N, int K, const
             }
 }
 
-// column sums (bias gradients): out[n] = sum_m X[m][n], fixed order
-__global__ void colsum_kernel(int M, int N, const float *__restrict__ X, int ldx, float *__restrict__ out) {
-    int n = blockIdx.x * blockDim.x + threadIdx.x;
-    if (n >= N) return;
+// column sums (bias gradients): out[n] = sum_m X[m][n] in a fixed order: 32 columns per CTA,
+// row group g (of 32) sums rows g, g + 32, ..., then the groups add in order
+__global__ void __launch_bounds__(1024) colsum_kernel(int M, int N, const float *__restrict__ X, int ldx,
+                                                      float *__restrict__ out) {
+    __shared__ float red[32][33];
+    const int c = threadIdx.x & 31, gr = threadIdx.x >> 5;
+    const int n = blockIdx.x * 32 + c;
     float s = 0.f;
-    for (int m = 0; m < M; ++m) s += X[(size_t)m * ldx + n];
-    out[n] = s;
+    if (n < N)
+        for (int m = gr; m < M; m += 32) s += X[(size_t)m * ldx + n];
+    red[gr][c] = s;
+    __syncthreads();
+    if (gr == 0 && n < N) {
+        float t = 0.f;
+        for (int g = 0; g < 32; ++g) t += red[g][c];
+        out[n] = t;
+    }
+}
+
+// split-K partial planes P[z][m][n] (z < S) summed in order into C[m][n]
+__global__ void splitk_reduce_kernel(int M, int N, int S, const float *__restrict__ P, float *__restrict__ C, int ldc) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= M * N) return;
+    float t = 0.f;
+    for (int z = 0; z < S; ++z) t += P[(size_t)z * M * N + i];
+    C[(size_t)(i / N) * ldc + i % N] = t;
 }
 
 // dY = 2 (Y - T)/(M N) and per-row squared error (for the loss)
@@ -242,24 +268,47 @@ __global__ void adam_kernel(int n, float *__restrict__ p, const float *__restric
 
 // tensor_core: BF16 operands on the tensor cores (the 256-wide layers); else the FP32 SIMT
 // product with BF16 weights (the first layer, whose 5 inputs stay unrounded)
+// part: scratch for split-K partial planes (SPLIT_MAX x M x N floats), or nullptr for no split.
+// A long K over few output tiles (the weight gradients: K = the batch, 16 tiles of 256 x 256)
+// is split so that about two CTAs per SM run; the planes are summed in a fixed order.
+constexpr int SPLIT_MAX = 16, SPLIT_MIN_K = 256;
 int gemm(cudaStream_t s, bool tensor_core, int M, int N, int K, const float *A, int sam, int sak, const float *B,
          int sbk, int sbn, int round_b, float *C, int ldc, int epi, const float *bias = nullptr,
-         const float *Z = nullptr, int ldz = 0, float *C2 = nullptr) {
-    if (tensor_core) {
-        dim3 grid((N + TC_TN - 1) / TC_TN, (M + TC_TM - 1) / TC_TM);
-        gemm_tc_kernel<<<grid, 128, 0, s>>>(M, N, K, A, sam, sak, B, sbk, sbn, C, ldc, epi, bias, Z, ldz, C2);
-    } else {
-        dim3 grid((N + TN - 1) / TN, (M + TM - 1) / TM);
-        gemm_kernel<<<grid, 256, 0, s>>>(M, N, K, A, sam, sak, B, sbk, sbn, round_b, C, ldc, epi, bias, Z, ldz, C2);
+         const float *Z = nullptr, int ldz = 0, float *C2 = nullptr, float *part = nullptr) {
+    const int tm = tensor_core ? TC_TM : TM, tn = tensor_core ? TC_TN : TN, tk = tensor_core ? TC_TK : TK;
+    const int tiles = ((N + tn - 1) / tn) * ((M + tm - 1) / tm);
+    int split = 1;
+    if (part && epi == EPI_PLAIN) {
+        int dev = 0, sms = 0;
+        CUDA_TRY(cudaGetDevice(&dev));
+        CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        split = (2 * sms + tiles - 1) / tiles;
+        split = max(1, min(split, min(SPLIT_MAX, K / SPLIT_MIN_K)));
     }
+    int kc = (K + split - 1) / split;
+    kc = (kc + tk - 1) / tk * tk;
+    split = (K + kc - 1) / kc;
+    float *dst = split > 1 ? part : C;
+    const int ldd = split > 1 ? N : ldc;
+    dim3 grid((N + tn - 1) / tn, (M + tm - 1) / tm, split);
+    if (tensor_core)
+        gemm_tc_kernel<<<grid, 128, 0, s>>>(M, N, K, kc, A, sam, sak, B, sbk, sbn, dst, ldd, epi, bias, Z, ldz, C2);
+    else
+        gemm_kernel<<<grid, 256, 0, s>>>(M, N, K, kc, A, sam, sak, B, sbk, sbn, round_b, dst, ldd, epi, bias, Z, ldz,
+                                         C2);
     CUDA_TRY(cudaGetLastError());
+    if (split > 1) {
+        splitk_reduce_kernel<<<(M * N + 255) / 256, 256, 0, s>>>(M, N, split, part, C, ldc);
+        CUDA_TRY(cudaGetLastError());
+    }
     return 0;
 }
 
 // workspace layout for n samples: Z[l] and H[l] for the 3 hidden layers (n x 256 each),
-// Y (n x 80), dY (n x 80), two gradient buffers (n x 256), row errors (n)
+// Y (n x 80), dY (n x 80), two gradient buffers (n x 256), row errors (n), then the split-K
+// partial planes of the weight gradients (SPLIT_MAX x 256 x 256)
 struct Ws {
-    float *Z[3], *H[3], *Y, *dY, *G0, *G1, *rowerr;
+    float *Z[3], *H[3], *Y, *dY, *G0, *G1, *rowerr, *part;
 };
 Ws carve(float *w, int n) {
     Ws s;
@@ -279,6 +328,8 @@ Ws carve(float *w, int n) {
     s.G1 = w + o;
     o += (size_t)n * HID;
     s.rowerr = w + o;
+    o += (size_t)n;
+    s.part = w + o;
     return s;
 }
 
@@ -301,7 +352,7 @@ int forward_all(cudaStream_t s, int n, const float *P, const float *x, float *y,
 }  // namespace
 
 extern "C" size_t mlp_workspace_bytes(int n) {
-    return sizeof(float) * ((size_t)n * (6 * HID + 2 * OUT + 2 * HID) + n);
+    return sizeof(float) * ((size_t)n * (6 * HID + 2 * OUT + 2 * HID) + n + (size_t)SPLIT_MAX * HID * HID);
 }
 
 extern "C" int mlp_forward(int n, const float *params, const float *x, float *y, float *workspace, void *stream) {
@@ -331,9 +382,10 @@ extern "C" int mlp_backward(int n, const float *params, const float *x, const fl
         const float *W = params + w_off(l);
         const float *hin = l > 0 ? w.H[l - 1] : x;
         // dW[o][i] = sum_s dZ[s][o] H[s][i]   (M = fo, N = fi, K = n)
-        rc = gemm(s, l > 0, fo, fi, n, dz, 1, fo, hin, fi, 1, 0, grad + w_off(l), fi, EPI_PLAIN);
+        rc = gemm(s, l > 0, fo, fi, n, dz, 1, fo, hin, fi, 1, 0, grad + w_off(l), fi, EPI_PLAIN, nullptr, nullptr, 0,
+                  nullptr, w.part);
         if (rc) return rc;
-        colsum_kernel<<<(fo + 127) / 128, 128, 0, s>>>(n, fo, dz, fo, grad + b_off(l));
+        colsum_kernel<<<(fo + 31) / 32, 1024, 0, s>>>(n, fo, dz, fo, grad + b_off(l));
         CUDA_TRY(cudaGetLastError());
         if (l > 0) {
             // dZ_{l-1}[s][i] = (sum_o dZ[s][o] W[o][i]) * gelu'(Z_{l-1}[s][i])
