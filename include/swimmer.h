@@ -143,8 +143,8 @@ int swimmer_kernel_eval(swimmer_handle *h, double alpha, double delta, double r_
                         const double *r, double *g1, double *g2, int precision, void *stream);
 
 /* Allocation-free variant of swimmer_kernel_eval, for callers that cannot allocate device
- * memory (for example code running while another component's stream capture is open, where
- * allocation fails, or services whose device-memory budget is fixed at start-up).  No
+ * memory (for example services whose device-memory budget is fixed at start-up, or code that
+ * must not grow the process's allocations per request).  No
  * handle: the table build of the one sample runs on scratch held in file-scope device
  * arrays (about 98 KB, kept by every GPU that loads the library until the process exits).
  * The paper has no counterpart; this is an interface convenience.
@@ -153,8 +153,8 @@ int swimmer_kernel_eval(swimmer_handle *h, double alpha, double delta, double r_
  *     rejected with SWIMMER_E_ARG and a message.
  *   - Allocates nothing (no cudaMalloc, cudaFree or allocating library routine).
  *   - The first call on a device does a one-time set-up on that device (device addresses of
- *     the arrays, constant tables, kernel attributes); make that first call before any
- *     stream capture.
+ *     the arrays, constant tables, kernel attributes, loading of the kernels); later calls
+ *     on that device only launch kernels.
  *   - Every call on a device shares the arrays, which keep the last call's contents; calls
  *     that overlap on the GPU (different streams, no ordering) race and give wrong results. */
 int swimmer_kernel_eval_noalloc(double alpha, double delta, double r_max, int m, const double *r,

@@ -744,9 +744,8 @@ int launch_kernel_eval(swimmer_handle *h, int m, const double *r, double *g1, do
 // ---------------------------------------------------------------------------------
 // Allocation-free kernel-function evaluation
 // ---------------------------------------------------------------------------------
-// Some callers may not allocate device memory at all: code that runs while someone else's
-// stream capture is open (allocation inside a capture region fails), or services that fix
-// their device-memory budget at start-up and must not grow it per request.  For them the
+// Some callers may not allocate device memory at all: services that fix their device-memory
+// budget at start-up and must not grow it per request.  For them the
 // table build of one sample (the kernels above that use scratch memory) runs on scratch
 // that lives in file-scope device arrays: every GPU that loads this library holds these
 // ~98 KB until the process exits, and every call on a device shares them.

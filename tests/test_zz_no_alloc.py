@@ -1,9 +1,8 @@
 """The allocation-free kernel-function entry point (swimmer_kernel_eval_noalloc) against the
 handle-based swimmer_kernel_eval.
 
-It serves callers that may not allocate device memory (open stream captures elsewhere in the
-process, fixed start-up memory budgets): its scratch is static device memory shared by all
-calls on a device.  This file is collected last so that a run stopping at the first failure
+It serves callers that may not allocate device memory (fixed start-up memory budgets): its
+scratch is static device memory shared by all calls on a device.  This file is collected last so that a run stopping at the first failure
 has already run every other test; it passes alone in a fresh process as well.
 """
 import numpy as np
